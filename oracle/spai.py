@@ -1,0 +1,217 @@
+"""Sparse approximate inverse Q ~ M^-1 on a prescribed sparsity pattern (Sec. 5, SPAI paragraph).
+
+Oracle (test infrastructure).  Column by column (Eq. FrobeniusDecomp), the
+entries allowed in column l, I_l, solve the small normal-equation system of
+Eq. NormalEqSolve,
+    q_l(I_l) = [M(:, I_l)^T M(:, I_l)]^-1 M(:, I_l)^T 1_l ,
+then Q <- (Q + Q^T)/2 (symmetrisation, same paragraph), then an SPD check and,
+if needed, a diagonal shift (Sec. 5.1, practical considerations).
+Reading for the shift size (the paper leaves it open): Q += (|lmin| + 1e-12 lmax) I.
+
+Patterns (Sec. 5.1: S(M^k)):
+  'diag'  S(1): q_l = M_ll / sum_k M_kl^2
+  'sm1'   S(M1): DoF pairs that share a tetrahedron (the structural pattern of M1)
+  'sm1sq' S(M1^2): pairs joined by a path of two such steps
+Pins: tests/test_oracle_spai.py (brute-force least squares on the full matrix,
+the S(1) closed form, the printed SPAI dispersion numbers of Table dispersionTable).
+"""
+import numpy as np
+import scipy.sparse as sp
+
+
+def structural_pattern(dof_map, n):
+    """Boolean CSR of DoF pairs (i, j) that appear together in some row of dof_map (per-tet DoFs)."""
+    T, m = dof_map.shape
+    R = np.repeat(dof_map[:, :, None], m, axis=2)
+    C = np.repeat(dof_map[:, None, :], m, axis=1)
+    ok = (R >= 0) & (C >= 0)
+    S = sp.csr_matrix((np.ones(ok.sum()), (R[ok], C[ok])), shape=(n, n))
+    S.data[:] = 1.0
+    return S
+
+
+def pattern(kind, M, dof_map=None):
+    n = M.shape[0]
+    if kind == "diag":
+        return sp.identity(n, format="csr")
+    if kind == "sm1":
+        return structural_pattern(dof_map, n) if dof_map is not None else (abs(M) > 0).astype(float).tocsr()
+    if kind == "sm1sq":
+        S = pattern("sm1", M, dof_map)
+        S2 = (S @ S).tocsr()
+        S2.data[:] = 1.0
+        return S2
+    raise ValueError(kind)
+
+
+def spai_columns(M, S):
+    """Unsymmetrised column-wise SPAI of Eq. NormalEqSolve on pattern S (both sparse, n x n)."""
+    M = sp.csc_matrix(M)
+    S = sp.csc_matrix(S)
+    n = M.shape[0]
+    rows, cols, vals = [], [], []
+    for l in range(n):
+        I = S.indices[S.indptr[l]:S.indptr[l + 1]]
+        A = M[:, I]                                   # n x |I|, sparse
+        J = np.unique(A.indices)
+        Ad = A[J, :].toarray()                        # the nonzero rows
+        rhs = np.zeros(len(J))
+        pos = np.searchsorted(J, l)
+        if pos < len(J) and J[pos] == l:
+            rhs[pos] = 1.0
+        q = np.linalg.solve(Ad.T @ Ad, Ad.T @ rhs)
+        rows.append(I)
+        cols.append(np.full(len(I), l))
+        vals.append(q)
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+
+
+def symmetrize(Q):
+    return ((Q + Q.T) * 0.5).tocsr()
+
+
+def spd_shift(Q, dense_limit=4000):
+    """Smallest / largest eigenvalue of symmetric Q, and Q shifted to SPD if needed."""
+    n = Q.shape[0]
+    if n <= dense_limit:
+        w = np.linalg.eigvalsh(Q.toarray())
+        lmin, lmax = w[0], w[-1]
+    else:
+        import scipy.sparse.linalg as spl
+        lmax = spl.eigsh(Q, k=1, which="LA", return_eigenvectors=False)[0]
+        lmin = spl.eigsh(Q, k=1, which="SA", return_eigenvectors=False)[0]
+    shift = 0.0
+    if lmin <= 0:
+        shift = abs(lmin) + 1e-12 * lmax
+        Q = (Q + shift * sp.identity(n)).tocsr()
+    return Q, lmin, lmax, shift
+
+
+def spai(M, kind="sm1", dof_map=None):
+    """Symmetric SPD SPAI Q1 ~ M^-1 (Sec. 5): columns, symmetrise, SPD check."""
+    S = pattern(kind, M, dof_map)
+    Q = symmetrize(spai_columns(M, S))
+    Q, lmin, lmax, shift = spd_shift(Q)
+    return Q, dict(lmin=lmin, lmax=lmax, shift=shift, nnz=Q.nnz)
+
+
+# ----------------------------------------------------------------------------
+# SPAI in a hierarchically orthogonalised basis (reading for orders k >= 2)
+#
+# SPAI is not invariant under a change of basis (Sec. 5: the column problems
+# depend on the basis through M).  For k >= 2 the integer-curl hierarchical
+# basis gives an ill-conditioned M1 and an indefinite symmetrised SPAI.  The
+# SPAI is then computed in the basis Lambda' = T Lambda, where T only adds
+# functions of sub-entities (the edges of a face; the edges and faces of a
+# tet) to higher-entity functions and normalises inside each entity:
+#   1. face DoFs F:  Lambda'_F = Lambda_F - c^T Lambda_E,  M1[E,E] c = M1[E,F]
+#      (E = interior DoFs of the face's three edges)
+#   2. cell DoFs Z:  Lambda'_Z = Lambda_Z - c^T Lambda_J,  M1[J,J] c = M1[J,Z]
+#      (J = interior edge and face DoFs of the tet, original basis)
+#   3. per entity group g: Lambda''_g = (M'[g,g])^(-1/2) Lambda'_g  (M' = T12 M1 T12^T)
+# and mapped back as Q1 = T^T Q'' T.  Because every tet that contains an entity
+# contains its sub-entities, Q1 keeps the pattern of Q'' (S(M1) or S(M1^2)), and
+# Q1 is SPD exactly when Q'' is.  The GYM with (Q1, integer C) is the GYM of the
+# basis Lambda'' with (Q'', C T^T): the same trajectory for b and E.
+# ----------------------------------------------------------------------------
+
+def entity_groups(fem):
+    """Lists of global 1-form DoFs per entity: edges, faces, cells (each a tuple)."""
+    k = fem.mesh.k
+    per_f = k * (k - 1)
+    d1 = fem.dof1
+    edges, faces, cells = {}, {}, {}
+    for t in range(d1.shape[0]):
+        d = d1[t]
+        for le in range(6):
+            g = tuple(int(x) for x in d[le * k:(le + 1) * k] if x >= 0)
+            if g:
+                edges[g[0]] = g
+        for lf in range(4):
+            g = tuple(int(x) for x in d[6 * k + lf * per_f:6 * k + (lf + 1) * per_f] if x >= 0)
+            if g:
+                faces[g[0]] = g
+        if k >= 3:
+            g = tuple(int(x) for x in d[6 * k + 4 * per_f:])
+            cells[g[0]] = g
+    return list(edges.values()), list(faces.values()), list(cells.values())
+
+
+def ortho_basis_transform(fem, M1):
+    """The matrix T of steps 1-3 above (sparse, N1 x N1)."""
+    from .mesh import LOCAL_EDGES, LOCAL_FACES
+    mesh = fem.mesh
+    k = mesh.k
+    per_f = k * (k - 1)
+    M = sp.csr_matrix(M1)
+    N1 = mesh.N1
+    T = sp.lil_matrix((N1, N1))
+    T.setdiag(1.0)
+    done_f, done_c = set(), set()
+    d1 = fem.dof1
+    for t in range(d1.shape[0]):
+        d = d1[t]
+        for lf, (a, b, c) in enumerate(LOCAL_FACES):
+            F = [int(x) for x in d[6 * k + lf * per_f:6 * k + (lf + 1) * per_f] if x >= 0]
+            if not F or F[0] in done_f:
+                continue
+            done_f.add(F[0])
+            E = []
+            for le, (p, q) in enumerate(LOCAL_EDGES):
+                if p in (a, b, c) and q in (a, b, c):
+                    E += [int(x) for x in d[le * k:(le + 1) * k] if x >= 0]
+            if E:
+                cE = np.linalg.solve(M[E][:, E].toarray(), M[E][:, F].toarray())
+                for jj, x in enumerate(F):
+                    for ii, y in enumerate(E):
+                        T[x, y] = -cE[ii, jj]
+        if k >= 3:
+            Z = [int(x) for x in d[6 * k + 4 * per_f:]]
+            if Z[0] in done_c:
+                continue
+            done_c.add(Z[0])
+            J = [int(x) for x in d[:6 * k + 4 * per_f] if x >= 0]
+            cJ = np.linalg.solve(M[J][:, J].toarray(), M[J][:, Z].toarray())
+            for jj, x in enumerate(Z):
+                for ii, y in enumerate(J):
+                    T[x, y] = -cJ[ii, jj]
+    T = T.tocsr()
+    Mp = (T @ M @ T.T).tocsr()
+    edges, faces, cells = entity_groups(fem)
+    r, c, v = [], [], []
+    for g in edges + faces + cells:
+        g = list(g)
+        w, V = np.linalg.eigh(Mp[g][:, g].toarray())
+        Lg = (V / np.sqrt(w)) @ V.T
+        for ii, x in enumerate(g):
+            for jj, y in enumerate(g):
+                r.append(x)
+                c.append(y)
+                v.append(Lg[ii, jj])
+    L = sp.csr_matrix((v, (r, c)), shape=(N1, N1))
+    return (L @ T).tocsr()
+
+
+def default_policy(order):
+    """(pattern, basis) used for each order: k = 1 S(M1) in the Whitney basis; k >= 2 S(M1^2), orthogonalised."""
+    return ("sm1", "plain") if order == 1 else ("sm1sq", "ortho")
+
+
+def gym_q1(fem, M1=None, pattern_kind=None, basis_kind=None):
+    """Q1 for the GYM of this mesh: SPAI (Eq. NormalEqSolve), symmetrised, SPD-checked."""
+    M1 = fem.M1() if M1 is None else M1
+    dp, db = default_policy(fem.mesh.k)
+    pattern_kind = pattern_kind or dp
+    basis_kind = basis_kind or db
+    S = pattern(pattern_kind, M1, fem.dof1)
+    if basis_kind == "plain":
+        Q = symmetrize(spai_columns(M1, S))
+    elif basis_kind == "ortho":
+        T = ortho_basis_transform(fem, M1)
+        Mp = (T @ M1 @ T.T).tocsr()
+        Q = (T.T @ symmetrize(spai_columns(Mp, S)) @ T).tocsr()
+        Q = symmetrize(Q)
+    else:
+        raise ValueError(basis_kind)
+    Q, lmin, lmax, shift = spd_shift(Q)
+    return Q, dict(lmin=lmin, lmax=lmax, shift=shift, nnz=Q.nnz, pattern=pattern_kind, basis=basis_kind)

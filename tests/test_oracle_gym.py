@@ -1,0 +1,167 @@
+"""Pins of the oracle's time stepping: Theorem symplecticity, Eq. eigenvaluePairs, Prop. stability,
+the exactly conserved discrete energy, Gauss' law, the (a, e) / (b, e) equivalence and the
+source work identity."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import synth
+from oracle import spai as SP
+from oracle.fem import FEM
+from oracle.gym import GYM, DipoleSource
+from oracle.mesh import KuhnMesh
+
+
+def _setup(n, k, seed=21, eps_range=(1, 4)):
+    f = FEM(KuhnMesh(n, k), eps=synth.tet_eps(seed, n, *eps_range))
+    M1 = f.M1()
+    Q, _ = SP.gym_q1(f, M1)
+    return f, GYM(f.C(), f.M2(), Q, M1)
+
+
+@pytest.mark.parametrize("n,k", [(2, 1), (2, 2)])
+def test_strang_map_is_symplectic(n, k):
+    f, g = _setup(n, k)
+    tau = 0.5 * g.tau_cfl()
+    J = g.strang_jacobian(tau)
+    N = f.mesh.N1
+    Om = np.block([[np.zeros((N, N)), np.eye(N)], [-np.eye(N), np.zeros((N, N))]])
+    assert abs(J.T @ Om @ J - Om).max() < 1e-12 * max(1.0, abs(J).max() ** 2)
+
+
+def test_symplectic_even_for_indefinite_symmetric_q1():
+    f, g = _setup(2, 1)
+    Q = g.Q1.toarray()
+    Q = Q - 1.5 * np.linalg.eigvalsh(Q)[-1] * np.eye(Q.shape[0]) * 0.5
+    g2 = GYM(f.C(), f.M2(), sp.csr_matrix(Q))
+    J = g2.strang_jacobian(0.01)
+    N = f.mesh.N1
+    Om = np.block([[np.zeros((N, N)), np.eye(N)], [-np.eye(N), np.zeros((N, N))]])
+    assert abs(J.T @ Om @ J - Om).max() < 1e-11 * abs(J).max() ** 2
+
+
+def test_eigenvalues_of_one_step_map_follow_the_2x2_blocks():
+    """eig(J) = 1 - z/2 +- sqrt(z(z-4))/2 with z = tau^2 w^2, w^2 in eig(Q1 P2)."""
+    f, g = _setup(2, 1)
+    tau = 0.7 * g.tau_cfl()
+    lam = np.linalg.eigvals(g.strang_jacobian(tau))
+    w2 = np.linalg.eigvals(g.Q1.toarray() @ g.P2.toarray()).real
+    z = tau ** 2 * np.clip(w2, 0, None)
+    pred = np.concatenate([1 - z / 2 + 0.5 * np.sqrt(z * (z - 4) + 0j), 1 - z / 2 - 0.5 * np.sqrt(z * (z - 4) + 0j)])
+    key = lambda x: (np.round(x.real, 8), np.round(abs(x.imag), 8))
+    assert np.allclose(sorted(lam, key=key), sorted(pred, key=key), atol=1e-8)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_cfl_bound_separates_stable_and_unstable(k):
+    f, g = _setup(2, k)
+    tc = g.tau_cfl()
+    lam_s = np.linalg.eigvals(g.strang_jacobian(0.9 * tc))
+    # gradient fields (omega = 0) form Jordan blocks at lambda = 1 whose computed eigenvalues
+    # carry sqrt(machine epsilon) noise; every other eigenvalue sits on the unit circle
+    osc = np.abs(lam_s - 1) > 1e-6
+    assert abs(np.abs(lam_s[osc]) - 1).max() < 1e-10
+    assert abs(np.abs(lam_s) - 1).max() < 1e-7
+    lam_u = np.linalg.eigvals(g.strang_jacobian(1.1 * tc))
+    big = lam_u[np.abs(lam_u) > 1 + 1e-6]
+    assert len(big) > 0 and np.all(abs(big.imag) < 1e-8)          # leave along the real axis
+    for x in big:                                                   # reciprocal partners
+        assert np.min(np.abs(lam_u - 1 / x)) < 1e-6
+
+
+def test_time_domain_growth_beyond_cfl_and_for_indefinite_q1():
+    f, g = _setup(2, 1)
+    tc = g.tau_cfl()
+    rng = np.random.default_rng(0)
+    e0 = rng.standard_normal(f.mesh.N1)
+    e, b, _ = g.run(e0, g.half_init(e0, np.zeros(f.mesh.N2), 1.1 * tc), 1.1 * tc, 400)
+    assert np.linalg.norm(e) > 1e3 * np.linalg.norm(e0)
+    e, b, _ = g.run(e0, g.half_init(e0, np.zeros(f.mesh.N2), 0.9 * tc), 0.9 * tc, 400)
+    assert np.linalg.norm(e) < 1e2 * np.linalg.norm(e0)
+    Q = g.Q1.toarray()
+    wp, Vp = np.linalg.eigh(g.P2.toarray())
+    u = Vp[:, -1]                                                   # a curl-carrying direction
+    Q_ind = Q - 2.0 * (u @ Q @ u) * np.outer(u, u)                 # u^T Q_ind u < 0
+    g2 = GYM(f.C(), f.M2(), sp.csr_matrix(Q_ind))
+    w2 = np.linalg.eigvals(Q_ind @ g.P2.toarray()).real
+    assert w2.min() < 0
+    tau = 0.05 * tc
+    e, b, _ = g2.run(e0, g2.half_init(e0, np.zeros(f.mesh.N2), tau), tau, 4000)
+    assert np.linalg.norm(e) > 1e3 * np.linalg.norm(e0)
+
+
+def test_discrete_energy_conserved_config1_like():
+    """N=4, k=1, TE(1,1,0) mode E = z sin(pi x) sin(pi y), dt = 0.5 tau_CFL, 1000 steps."""
+    f = FEM(KuhnMesh(4, 1))
+    M1 = f.M1()
+    Q, _ = SP.gym_q1(f, M1)
+    g = GYM(f.C(), f.M2(), Q, M1)
+    E0 = lambda x: np.stack([0 * x[:, 0], 0 * x[:, 0], np.sin(np.pi * x[:, 0]) * np.sin(np.pi * x[:, 1])], axis=1)
+    e0 = M1 @ f.edge_interpolant(E0)
+    tau = 0.5 * g.tau_cfl()
+    b = g.half_init(e0, np.zeros(f.mesh.N2), tau)
+    W0 = g.W(e0, b, tau)
+    e, b, W = g.run(e0, b, tau, 1000, energy_every=1)
+    drift = np.max(np.abs(np.array(W) - W0)) / W0
+    assert drift < 1e-13
+    # the paper's H~ oscillates boundedly (Sec. 7.5)
+    H = [g.H_tilde(e0, np.zeros(f.mesh.N2))]
+    e2, b2 = e0.copy(), g.half_init(e0, np.zeros(f.mesh.N2), tau)
+    for n in range(200):
+        e2, b2, _, _ = g.step(e2, b2, tau)
+        H.append(g.H_tilde(e2, g.sync(e2, b2, tau)))
+    H = np.array(H)
+    assert np.max(np.abs(H - H[0])) / H[0] < 0.05
+
+
+@pytest.mark.parametrize("n,k", [(3, 1), (2, 2)])
+def test_gauss_law_and_divergence_free_b(n, k):
+    f, g = _setup(n, k)
+    G, D = f.G(), f.D()
+    rng = np.random.default_rng(5)
+    e0 = rng.standard_normal(f.mesh.N1)
+    tau = 0.5 * g.tau_cfl()
+    b = g.half_init(e0, np.zeros(f.mesh.N2), tau)
+    e, b, _ = g.run(e0, b, tau, 300)
+    assert abs(G.T @ e - G.T @ e0).max() < 1e-11 * abs(e0).max()
+    assert abs(D @ b).max() < 1e-11 * abs(b).max()
+
+
+def test_leapfrog_equals_strang_in_a_e_variables():
+    """(b, e) leapfrog with half steps equals Phi_tau (Eq. strangSplit) on (a, e) with b = C a."""
+    f, g = _setup(2, 2)
+    rng = np.random.default_rng(8)
+    a0 = rng.standard_normal(f.mesh.N1)
+    e0 = rng.standard_normal(f.mesh.N1)
+    tau = 0.4 * g.tau_cfl()
+    a, e = a0.copy(), e0.copy()
+    for _ in range(25):
+        a, e = g.strang(a, e, tau)
+    b = g.half_init(e0, g.C @ a0, tau)
+    e2, b2, _ = g.run(e0.copy(), b, tau, 25)
+    assert np.allclose(e2, e, rtol=1e-12, atol=1e-12 * abs(e).max())
+    assert np.allclose(g.sync(e2, b2, tau), g.C @ a, rtol=1e-11, atol=1e-11 * abs(g.C @ a).max())
+
+
+def test_source_work_identity_and_linearity():
+    """W_{n+1} - W_n = -tau (e_n + e_{n+1})^T Q1 j_{n+1/2} / 2, and the response is linear in s."""
+    f, g = _setup(3, 2, seed=31)
+    tau = 0.5 * g.tau_cfl()
+    src = [dict(x=np.array([0.41, 0.52, 0.47]), d=np.array([0.0, 0.0, 1.0]), amp=1.0,
+                omega=np.pi * np.sqrt(5.0), width_steps=5.0)]
+    J = DipoleSource(f, src, tau)
+    e = np.zeros(f.mesh.N1)
+    b = np.zeros(f.mesh.N2)
+    res = []
+    for n in range(60):
+        j = J((n + 0.5) * tau)
+        W0 = g.W(e, b, tau)
+        e1, b1, _, _ = g.step(e, b, tau, j)
+        W1 = g.W(e1, b1, tau)
+        work = -tau * 0.5 * (e + e1) @ (g.Q1 @ j)
+        res.append(abs(W1 - W0 - work) / max(abs(W1), 1e-300))
+        e, b = e1, b1
+    assert np.linalg.norm(e) > 0 and max(res) < 1e-10
+    J2 = DipoleSource(f, [dict(src[0], amp=2.0)], tau)
+    e2, b2, _ = g.run(np.zeros(f.mesh.N1), np.zeros(f.mesh.N2), tau, 60, source=J2)
+    assert np.allclose(e2, 2 * e, rtol=1e-12, atol=1e-14)

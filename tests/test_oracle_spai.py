@@ -1,0 +1,122 @@
+"""Pins of the oracle's SPAI (Sec. 5, Eq. NormalEqSolve) against brute force, closed forms and
+the frequencies printed in Table dispersionTable."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import synth
+from oracle import spai as SP
+from oracle.cubical2d import Torus2D, zero_crossing_frequency
+from oracle.fem import FEM
+from oracle.gym import GYM
+from oracle.mesh import KuhnMesh
+
+
+def test_diagonal_spai_closed_form():
+    f = FEM(KuhnMesh(3, 2), eps=synth.tet_eps(11, 3, 1, 4))
+    M = f.M1()
+    Q = SP.spai_columns(M, SP.pattern("diag", M)).diagonal()
+    Md = M.toarray()
+    assert np.allclose(Q, np.diag(Md) / np.sum(Md ** 2, axis=0), rtol=1e-13)
+
+
+@pytest.mark.parametrize("n,k,kind", [(3, 1, "sm1"), (2, 2, "sm1"), (2, 2, "sm1sq")])
+def test_columns_solve_the_least_squares_problem(n, k, kind):
+    """Each column minimises ||M q - 1_l|| over its pattern: compare with dense lstsq on all rows."""
+    f = FEM(KuhnMesh(n, k), eps=synth.tet_eps(12, n, 1, 4))
+    M = f.M1()
+    S = SP.pattern(kind, M, f.dof1)
+    Q = SP.spai_columns(M, S).toarray()
+    Md = M.toarray()
+    Sc = S.tocsc()
+    rng = np.random.default_rng(0)
+    for l in rng.choice(M.shape[0], size=6, replace=False):
+        I = Sc.indices[Sc.indptr[l]:Sc.indptr[l + 1]]
+        rhs = np.zeros(M.shape[0])
+        rhs[l] = 1.0
+        q, *_ = np.linalg.lstsq(Md[:, I], rhs, rcond=None)
+        assert np.allclose(Q[I, l], q, rtol=1e-8, atol=1e-10 * abs(q).max())
+        assert np.count_nonzero(Q[:, l]) <= len(I)
+
+
+def test_structural_pattern_is_tet_sharing():
+    f = FEM(KuhnMesh(2, 1))
+    S = SP.pattern("sm1", f.M1(), f.dof1).toarray() > 0
+    ref = np.zeros_like(S)
+    for d in f.dof1:
+        d = d[d >= 0]
+        ref[np.ix_(d, d)] = True
+    assert np.array_equal(S, ref)
+
+
+@pytest.mark.parametrize("n,k", [(4, 1), (3, 2), (2, 3)])
+def test_default_policy_gives_spd_without_shift(n, k):
+    f = FEM(KuhnMesh(n, k), eps=synth.tet_eps(13, n, 1, 4))
+    Q, info = SP.gym_q1(f)
+    assert info["shift"] == 0.0 and info["lmin"] > 0
+    assert abs(Q - Q.T).max() < 1e-12 * abs(Q).max()
+    # the pattern of Q1 stays inside the requested structural pattern
+    S = SP.pattern(info["pattern"], f.M1(), f.dof1)
+    assert ((abs(Q) > 0).astype(int) - (S > 0).astype(int)).max() <= 0
+
+
+def test_ortho_basis_keeps_the_dynamics_and_pattern():
+    """Q1 = T^T Q'' T: the GYM of basis Lambda'' in integer-C variables; check against the
+    primed-basis GYM built directly (same P2 spectrum) on a tiny mesh."""
+    f = FEM(KuhnMesh(2, 2), eps=synth.tet_eps(14, 2, 1, 4))
+    M1 = f.M1()
+    T = SP.ortho_basis_transform(f, M1).toarray()
+    Mp = T @ M1.toarray() @ T.T
+    # T is sub-entity triangular: every face/cell row only touches its own sub-entities
+    Sm = SP.pattern("sm1", M1, f.dof1).toarray() > 0
+    assert np.all((np.abs(T) > 0) <= Sm)
+    # exact inverse is basis independent: T^T (T M T^T)^-1 T = M^-1
+    assert np.allclose(T.T @ np.linalg.inv(Mp) @ T, np.linalg.inv(M1.toarray()), rtol=1e-8, atol=1e-10)
+    # the primed mass matrix is normalised inside each entity
+    for g in sum(SP.entity_groups(f), []):
+        g = list(g)
+        assert np.allclose(Mp[np.ix_(g, g)], np.eye(len(g)), atol=1e-10)
+
+
+# ---------------------------------------------------------------- Table dispersionTable
+def _dispersion(kind):
+    t = Torus2D(20, 20)
+    M1, C, M2 = t.M1(), t.C(), t.M2()
+    if kind == "exact":
+        Q = sp.csr_matrix(np.linalg.inv(M1.toarray()))
+    else:
+        Q, _ = SP.spai(M1, kind)
+    g = GYM(C, M2, Q)
+    a = t.mode_sin_y()
+    omega_space = np.sqrt((a @ (Q @ (g.P2 @ a))) / (a @ a))
+    # time domain: the lowest exact eigenmode v of M1^-1 P2 (here e = M1 a), CFL factor 0.3,
+    # 200 periods, zero crossings of <e(t), e(0)>
+    v = M1 @ a
+    v /= np.linalg.norm(v)
+    tau = 0.3 * g.tau_cfl()
+    n = int(200 * 2 * np.pi / omega_space / tau)
+    e, b = v.copy(), g.half_init(v, np.zeros(t.N2), tau)
+    proj = [v @ v]
+    for _ in range(n):
+        e, b, _, _ = g.step(e, b, tau)
+        proj.append(e @ v)
+    return omega_space, zero_crossing_frequency(np.array(proj), tau), t.hx
+
+
+def test_dispersion_exact_feec():
+    w, wt, h = _dispersion("exact")
+    assert np.isclose(w, np.sqrt(6 / h ** 2 * (1 - np.cos(h)) / (2 + np.cos(h))), rtol=1e-12)
+    assert abs(w / 1.0041 - 1) < 1e-4 and abs(wt / 1.0041 - 1) < 3e-4
+
+
+def test_dispersion_diagonal_spai_matches_yee_row():
+    w, wt, h = _dispersion("diag")
+    assert np.isclose(w, np.sqrt(4.0 / 3.0) * 2 / h * np.sin(h / 2), rtol=1e-12)
+    assert abs(w / 1.1499 - 1) < 1e-4 and abs(wt / 1.1499 - 1) < 3e-4
+    assert abs((w - 1.0041) / 1.0041 - 0.145) < 5e-4          # printed +14.5 %
+
+
+def test_dispersion_spai_sm1_matches_printed_value():
+    w, wt, h = _dispersion("sm1")
+    assert abs(wt / 0.9634 - 1) < 3e-4 and abs(w / 0.9634 - 1) < 3e-4
+    assert abs((wt - 1.0041) / 1.0041 + 0.041) < 5e-4         # printed -4.1 %
