@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Benchmark of the GYM leapfrog on GB300: field DoF-updates/s.
+
+Workload (default): PEC cube, N = 32 cubes per side split into Kuhn tets (196,608 tets), order
+k = 2, per-tet permittivity i.i.d. U[1,4) (seed 2000), mu = 1, one Gaussian-modulated z-dipole
+(centre frequency pi sqrt 5, width 20 steps) at a point U[0.2,0.8)^3 (seed 2001), dt = 0.5 tau_CFL,
+2000 leapfrog steps per run, FP32 fields.  One benchmark step is one whole 2000-step run from the
+zero state; value = (N1 + N2) * 2000 / run time, summed over ranks (independent replicas).
+
+Run:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "field DoF-updates/s on 1 GB300 (FP32/batched vs FP64) at stated L2 error/energy drift"
+UNIT = "DoF-updates/s"
+
+
+def workload(n=32, k=2, leapfrog_steps=2000):
+    x0 = synth.source_positions(2001, 1)[0]
+    return dict(n=n, k=k, eps=synth.tet_eps(2000, n, 1.0, 4.0), x0=x0, d=np.array([0.0, 0.0, 1.0]),
+                omega=np.pi * np.sqrt(5.0), width=20.0, steps=leapfrog_steps)
+
+
+def source_for(W, dt):
+    sigma = W["width"] * dt
+    return [dict(x=W["x0"], d=W["d"], amp=1.0, omega=W["omega"], t0=4 * sigma, sigma=sigma, rhs=0)]
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            P = json.load(f)
+        return float(P["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+def oracle_sample(steps=2000, n=4):
+    """The FP64 CPU oracle as it stands, on a bounded sample of the workload: the same recipe on an
+    n^3 cube (eps seed 2000, same source), `steps` leapfrog steps; returns DoF-updates/s."""
+    from oracle import spai as SP
+    from oracle.fem import FEM
+    from oracle.gym import GYM, DipoleSource
+    from oracle.mesh import KuhnMesh
+    W = workload(n=n, k=2, leapfrog_steps=steps)
+    f = FEM(KuhnMesh(n, 2), eps=W["eps"])
+    M1 = f.M1()
+    Q, _ = SP.gym_q1(f, M1)
+    g = GYM(f.C(), f.M2(), Q, M1)
+    dt = 0.5 * g.tau_cfl()
+    src = [dict(x=W["x0"], d=W["d"], amp=1.0, omega=W["omega"], width_steps=W["width"])]
+    J = DipoleSource(f, src, dt)
+    e = np.zeros(f.mesh.N1)
+    b = np.zeros(f.mesh.N2)
+    t0 = time.perf_counter()
+    g.run(e, b, dt, steps, source=J)
+    el = time.perf_counter() - t0
+    units = (f.mesh.N1 + f.mesh.N2) * steps
+    return units / el, el, dict(n=n, k=2, N1=f.mesh.N1, N2=f.mesh.N2, steps=steps)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, el, info = oracle_sample()
+        if i >= args.warmup:
+            vals.append((v, el))
+    value = float(np.mean([v for v, _ in vals]))
+    ms = float(np.mean([el for _, el in vals]) * 1e3)
+    sample = (f"FP64 CPU oracle (scipy sparse, single thread), same recipe on a {info['n']}^3 cube, k=2 "
+              f"(N1={info['N1']}, N2={info['N2']}), {info['steps']} leapfrog steps per step")
+    line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic",
+                config=dict(workload="PEC cube N=32, k=2, eps~U[1,4) seed 2000, z-dipole, 2000 steps "
+                                     "(oracle timed on a bounded N=4 sample)"),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=1, kind="oracle", sample=sample),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2301_01753_gb300 as Y
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    W = workload(n=args.n, k=args.order, leapfrog_steps=args.leapfrog_steps)
+    stream = torch.cuda.current_stream()
+    prec = Y.YGM_FP32 if args.precision == "fp32" else Y.YGM_FP64
+    tb = time.perf_counter()
+    ctx = Y.Context(W["n"], W["k"], eps=W["eps"], precision=prec, device=local_rank, stream=stream.cuda_stream)
+    setup_s = time.perf_counter() - tb
+    dt = 0.5 * ctx.tau_cfl
+    src = source_for(W, dt)
+    tdt = torch.float32 if prec == Y.YGM_FP32 else torch.float64
+    ze = torch.zeros(ctx.N1, dtype=tdt, device="cuda")
+    zb = torch.zeros(ctx.N2, dtype=tdt, device="cuda")
+    units = (ctx.N1 + ctx.N2) * W["steps"]
+
+    def one_run():
+        ctx.set_state(ze, zb)
+        ctx.step(W["steps"], dt, src)
+
+    for _ in range(args.warmup):
+        one_run()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ctx.kernel_timing(True)
+    ctx.kernel_times()
+    l0 = ctx.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            one_run()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    launches = ctx.launch_count() - l0
+    kt = ctx.kernel_times()
+    ctx.kernel_timing(False)
+    ms = ms_total / args.steps
+    t_max = ms_total
+    if dist:
+        tt = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * units * args.steps / (t_max * 1e-3)
+
+    # end to end through the public API with host buffers (pinned): H2D state in, D2H state out
+    he = torch.zeros(ctx.N1, dtype=tdt).pin_memory().numpy()
+    hb = torch.zeros(ctx.N2, dtype=tdt).pin_memory().numpy()
+    oe = torch.empty(ctx.N1, dtype=tdt).pin_memory().numpy()
+    ob = torch.empty(ctx.N2, dtype=tdt).pin_memory().numpy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.set_state(he, hb)
+        ctx.step(W["steps"], dt, src)
+        ctx.get_state(synced=True, out_e=oe, out_b=ob)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_val = units / e2e_s
+    if dist:
+        tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_val = world * units / float(tt.item())
+    rs = 4 if prec == Y.YGM_FP32 else 8
+
+    # roofline of the dominant kernel (Q1 apply): algorithmic bytes = unique symmetric Q1 values
+    # + e read + x write
+    qms, qn = kt["k_qapply"]
+    q_unique = (ctx.q1_nnz + ctx.N1) // 2
+    alg_bytes = rs * (q_unique + 2 * ctx.N1)
+    q_avg_s = (qms / max(qn, 1)) * 1e-3
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / q_avg_s / 1e9
+    step_kernels = {k: dict(ms_per_launch=(v[0] / v[1] if v[1] else None), launches=v[1]) for k, v in kt.items()}
+
+    # accuracy at the stated configuration: FP32 vs the FP64 GPU path (same operators, one run),
+    # and the discrete energy drift after the pulse has passed
+    acc = None
+    if rank == 0 and not args.no_accuracy:
+        e32, b32 = ctx.get_state(synced=True)
+        ref = Y.Context(W["n"], W["k"], eps=W["eps"], precision=Y.YGM_FP64, device=local_rank,
+                        energy_every=100, stream=stream.cuda_stream)
+        ref.set_state(np.zeros(ref.N1), np.zeros(ref.N2))
+        torch.cuda.synchronize()
+        t64 = time.perf_counter()
+        ref.step(W["steps"], dt, src)
+        e64, b64 = ref.get_state(synced=True)
+        t64 = time.perf_counter() - t64
+        Wh = ref.energy_history()
+        ctx32 = Y.Context(W["n"], W["k"], eps=W["eps"], precision=Y.YGM_FP32, device=local_rank, energy_every=100,
+                          stream=stream.cuda_stream) if prec == Y.YGM_FP32 else None
+        drift32 = None
+        if ctx32 is not None:
+            ctx32.set_state(np.zeros(ctx32.N1, np.float32), np.zeros(ctx32.N2, np.float32))
+            ctx32.step(W["steps"], dt, src)
+            W32 = ctx32.energy_history()
+            drift32 = float(np.max(np.abs(W32[3:] - W32[3])) / W32[3])
+            ctx32.close()
+        acc = dict(rel_l2_e_vs_fp64_gpu=float(np.linalg.norm(e32 - e64) / np.linalg.norm(e64)),
+                   rel_l2_b_vs_fp64_gpu=float(np.linalg.norm(b32 - b64) / np.linalg.norm(b64)),
+                   energy_drift_fp64_after_pulse=float(np.max(np.abs(Wh[3:] - Wh[3])) / Wh[3]),
+                   energy_drift_fp32_after_pulse=drift32,
+                   fp64_gpu_value=units / t64, fp64_gpu_ms_per_run=t64 * 1e3)
+        ref.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, el, info = oracle_sample(steps=args.cpu_steps)
+        cpu = dict(value=v, unit=UNIT, cores=1, kind="oracle",
+                   sample=(f"FP64 oracle, same recipe on a {info['n']}^3 cube (N1={info['N1']}, N2={info['N2']}), "
+                           f"{info['steps']} steps, {el:.1f} s"))
+    if rank == 0:
+        line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                    ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None,
+                    dtype="f32" if prec == Y.YGM_FP32 else "f64", data="synthetic",
+                    config=dict(workload=f"PEC cube N={W['n']} (6N^3={6 * W['n'] ** 3} Kuhn tets), k={W['k']}, "
+                                         f"eps~U[1,4) seed 2000, z-dipole seed 2001, dt=0.5 tau_CFL, "
+                                         f"{W['steps']} leapfrog steps per step",
+                                N1=ctx.N1, N2=ctx.N2, dofs=ctx.N1 + ctx.N2, leapfrog_steps=W["steps"],
+                                q1_nnz=ctx.q1_nnz, q1=ctx.q1_info(), dt=dt, setup_s=setup_s,
+                                parallelism=f"replicas{world}" if world > 1 else "single",
+                                l2_policy="inputs larger than L2 (Q1 %.0f MB > 129 MB L2)" % (rs * q_unique / 1e6)),
+                    e2e=dict(value=e2e_val, unit=UNIT, h2d_bytes_per_step=rs * (ctx.N1 + ctx.N2),
+                             d2h_bytes_per_step=rs * (ctx.N1 + ctx.N2)),
+                    gpu_launches=launches,
+                    roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
+                                  traffic=None, kernel="k_qapply", bytes_per_launch=alg_bytes,
+                                  peak_source=f"{peak_kind} hbm_gbs"),
+                    kernels=step_kernels, clocks=clk.summary(), accuracy=acc, cpu_baseline=cpu)
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--n", type=int, default=32)
+    ap.add_argument("--order", type=int, default=2)
+    ap.add_argument("--leapfrog-steps", type=int, default=2000)
+    ap.add_argument("--cpu-steps", type=int, default=2000)
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,180 @@
+/*
+ * ygm.h -- C ABI of the GB300 (sm_103a) generalized Yee method (GYM) leapfrog library.
+ *
+ * The method (Glasser & Qin, "Generalized Yee methods"): Maxwell's equations on a
+ * de Rham-conforming finite element complex, with the Hamiltonian
+ *     H~ = 1/2 e^T Q1 e + 1/2 a^T C^T M2 C a            (Eq. discTildeHamilSystem)
+ * where Q1 ~ M1^-1 is a sparse SPD approximate inverse (Sec. 5, Eq. NormalEqSolve)
+ * and C is the integer curl of the complex (Eq. discreteDeRham).  Time stepping is the
+ * Strang composition of the two exact shear maps (Eqs. shearMaps, strangSplit), run in
+ * the staggered (b, e) form of Eq. preYeeFEECEqns / Eq. YeeLeapfrog:
+ *     x         = Q1 e_n
+ *     b_{n+1/2} = b_{n-1/2} - dt C x
+ *     e_{n+1}   = e_n + dt (C^T M2 b_{n+1/2} - j_{n+1/2})
+ * Units: eps0 = mu0 = c = 1.
+ *
+ * Domain: the PEC cube [0, side]^3 cut into n^3 cubes, each split into the 6 Kuhn
+ * tetrahedra; tet index t = 6 (cx + n (cy + n cz)) + shape, shape in order of the vertex
+ * chains (x,xy), (x,xz), (y,xy), (y,yz), (z,xz), (z,yz).  Order k = 1, 2, 3: trimmed
+ * P_k^- Lambda^1 / P_k^- Lambda^2 in a hierarchical exact-sequence basis whose C, G, D
+ * have entries in {0, +-1}.
+ *
+ * DoF layout (e, b, and every vector crossing this ABI): DoFs are grouped in classes
+ * (entity shape, DoF index inside the entity); classes are ordered edges (7 shapes,
+ * offsets x, y, xy, z, xz, yz, xyz), faces (12 shapes), tets (6 shapes), each shape with
+ * its k (edge), k(k-1) (face), k(k-1)(k-2)/2 (tet) 1-form DoFs, or k(k+1)/2 (face),
+ * (k-1)k(k+1)/2 (tet) 2-form DoFs.  Inside a class the anchors v (smallest vertex of the
+ * entity, lattice coordinates) run x fastest over the interior box: along axis a,
+ * v_a in [0, n-1] if the entity extends along a, else [1, n-1] (PEC removes entities
+ * lying in the boundary).  With R right-hand sides, vectors are row-major [N][R]
+ * (R contiguous).
+ *
+ * Conventions: every function returns 0 on success or a negative YGM_E* code; no
+ * exception crosses the ABI; ygm_last_error() gives the message of the last failure of
+ * that context.  Host pointers are read or written synchronously; device pointers
+ * (on_device = 1) are read or written in stream order on the context's stream, which is
+ * also where every kernel of this library runs.  The context owns all device memory it
+ * allocates; inputs are copied, the caller keeps its buffers.
+ */
+#ifndef YGM_H
+#define YGM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define YGM_OK        0
+#define YGM_EINVAL   -1   /* bad argument (sizes, NULL, NaN, non-positive eps/mu, ...) */
+#define YGM_ECFL     -2   /* dt > tau_CFL (1 + 1e-12): refused, nothing is run (Prop. stability) */
+#define YGM_ENOTSPD  -3   /* Q1 not SPD even after the allowed diagonal shift */
+#define YGM_ENOMEM   -4   /* host or device allocation failed */
+#define YGM_ECUDA    -5   /* a CUDA call failed (message carries cudaGetErrorString) */
+#define YGM_ETIMEOUT -6   /* a bounded device wait gave up */
+#define YGM_ENODEV   -7   /* no CUDA device is available */
+
+#define YGM_FP64 0        /* fields, Q1 and arithmetic in double */
+#define YGM_FP32 1        /* fields, Q1 and arithmetic in float; diagnostics in double */
+
+#define YGM_Q1_DEFAULT 0  /* k = 1: S(M1); k >= 2: S(M1^2) in the orthogonalised basis */
+#define YGM_Q1_DIAG    1  /* S(1): q_l = M_ll / sum_k M_kl^2 */
+#define YGM_Q1_SM1     2  /* S(M1): DoF pairs sharing a tetrahedron, plain basis */
+#define YGM_Q1_SM1SQ   3  /* S(M1^2), orthogonalised basis for k >= 2 */
+
+typedef struct ygm_ctx ygm_ctx;
+
+typedef struct {
+    int32_t n;       /* cubes per side, >= 1 */
+    double side;     /* edge length of the cube, > 0 */
+} ygm_mesh;
+
+typedef struct {
+    int32_t precision;     /* YGM_FP64 or YGM_FP32 */
+    int32_t q1_pattern;    /* YGM_Q1_* */
+    int32_t n_rhs;         /* R >= 1 right-hand sides (independent excitations) */
+    int32_t energy_every;  /* record W_n every K steps inside ygm_step; 0 = off */
+    int32_t threads;       /* host threads for the FP64 set-up; 0 = all cores */
+    int32_t device;        /* CUDA device ordinal; -1 = host-only set-up (operators can be
+                              inspected with ygm_sizes / ygm_export_q1 / ygm_local_blocks /
+                              ygm_q1_info; every stepping call returns YGM_ENODEV) */
+    void*   stream;        /* cudaStream_t to run on; NULL = the context creates its own */
+} ygm_opts;
+
+/* Point dipole J = d delta(x - x0) s(t), s(t) = amp exp(-((t - t0)/sigma)^2) sin(omega (t - t0)),
+ * entering e through j_i = s(t) d . Lambda1_i(x0) (template: the current term of Eq. allEOM). */
+typedef struct {
+    double x[3];      /* position inside the cube */
+    double d[3];      /* dipole moment direction and size */
+    double amp, omega, t0, sigma;
+    int32_t rhs;      /* which right-hand side column it drives, 0 <= rhs < n_rhs */
+} ygm_source;
+
+/* Build the mesh, bases, M1(eps), M2(mu), C, Q1 (SPAI, FP64, symmetrised, SPD-checked),
+ * tau_CFL = 2 / sqrt(lambda_max(Q1 P2)) (Prop. stability) and upload the operators.
+ * eps, mu: per-tet arrays of length 6 n^3 (host, copied) or NULL for 1.  The state starts at
+ * e = 0, b = 0, t = 0.  Errors: YGM_EINVAL, YGM_ENOTSPD, YGM_ENOMEM, YGM_ECUDA, YGM_ENODEV;
+ * on error *out is NULL. */
+int ygm_create(const ygm_mesh* mesh, int order, const double* eps, const double* mu,
+               const ygm_opts* opts, ygm_ctx** out);
+
+/* Sizes: N1 (1-form DoFs), N2 (2-form DoFs), stored nonzeros of the symmetric Q1, and
+ * tau_CFL.  Any pointer may be NULL. */
+int ygm_sizes(const ygm_ctx* ctx, int64_t* n1, int64_t* n2, int64_t* q1_nnz, double* dt_cfl);
+
+/* Copy a state in: e [N1][R], b [N2][R] in the context precision (double for YGM_FP64,
+ * float for YGM_FP32), synchronised (b at the same time as e).  Resets the step count to 0
+ * and the staggering (the next ygm_step starts with the initial half step). */
+int ygm_set_state(ygm_ctx* ctx, const void* e, const void* b, int on_device);
+
+/* Copy the state out.  synced = 1 returns b at the time of e (b_n = b_{n-1/2} - dt/2 C Q1 e_n,
+ * the closing half step of Eq. strangSplit, computed into scratch, state untouched);
+ * synced = 0 returns the staggered b_{n-1/2}.  Either pointer may be NULL. */
+int ygm_get_state(ygm_ctx* ctx, void* e, void* b, int on_device, int synced);
+
+/* e0 = M1 Pi E0: k = 1 the canonical Whitney interpolant (edge integrals, Eq. WhitneyFormDefn)
+ * scaled by M1; k >= 2 the L2 load vector int E0 . Lambda1_i (= M1 times the L2 projection).
+ * E0(x, out, user) is called on host points; the result is written to e for column `rhs`
+ * and b is set to 0 (a state set: step count reset). */
+int ygm_project_E(ygm_ctx* ctx, void (*E0)(const double x[3], double out[3], void* user),
+                  void* user, int32_t rhs);
+
+/* Advance n full steps of size dt (Eq. YeeLeapfrog), with the sources active.  dt must not
+ * exceed tau_CFL (YGM_ECFL, nothing run).  The first step after a state set runs the initial
+ * half step b_{-1/2} = b_0 + dt/2 C Q1 e_0.  A dt different from the previous call's is handled
+ * by closing the old staggering with dt_old/2 and reopening it with dt/2 (exact Strang
+ * composition).  Asynchronous on the context stream; returns after enqueueing. */
+int ygm_step(ygm_ctx* ctx, int64_t n, double dt, const ygm_source* src, int32_t n_src);
+
+/* Conserved discrete energy of the current state (e_n, b_{n-1/2}), per right-hand side:
+ *   W_n = 1/2 e_n^T Q1 e_n + 1/2 b_{n+1/2}^T M2 b_{n-1/2}
+ * (telescoping invariant of the leapfrog; exact up to round-off without sources), and the
+ * paper's H~ = 1/2 e^T Q1 e + 1/2 b_n^T M2 b_n at synchronised time.  FP64 compensated
+ * (Neumaier) sums in a fixed order.  W, Htilde: host arrays of length R; Htilde may be NULL.
+ * Synchronises the context stream. */
+int ygm_energy(ygm_ctx* ctx, double* W, double* Htilde);
+
+/* Energies W recorded by ygm_step every energy_every steps since the last state set:
+ * copies up to max_count values (per RHS, [count][R]) to host `out` and returns the count in
+ * *count.  Synchronises the context stream. */
+int ygm_energy_history(ygm_ctx* ctx, double* out, int64_t max_count, int64_t* count);
+
+/* Current time step index (full steps since the last state set) and time. */
+int ygm_time(const ygm_ctx* ctx, int64_t* step, double* t);
+
+/* The assembled symmetric Q1 in CSR over the global DoF numbering (FP64, as computed by the
+ * set-up; columns sorted).  rowptr: N1 + 1 entries, colind / val: q1_nnz entries (host). */
+int ygm_export_q1(const ygm_ctx* ctx, int64_t* rowptr, int64_t* colind, double* val);
+
+/* SPD check of Q1 (Sec. 5.1, practical considerations): Lanczos estimates of the smallest and
+ * largest eigenvalue before any shift, the diagonal shift applied (0 if none), lambda_max(Q1 P2),
+ * and which pattern / basis was used (YGM_Q1_*, ortho = 1 for the orthogonalised basis). */
+int ygm_q1_info(const ygm_ctx* ctx, double* lmin, double* lmax, double* shift, double* omega_max_sq,
+                int32_t* pattern, int32_t* ortho);
+
+/* Local reference blocks (FP64, identical for the 6 Kuhn shapes in local order):
+ * M1 (n1 x n1), M2 restricted to the curl-carrying 2-forms (n2a x n2a), sizes in n1/n2a. */
+int ygm_local_blocks(const ygm_ctx* ctx, int32_t* n1, int32_t* n2a, double* M1, double* M2a);
+
+/* Per-launch CUDA-event timing on the context stream: enable = 1 brackets every kernel launch
+ * with a pair of events; ygm_kernel_times synchronises, returns the summed milliseconds and
+ * launch counts of each kernel kind since the last query (kinds: 0 Q1 apply, 1 curl -> b,
+ * 2 curl^T M2 -> e, 3 sources, 4 energy) into ms[5] / count[5], and clears the record. */
+int ygm_kernel_timing(ygm_ctx* ctx, int enable);
+int ygm_kernel_times(ygm_ctx* ctx, double* ms, int64_t* count);
+
+/* Launch statistics: kernels launched by this context so far (all kernels of the library). */
+int ygm_launch_count(const ygm_ctx* ctx, int64_t* count);
+
+/* Message of the last failure on this context (or of the last failed ygm_create when ctx is
+ * NULL).  Valid until the next call on the same context. */
+const char* ygm_last_error(const ygm_ctx* ctx);
+
+/* Free the context and its device memory; NULL-safe.  Synchronises the stream. */
+void ygm_destroy(ygm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* YGM_H */

@@ -96,23 +96,19 @@ def spai(M, kind="sm1", dof_map=None):
 
 
 # ----------------------------------------------------------------------------
-# SPAI in a hierarchically orthogonalised basis (reading for orders k >= 2)
+# SPAI in an entity-orthonormalised basis (reading for orders k >= 2)
 #
 # SPAI is not invariant under a change of basis (Sec. 5: the column problems
 # depend on the basis through M).  For k >= 2 the integer-curl hierarchical
 # basis gives an ill-conditioned M1 and an indefinite symmetrised SPAI.  The
-# SPAI is then computed in the basis Lambda' = T Lambda, where T only adds
-# functions of sub-entities (the edges of a face; the edges and faces of a
-# tet) to higher-entity functions and normalises inside each entity:
-#   1. face DoFs F:  Lambda'_F = Lambda_F - c^T Lambda_E,  M1[E,E] c = M1[E,F]
-#      (E = interior DoFs of the face's three edges)
-#   2. cell DoFs Z:  Lambda'_Z = Lambda_Z - c^T Lambda_J,  M1[J,J] c = M1[J,Z]
-#      (J = interior edge and face DoFs of the tet, original basis)
-#   3. per entity group g: Lambda''_g = (M'[g,g])^(-1/2) Lambda'_g  (M' = T12 M1 T12^T)
-# and mapped back as Q1 = T^T Q'' T.  Because every tet that contains an entity
-# contains its sub-entities, Q1 keeps the pattern of Q'' (S(M1) or S(M1^2)), and
-# Q1 is SPD exactly when Q'' is.  The GYM with (Q1, integer C) is the GYM of the
-# basis Lambda'' with (Q'', C T^T): the same trajectory for b and E.
+# SPAI is then computed in the basis Lambda' = T Lambda, T block diagonal over
+# the mesh entities: the DoFs of one edge (or face, or cell) are replaced by
+# their symmetric (Lowdin) orthonormalisation in the M1(eps) inner product,
+#     Lambda'_g = (M1[g,g])^(-1/2) Lambda_g ,
+# and the result is mapped back as Q1 = T^T Q' T.  Every DoF of an entity lives
+# on the same tets, so T keeps the sparsity of M1, Q1 keeps the pattern of Q'
+# (S(M1) or S(M1^2)), and Q1 is SPD exactly when Q' is.  The GYM with (Q1,
+# integer C) is the GYM of the basis Lambda' with (Q', C T^T): the same b and E.
 # ----------------------------------------------------------------------------
 
 def entity_groups(fem):
@@ -138,58 +134,21 @@ def entity_groups(fem):
 
 
 def ortho_basis_transform(fem, M1):
-    """The matrix T of steps 1-3 above (sparse, N1 x N1)."""
-    from .mesh import LOCAL_EDGES, LOCAL_FACES
-    mesh = fem.mesh
-    k = mesh.k
-    per_f = k * (k - 1)
+    """Block-diagonal T: per entity group g, T[g, g] = (M1[g, g])^(-1/2) (sparse, N1 x N1)."""
     M = sp.csr_matrix(M1)
-    N1 = mesh.N1
-    T = sp.lil_matrix((N1, N1))
-    T.setdiag(1.0)
-    done_f, done_c = set(), set()
-    d1 = fem.dof1
-    for t in range(d1.shape[0]):
-        d = d1[t]
-        for lf, (a, b, c) in enumerate(LOCAL_FACES):
-            F = [int(x) for x in d[6 * k + lf * per_f:6 * k + (lf + 1) * per_f] if x >= 0]
-            if not F or F[0] in done_f:
-                continue
-            done_f.add(F[0])
-            E = []
-            for le, (p, q) in enumerate(LOCAL_EDGES):
-                if p in (a, b, c) and q in (a, b, c):
-                    E += [int(x) for x in d[le * k:(le + 1) * k] if x >= 0]
-            if E:
-                cE = np.linalg.solve(M[E][:, E].toarray(), M[E][:, F].toarray())
-                for jj, x in enumerate(F):
-                    for ii, y in enumerate(E):
-                        T[x, y] = -cE[ii, jj]
-        if k >= 3:
-            Z = [int(x) for x in d[6 * k + 4 * per_f:]]
-            if Z[0] in done_c:
-                continue
-            done_c.add(Z[0])
-            J = [int(x) for x in d[:6 * k + 4 * per_f] if x >= 0]
-            cJ = np.linalg.solve(M[J][:, J].toarray(), M[J][:, Z].toarray())
-            for jj, x in enumerate(Z):
-                for ii, y in enumerate(J):
-                    T[x, y] = -cJ[ii, jj]
-    T = T.tocsr()
-    Mp = (T @ M @ T.T).tocsr()
+    N1 = fem.mesh.N1
     edges, faces, cells = entity_groups(fem)
     r, c, v = [], [], []
     for g in edges + faces + cells:
         g = list(g)
-        w, V = np.linalg.eigh(Mp[g][:, g].toarray())
+        w, V = np.linalg.eigh(M[g][:, g].toarray())
         Lg = (V / np.sqrt(w)) @ V.T
         for ii, x in enumerate(g):
             for jj, y in enumerate(g):
                 r.append(x)
                 c.append(y)
                 v.append(Lg[ii, jj])
-    L = sp.csr_matrix((v, (r, c)), shape=(N1, N1))
-    return (L @ T).tocsr()
+    return sp.csr_matrix((v, (r, c)), shape=(N1, N1))
 
 
 def default_policy(order):
@@ -197,12 +156,17 @@ def default_policy(order):
     return ("sm1", "plain") if order == 1 else ("sm1sq", "ortho")
 
 
+def basis_for(order, pattern_kind):
+    """The orthogonalised basis is used exactly for S(M1^2) at orders k >= 2; otherwise the plain basis."""
+    return "ortho" if (order >= 2 and pattern_kind == "sm1sq") else "plain"
+
+
 def gym_q1(fem, M1=None, pattern_kind=None, basis_kind=None):
     """Q1 for the GYM of this mesh: SPAI (Eq. NormalEqSolve), symmetrised, SPD-checked."""
     M1 = fem.M1() if M1 is None else M1
-    dp, db = default_policy(fem.mesh.k)
+    dp, _ = default_policy(fem.mesh.k)
     pattern_kind = pattern_kind or dp
-    basis_kind = basis_kind or db
+    basis_kind = basis_kind or basis_for(fem.mesh.k, pattern_kind)
     S = pattern(pattern_kind, M1, fem.dof1)
     if basis_kind == "plain":
         Q = symmetrize(spai_columns(M1, S))

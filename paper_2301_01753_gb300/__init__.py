@@ -1,0 +1,248 @@
+"""Python binding of libygm (the GB300 generalized Yee method leapfrog library).
+
+Argument marshalling only: every step of the time integration runs in the library's CUDA
+kernels, and the FP64 operator set-up runs in its C++ host code.  Names follow the C ABI
+in include/ygm.h.  The library is built in-tree (paper_2301_01753_gb300/libygm.so); if it
+is missing, importing this module raises -- there is no fallback path.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libygm.so")
+
+YGM_OK, YGM_EINVAL, YGM_ECFL, YGM_ENOTSPD, YGM_ENOMEM, YGM_ECUDA, YGM_ETIMEOUT, YGM_ENODEV = 0, -1, -2, -3, -4, -5, -6, -7
+YGM_FP64, YGM_FP32 = 0, 1
+YGM_Q1_DEFAULT, YGM_Q1_DIAG, YGM_Q1_SM1, YGM_Q1_SM1SQ = 0, 1, 2, 3
+
+EXPORTED = ["ygm_create", "ygm_sizes", "ygm_set_state", "ygm_get_state", "ygm_project_E", "ygm_step",
+            "ygm_energy", "ygm_energy_history", "ygm_time", "ygm_export_q1", "ygm_q1_info",
+            "ygm_local_blocks", "ygm_kernel_timing", "ygm_kernel_times", "ygm_launch_count",
+            "ygm_last_error", "ygm_destroy"]
+KERNEL_KINDS = ["k_qapply", "k_curl_b", "k_curlT_e", "k_source", "k_energy"]
+
+
+class YgmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"ygm error {code}: {msg}")
+        self.code = code
+
+
+class ygm_mesh(C.Structure):
+    _fields_ = [("n", C.c_int32), ("side", C.c_double)]
+
+
+class ygm_opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("q1_pattern", C.c_int32), ("n_rhs", C.c_int32),
+                ("energy_every", C.c_int32), ("threads", C.c_int32), ("device", C.c_int32),
+                ("stream", C.c_void_p)]
+
+
+class ygm_source(C.Structure):
+    _fields_ = [("x", C.c_double * 3), ("d", C.c_double * 3), ("amp", C.c_double), ("omega", C.c_double),
+                ("t0", C.c_double), ("sigma", C.c_double), ("rhs", C.c_int32)]
+
+
+E0_CB = C.CFUNCTYPE(None, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p)
+
+
+def load_library(path=LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with __graft_entry__.build() "
+                          "(python -m paper_2301_01753_gb300._build)")
+    lib = C.CDLL(path)
+    P, I64, D = C.c_void_p, C.c_int64, C.c_double
+    pI64, pD, pI32 = C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_int32)
+    sig = {
+        "ygm_create": (C.c_int, [C.POINTER(ygm_mesh), C.c_int, pD, pD, C.POINTER(ygm_opts), C.POINTER(P)]),
+        "ygm_sizes": (C.c_int, [P, pI64, pI64, pI64, pD]),
+        "ygm_set_state": (C.c_int, [P, P, P, C.c_int]),
+        "ygm_get_state": (C.c_int, [P, P, P, C.c_int, C.c_int]),
+        "ygm_project_E": (C.c_int, [P, E0_CB, P, C.c_int32]),
+        "ygm_step": (C.c_int, [P, I64, D, C.POINTER(ygm_source), C.c_int32]),
+        "ygm_energy": (C.c_int, [P, pD, pD]),
+        "ygm_energy_history": (C.c_int, [P, pD, I64, pI64]),
+        "ygm_time": (C.c_int, [P, pI64, pD]),
+        "ygm_export_q1": (C.c_int, [P, pI64, pI64, pD]),
+        "ygm_q1_info": (C.c_int, [P, pD, pD, pD, pD, pI32, pI32]),
+        "ygm_local_blocks": (C.c_int, [P, pI32, pI32, pD, pD]),
+        "ygm_kernel_timing": (C.c_int, [P, C.c_int]),
+        "ygm_kernel_times": (C.c_int, [P, pD, pI64]),
+        "ygm_launch_count": (C.c_int, [P, pI64]),
+        "ygm_last_error": (C.c_char_p, [P]),
+        "ygm_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = load_library()
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array or a torch tensor (contiguous), and whether it is on a device."""
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return C.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
+    assert isinstance(a, np.ndarray) and a.flags.c_contiguous
+    return a.ctypes.data_as(C.c_void_p), 0
+
+
+class Context:
+    """One GYM cavity: operators on the device plus the state (e, b)."""
+
+    def __init__(self, n, order, eps=None, mu=None, side=1.0, precision=YGM_FP64, q1_pattern=YGM_Q1_DEFAULT,
+                 n_rhs=1, energy_every=0, threads=0, device=0, stream=None):
+        self._h = C.c_void_p()
+        mesh = ygm_mesh(int(n), float(side))
+        opts = ygm_opts(precision, q1_pattern, n_rhs, energy_every, threads, device,
+                        C.c_void_p(stream) if stream else None)
+        T = 6 * n ** 3
+        self._eps = None if eps is None else np.ascontiguousarray(eps, np.float64)
+        self._mu = None if mu is None else np.ascontiguousarray(mu, np.float64)
+        for a in (self._eps, self._mu):
+            if a is not None and a.shape != (T,):
+                raise ValueError(f"per-tet arrays must have length 6 n^3 = {T}")
+        pe = self._eps.ctypes.data_as(C.POINTER(C.c_double)) if self._eps is not None else None
+        pm = self._mu.ctypes.data_as(C.POINTER(C.c_double)) if self._mu is not None else None
+        rc = _lib.ygm_create(C.byref(mesh), int(order), pe, pm, C.byref(opts), C.byref(self._h))
+        if rc:
+            raise YgmError(rc, _lib.ygm_last_error(None).decode())
+        self.n, self.order, self.precision, self.n_rhs = n, order, precision, n_rhs
+        self.dtype = np.float64 if precision == YGM_FP64 else np.float32
+        self.N1, self.N2, self.q1_nnz, self.tau_cfl = self.sizes()
+
+    # ---------------------------------------------------------------- helpers
+    def _check(self, rc):
+        if rc:
+            raise YgmError(rc, _lib.ygm_last_error(self._h).decode())
+
+    def close(self):
+        if self._h:
+            _lib.ygm_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---------------------------------------------------------------- ABI calls
+    def sizes(self):
+        n1, n2, nnz, dt = C.c_int64(), C.c_int64(), C.c_int64(), C.c_double()
+        self._check(_lib.ygm_sizes(self._h, C.byref(n1), C.byref(n2), C.byref(nnz), C.byref(dt)))
+        return n1.value, n2.value, nnz.value, dt.value
+
+    def set_state(self, e, b):
+        pe, de = _ptr(e)
+        pb, db = _ptr(b)
+        assert de == db
+        self._check(_lib.ygm_set_state(self._h, pe, pb, de))
+
+    def get_state(self, synced=True, out_e=None, out_b=None):
+        R = self.n_rhs
+        e = out_e if out_e is not None else np.empty(self.N1 * R, self.dtype)
+        b = out_b if out_b is not None else np.empty(self.N2 * R, self.dtype)
+        pe, de = _ptr(e)
+        pb, db = _ptr(b)
+        self._check(_lib.ygm_get_state(self._h, pe, pb, de, 1 if synced else 0))
+        return e, b
+
+    def project_E(self, E0, rhs=0):
+        """E0(x: ndarray(3)) -> ndarray(3), evaluated on host points by the library."""
+        def cb(xp, outp, user):
+            v = E0(np.array([xp[0], xp[1], xp[2]]))
+            outp[0], outp[1], outp[2] = float(v[0]), float(v[1]), float(v[2])
+        self._cb = E0_CB(cb)
+        self._check(_lib.ygm_project_E(self._h, self._cb, None, rhs))
+
+    def step(self, n, dt, sources=()):
+        arr = (ygm_source * max(1, len(sources)))()
+        for i, s in enumerate(sources):
+            arr[i].x[:] = list(map(float, s["x"]))
+            arr[i].d[:] = list(map(float, s["d"]))
+            arr[i].amp = float(s.get("amp", 1.0))
+            arr[i].omega = float(s["omega"])
+            arr[i].t0 = float(s["t0"])
+            arr[i].sigma = float(s["sigma"])
+            arr[i].rhs = int(s.get("rhs", 0))
+        self._check(_lib.ygm_step(self._h, int(n), float(dt), arr, len(sources)))
+
+    def energy(self):
+        W = (C.c_double * self.n_rhs)()
+        H = (C.c_double * self.n_rhs)()
+        self._check(_lib.ygm_energy(self._h, W, H))
+        return np.array(W[:]), np.array(H[:])
+
+    def energy_history(self, max_count=1 << 16):
+        out = np.empty(max_count * self.n_rhs)
+        cnt = C.c_int64()
+        self._check(_lib.ygm_energy_history(self._h, out.ctypes.data_as(C.POINTER(C.c_double)), max_count,
+                                            C.byref(cnt)))
+        return out[:cnt.value * self.n_rhs].copy()
+
+    def time(self):
+        s, t = C.c_int64(), C.c_double()
+        self._check(_lib.ygm_time(self._h, C.byref(s), C.byref(t)))
+        return s.value, t.value
+
+    def export_q1(self):
+        """(rowptr, colind, val) of the symmetric FP64 Q1 over the global numbering."""
+        rp = np.empty(self.N1 + 1, np.int64)
+        ci = np.empty(self.q1_nnz, np.int64)
+        va = np.empty(self.q1_nnz, np.float64)
+        self._check(_lib.ygm_export_q1(self._h, rp.ctypes.data_as(C.POINTER(C.c_int64)),
+                                       ci.ctypes.data_as(C.POINTER(C.c_int64)),
+                                       va.ctypes.data_as(C.POINTER(C.c_double))))
+        return rp, ci, va
+
+    def q1_info(self):
+        lmin, lmax, sh, w2 = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+        pat, orth = C.c_int32(), C.c_int32()
+        self._check(_lib.ygm_q1_info(self._h, C.byref(lmin), C.byref(lmax), C.byref(sh), C.byref(w2),
+                                     C.byref(pat), C.byref(orth)))
+        return dict(lmin=lmin.value, lmax=lmax.value, shift=sh.value, omega_max_sq=w2.value,
+                    pattern=pat.value, ortho=orth.value)
+
+    def local_blocks(self):
+        n1, n2a = C.c_int32(), C.c_int32()
+        self._check(_lib.ygm_local_blocks(self._h, C.byref(n1), C.byref(n2a), None, None))
+        M1 = np.empty(n1.value ** 2)
+        M2 = np.empty(n2a.value ** 2)
+        self._check(_lib.ygm_local_blocks(self._h, C.byref(n1), C.byref(n2a),
+                                          M1.ctypes.data_as(C.POINTER(C.c_double)),
+                                          M2.ctypes.data_as(C.POINTER(C.c_double))))
+        return M1.reshape(n1.value, -1), M2.reshape(n2a.value, -1)
+
+    def kernel_timing(self, enable=True):
+        self._check(_lib.ygm_kernel_timing(self._h, 1 if enable else 0))
+
+    def kernel_times(self):
+        """{kernel: (total ms, launches)} since the last call (requires kernel_timing(True))."""
+        ms = (C.c_double * 5)()
+        cnt = (C.c_int64 * 5)()
+        self._check(_lib.ygm_kernel_times(self._h, ms, cnt))
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+    def launch_count(self):
+        c = C.c_int64()
+        self._check(_lib.ygm_launch_count(self._h, C.byref(c)))
+        return c.value
+
+
+def pulse_source(x, d, omega, dt, width_steps=20.0, amp=1.0, t0_sigmas=4.0, rhs=0):
+    """Dipole with s(t) = amp exp(-((t - t0)/sigma)^2) sin(omega (t - t0)), sigma = width * dt, t0 = 4 sigma."""
+    sigma = width_steps * dt
+    return dict(x=x, d=d, amp=amp, omega=omega, t0=t0_sigmas * sigma, sigma=sigma, rhs=rhs)

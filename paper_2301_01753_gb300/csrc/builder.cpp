@@ -1,0 +1,1412 @@
+// FP64 host set-up of the GYM operators (see builder.h).
+//
+// Paper passages: Sec. 2 (de Rham complex, mass matrices), Sec. 5 (SPAI, Eq. NormalEqSolve,
+// symmetrisation, SPD check), Prop. stability (CFL bound), Sec. 3 (shear maps use Q1, C, M2).
+#include "builder.h"
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <numeric>
+#include <stdexcept>
+#include <thread>
+
+namespace ygm {
+
+// ============================================================== small utilities
+static void parallel_for(int64_t n, int threads, const std::function<void(int64_t, int64_t, int)>& fn) {
+    if (threads <= 1 || n < 64) {
+        fn(0, n, 0);
+        return;
+    }
+    std::vector<std::thread> pool;
+    std::atomic<int64_t> next(0);
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(4096, n / (threads * 16) + 1));
+    for (int t = 0; t < threads; ++t) {
+        pool.emplace_back([&, t]() {
+            for (;;) {
+                int64_t b = next.fetch_add(chunk);
+                if (b >= n) break;
+                fn(b, std::min(n, b + chunk), t);
+            }
+        });
+    }
+    for (auto& th : pool) th.join();
+}
+
+static int default_threads(int t) {
+    if (t > 0) return t;
+    unsigned h = std::thread::hardware_concurrency();
+    return h ? (int)h : 4;
+}
+
+// Dense symmetric positive definite solve by Cholesky (in place); returns false if not SPD.
+// Row-major storage; the factor L overwrites the lower triangle (row i of L is contiguous).
+// The trailing update of each 4-column panel is done in 4 x 4 register tiles of dot products
+// over the already factored columns, so each loaded value feeds two FMAs.
+static bool cholesky_solve(int m, double* A, double* b, int nrhs) {
+    for (int j0 = 0; j0 < m; j0 += 4) {
+        const int jb = std::min(4, m - j0);
+        // panel update: A(i, j0+c) -= sum_{k < j0} L(i, k) L(j0+c, k), i >= j0
+        if (j0 > 0) {
+            const double* Lj[4];
+            for (int c = 0; c < 4; ++c) Lj[c] = A + (int64_t)(j0 + std::min(c, jb - 1)) * m;
+            int i0 = j0;
+            for (; i0 + 4 <= m; i0 += 4) {
+                const double* Li0 = A + (int64_t)i0 * m;
+                const double* Li1 = Li0 + m;
+                const double* Li2 = Li1 + m;
+                const double* Li3 = Li2 + m;
+                double a00 = 0, a01 = 0, a02 = 0, a03 = 0, a10 = 0, a11 = 0, a12 = 0, a13 = 0;
+                double a20 = 0, a21 = 0, a22 = 0, a23 = 0, a30 = 0, a31 = 0, a32 = 0, a33 = 0;
+                for (int k = 0; k < j0; ++k) {
+                    const double b0 = Lj[0][k], b1 = Lj[1][k], b2 = Lj[2][k], b3 = Lj[3][k];
+                    const double x0 = Li0[k], x1 = Li1[k], x2 = Li2[k], x3 = Li3[k];
+                    a00 += x0 * b0; a01 += x0 * b1; a02 += x0 * b2; a03 += x0 * b3;
+                    a10 += x1 * b0; a11 += x1 * b1; a12 += x1 * b2; a13 += x1 * b3;
+                    a20 += x2 * b0; a21 += x2 * b1; a22 += x2 * b2; a23 += x2 * b3;
+                    a30 += x3 * b0; a31 += x3 * b1; a32 += x3 * b2; a33 += x3 * b3;
+                }
+                const double acc[4][4] = {{a00, a01, a02, a03}, {a10, a11, a12, a13},
+                                          {a20, a21, a22, a23}, {a30, a31, a32, a33}};
+                for (int r = 0; r < 4; ++r)
+                    for (int c = 0; c < jb; ++c)
+                        if (i0 + r >= j0 + c) A[(int64_t)(i0 + r) * m + j0 + c] -= acc[r][c];
+            }
+            for (; i0 < m; ++i0) {
+                const double* Li = A + (int64_t)i0 * m;
+                for (int c = 0; c < jb; ++c) {
+                    if (i0 < j0 + c) continue;
+                    double s = 0;
+                    for (int k = 0; k < j0; ++k) s += Li[k] * Lj[c][k];
+                    A[(int64_t)i0 * m + j0 + c] -= s;
+                }
+            }
+        }
+        // factor the panel columns j0 .. j0+jb-1 (left-looking inside the panel)
+        for (int c = 0; c < jb; ++c) {
+            const int j = j0 + c;
+            double* Aj = A + (int64_t)j * m;
+            for (int p = j0; p < j; ++p) Aj[j] -= Aj[p] * Aj[p];
+            const double d = Aj[j];
+            if (!(d > 0)) return false;
+            const double sd = std::sqrt(d);
+            Aj[j] = sd;
+            const double inv = 1.0 / sd;
+            for (int i = j + 1; i < m; ++i) {
+                double* Ai = A + (int64_t)i * m;
+                double s = Ai[j];
+                for (int p = j0; p < j; ++p) s -= Ai[p] * Aj[p];
+                Ai[j] = s * inv;
+            }
+        }
+    }
+    for (int r = 0; r < nrhs; ++r) {
+        double* x = b + (int64_t)r * m;
+        for (int i = 0; i < m; ++i) {
+            const double* Ai = A + (int64_t)i * m;
+            double s = x[i];
+            for (int p = 0; p < i; ++p) s -= Ai[p] * x[p];
+            x[i] = s / Ai[i];
+        }
+        for (int i = m - 1; i >= 0; --i) {
+            const double* Ai = A + (int64_t)i * m;
+            x[i] /= Ai[i];
+            const double xi = x[i];
+            for (int p = 0; p < i; ++p) x[p] -= Ai[p] * xi;
+        }
+    }
+    return true;
+}
+
+// Symmetric eigen-decomposition by cyclic Jacobi rotations (small matrices only).
+static void jacobi_eigen(int m, std::vector<double> A, std::vector<double>& w, std::vector<double>& V) {
+    V.assign((size_t)m * m, 0.0);
+    for (int i = 0; i < m; ++i) V[(size_t)i * m + i] = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0;
+        for (int i = 0; i < m; ++i)
+            for (int j = i + 1; j < m; ++j) off += A[(size_t)i * m + j] * A[(size_t)i * m + j];
+        if (off < 1e-30) break;
+        for (int p = 0; p < m; ++p)
+            for (int q = p + 1; q < m; ++q) {
+                double apq = A[(size_t)p * m + q];
+                if (std::fabs(apq) < 1e-300) continue;
+                double app = A[(size_t)p * m + p], aqq = A[(size_t)q * m + q];
+                double theta = 0.5 * (aqq - app) / apq;
+                double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < m; ++k) {
+                    double akp = A[(size_t)k * m + p], akq = A[(size_t)k * m + q];
+                    A[(size_t)k * m + p] = c * akp - s * akq;
+                    A[(size_t)k * m + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < m; ++k) {
+                    double apk = A[(size_t)p * m + k], aqk = A[(size_t)q * m + k];
+                    A[(size_t)p * m + k] = c * apk - s * aqk;
+                    A[(size_t)q * m + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < m; ++k) {
+                    double vkp = V[(size_t)k * m + p], vkq = V[(size_t)k * m + q];
+                    V[(size_t)k * m + p] = c * vkp - s * vkq;
+                    V[(size_t)k * m + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    w.resize(m);
+    for (int i = 0; i < m; ++i) w[i] = A[(size_t)i * m + i];
+}
+
+// ============================================================== lattice
+static const int EDGE_D[7] = {1, 2, 3, 4, 5, 6, 7};
+static const int FACE_D[12][2] = {{1, 3}, {2, 3}, {1, 5}, {4, 5}, {2, 6}, {4, 6},
+                                  {1, 7}, {2, 7}, {3, 7}, {4, 7}, {5, 7}, {6, 7}};
+static const int TET_D[6][2] = {{1, 3}, {1, 5}, {2, 3}, {2, 6}, {4, 5}, {4, 6}};
+static const int LEDGE[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+static const int LFACE[4][3] = {{0, 1, 2}, {0, 1, 3}, {0, 2, 3}, {1, 2, 3}};
+
+static int face_index(int d1, int d2) {
+    for (int i = 0; i < 12; ++i)
+        if (FACE_D[i][0] == d1 && FACE_D[i][1] == d2) return i;
+    return -1;
+}
+static inline int bit(int m, int a) { return (m >> a) & 1; }
+
+bool Nbr::operator<(const Nbr& o) const {
+    if (d[2] != o.d[2]) return d[2] < o.d[2];
+    if (d[1] != o.d[1]) return d[1] < o.d[1];
+    if (d[0] != o.d[0]) return d[0] < o.d[0];
+    return cls < o.cls;
+}
+bool Nbr::operator==(const Nbr& o) const {
+    return cls == o.cls && d[0] == o.d[0] && d[1] == o.d[1] && d[2] == o.d[2];
+}
+
+int64_t Lattice::index(const std::vector<DofClass>& cls, int c, int x, int y, int z) const {
+    const Box& b = cls[c].box;
+    int r0 = x - b.lo[0], r1 = y - b.lo[1], r2 = z - b.lo[2];
+    if (r0 < 0 || r1 < 0 || r2 < 0 || r0 >= b.num[0] || r1 >= b.num[1] || r2 >= b.num[2]) return -1;
+    return b.offset + ((int64_t)r2 * b.num[1] + r1) * b.num[0] + r0;
+}
+
+void Lattice::build(int n_, int k_, double side) {
+    n = n_;
+    k = k_;
+    h = side / n;
+    const int e1 = k, f1 = k * (k - 1), t1 = k * (k - 1) * (k - 2) / 2;
+    const int f2 = k * (k + 1) / 2, t2 = (k - 1) * k * (k + 1) / 2;
+    auto mk = [&](std::vector<DofClass>& v, int kind, int shape, int j, int ext, bool active) {
+        DofClass c{};
+        c.kind = kind;
+        c.shape = shape;
+        c.j = j;
+        c.ext = ext;
+        c.active = active;
+        for (int a = 0; a < 3; ++a) {
+            c.box.lo[a] = bit(ext, a) ? 0 : 1;
+            c.box.num[a] = bit(ext, a) ? n : n - 1;
+        }
+        c.box.size = (int64_t)c.box.num[0] * c.box.num[1] * c.box.num[2];
+        v.push_back(c);
+    };
+    c1.clear();
+    c2.clear();
+    // 1-forms: edge j = 0 Whitney (active), j >= 1 gradients; face: gradient at j = 5 (k = 3)
+    for (int s = 0; s < 7; ++s)
+        for (int j = 0; j < e1; ++j) mk(c1, 0, s, j, EDGE_D[s], j == 0);
+    for (int s = 0; s < 12; ++s)
+        for (int j = 0; j < f1; ++j) mk(c1, 1, s, j, FACE_D[s][1], !(k == 3 && j == 5));
+    for (int s = 0; s < 6; ++s)
+        for (int j = 0; j < t1; ++j) mk(c1, 2, s, j, 7, true);
+    // 2-forms: face DoFs are all rows of C; tet DoFs: curls of cell 1-forms (k = 3, j < 3)
+    for (int s = 0; s < 12; ++s)
+        for (int j = 0; j < f2; ++j) mk(c2, 1, s, j, FACE_D[s][1], true);
+    for (int s = 0; s < 6; ++s)
+        for (int j = 0; j < t2; ++j) mk(c2, 2, s, j, 7, k == 3 && j < 3);
+    int64_t off = 0;
+    for (auto& c : c1) {
+        c.box.offset = off;
+        off += c.box.size;
+    }
+    N1 = off;
+    off = 0;
+    for (auto& c : c2) {
+        c.box.offset = off;
+        off += c.box.size;
+    }
+    N2 = off;
+    n1 = 6 * e1 + 4 * f1 + t1;
+    n2 = 4 * f2 + t2;
+    // local DoF maps for every tet shape
+    for (int s = 0; s < 6; ++s) {
+        const int vo[4] = {0, TET_D[s][0], TET_D[s][1], 7};
+        loc1[s].clear();
+        loc2[s].clear();
+        for (int le = 0; le < 6; ++le) {
+            int a = LEDGE[le][0], b = LEDGE[le][1];
+            int d = vo[b] ^ vo[a];
+            for (int j = 0; j < e1; ++j) {
+                LocalDof L{(d - 1) * e1 + j, {bit(vo[a], 0), bit(vo[a], 1), bit(vo[a], 2)}};
+                loc1[s].push_back(L);
+            }
+        }
+        for (int lf = 0; lf < 4; ++lf) {
+            int a = LFACE[lf][0], b = LFACE[lf][1], c = LFACE[lf][2];
+            int fs = face_index(vo[b] ^ vo[a], vo[c] ^ vo[a]);
+            for (int j = 0; j < f1; ++j) {
+                LocalDof L{7 * e1 + fs * f1 + j, {bit(vo[a], 0), bit(vo[a], 1), bit(vo[a], 2)}};
+                loc1[s].push_back(L);
+            }
+            for (int j = 0; j < f2; ++j) {
+                LocalDof L{fs * f2 + j, {bit(vo[a], 0), bit(vo[a], 1), bit(vo[a], 2)}};
+                loc2[s].push_back(L);
+            }
+        }
+        for (int j = 0; j < t1; ++j) loc1[s].push_back(LocalDof{7 * e1 + 12 * f1 + s * t1 + j, {0, 0, 0}});
+        for (int j = 0; j < t2; ++j) loc2[s].push_back(LocalDof{12 * f2 + s * t2 + j, {0, 0, 0}});
+    }
+    act2.clear();
+    for (int r = 0; r < n2; ++r)
+        if (c2[loc2[0][r].cls].active) act2.push_back(r);
+    n2a = (int)act2.size();
+    // incidences: every (shape, local DoF) with class c gives a tet at cube = anchor - off
+    inc1.assign(c1.size(), {});
+    for (int s = 0; s < 6; ++s)
+        for (int r = 0; r < n1; ++r) {
+            const LocalDof& L = loc1[s][r];
+            inc1[L.cls].push_back(Incidence{{-L.off[0], -L.off[1], -L.off[2]}, s, r});
+        }
+}
+
+void Lattice::tet_dofs1(int64_t t, int64_t* out) const {
+    int s = (int)(t % 6);
+    int64_t cube = t / 6;
+    int cx = (int)(cube % n), cy = (int)((cube / n) % n), cz = (int)(cube / ((int64_t)n * n));
+    for (int r = 0; r < n1; ++r) {
+        const LocalDof& L = loc1[s][r];
+        out[r] = index1(L.cls, cx + L.off[0], cy + L.off[1], cz + L.off[2]);
+    }
+}
+void Lattice::tet_dofs2(int64_t t, int64_t* out) const {
+    int s = (int)(t % 6);
+    int64_t cube = t / 6;
+    int cx = (int)(cube % n), cy = (int)((cube / n) % n), cz = (int)(cube / ((int64_t)n * n));
+    for (int r = 0; r < n2; ++r) {
+        const LocalDof& L = loc2[s][r];
+        out[r] = index2(L.cls, cx + L.off[0], cy + L.off[1], cz + L.off[2]);
+    }
+}
+void Lattice::decode1(int64_t g, int* cls, int v[3]) const {
+    int c = 0;
+    while (c + 1 < (int)c1.size() && c1[c + 1].box.offset <= g) ++c;
+    const Box& b = c1[c].box;
+    int64_t r = g - b.offset;
+    v[0] = (int)(r % b.num[0]) + b.lo[0];
+    v[1] = (int)((r / b.num[0]) % b.num[1]) + b.lo[1];
+    v[2] = (int)(r / ((int64_t)b.num[0] * b.num[1])) + b.lo[2];
+    *cls = c;
+}
+
+// ============================================================== polynomial bases
+// 1-form term: c * l^a * g_m ; 2-form term: c * l^a * (g_p x g_q)
+struct T1 {
+    double c;
+    int a[4];
+    int m;
+};
+struct T2 {
+    double c;
+    int a[4];
+    int p, q;
+};
+using F1 = std::vector<T1>;
+using F2 = std::vector<T2>;
+struct Poly {
+    std::vector<std::pair<double, std::array<int, 4>>> t;
+};
+static Poly mono(std::initializer_list<int> idx, double c = 1.0) {
+    std::array<int, 4> a{0, 0, 0, 0};
+    for (int i : idx) a[i]++;
+    Poly P;
+    P.t.push_back({c, a});
+    return P;
+}
+static Poly operator+(Poly A, const Poly& B) {
+    for (auto& x : B.t) A.t.push_back(x);
+    return A;
+}
+static F1 pw(const Poly& P, int a, int b) {  // P (l_a g_b - l_b g_a)
+    F1 f;
+    for (auto& [c, al] : P.t) {
+        T1 u{c, {al[0], al[1], al[2], al[3]}, b};
+        u.a[a]++;
+        f.push_back(u);
+        T1 v{-c, {al[0], al[1], al[2], al[3]}, a};
+        v.a[b]++;
+        f.push_back(v);
+    }
+    return f;
+}
+static F1 grad(const Poly& P) {
+    F1 f;
+    for (auto& [c, al] : P.t)
+        for (int m = 0; m < 4; ++m)
+            if (al[m] > 0) {
+                T1 u{c * al[m], {al[0], al[1], al[2], al[3]}, m};
+                u.a[m]--;
+                f.push_back(u);
+            }
+    return f;
+}
+static F2 curl(const F1& f) {
+    F2 g;
+    for (auto& u : f)
+        for (int m = 0; m < 4; ++m)
+            if (u.a[m] > 0) {
+                T2 v{u.c * u.a[m], {u.a[0], u.a[1], u.a[2], u.a[3]}, m, u.m};
+                v.a[m]--;
+                g.push_back(v);
+            }
+    return g;
+}
+static F2 whitney2(int a, int b, int c) {
+    F2 g;
+    T2 u{2.0, {0, 0, 0, 0}, b, c};
+    u.a[a] = 1;
+    g.push_back(u);
+    T2 v{2.0, {0, 0, 0, 0}, c, a};
+    v.a[b] = 1;
+    g.push_back(v);
+    T2 w{2.0, {0, 0, 0, 0}, a, b};
+    w.a[c] = 1;
+    g.push_back(w);
+    return g;
+}
+
+// Local 1-form basis in the local order of the lattice (edges, faces, cell), plus a flag
+// telling which functions are gradients.
+static void one_forms(int k, std::vector<F1>& F, std::vector<bool>& is_grad) {
+    F.clear();
+    is_grad.clear();
+    for (int le = 0; le < 6; ++le) {
+        int a = LEDGE[le][0], b = LEDGE[le][1];
+        F.push_back(pw(mono({}), a, b));
+        is_grad.push_back(false);
+        if (k >= 2) {
+            F.push_back(grad(mono({a, b})));
+            is_grad.push_back(true);
+        }
+        if (k >= 3) {
+            F.push_back(grad(mono({a, b, b}) + mono({a, a, b}, -1.0)));
+            is_grad.push_back(true);
+        }
+    }
+    for (int lf = 0; lf < 4; ++lf) {
+        int a = LFACE[lf][0], b = LFACE[lf][1], c = LFACE[lf][2];
+        if (k >= 2) {
+            F.push_back(pw(mono({c}), a, b));
+            F.push_back(pw(mono({b}), a, c));
+            is_grad.push_back(false);
+            is_grad.push_back(false);
+        }
+        if (k >= 3) {
+            F.push_back(pw(mono({a, c}), a, b));
+            F.push_back(pw(mono({b, c}), a, b));
+            F.push_back(pw(mono({a, b}), a, c));
+            F.push_back(grad(mono({a, b, c})));
+            is_grad.insert(is_grad.end(), {false, false, false, true});
+        }
+    }
+    if (k >= 3) {
+        F.push_back(pw(mono({2, 3}), 0, 1));
+        F.push_back(pw(mono({1, 3}), 0, 2));
+        F.push_back(pw(mono({1, 2}), 0, 3));
+        is_grad.insert(is_grad.end(), {false, false, false});
+    }
+}
+
+static double fact(int n) {
+    double r = 1;
+    for (int i = 2; i <= n; ++i) r *= i;
+    return r;
+}
+// int_T l^a dx = 6 |T| a! / (|a| + 3)!
+static double bary_integral(const int a[4], double vol) {
+    int s = a[0] + a[1] + a[2] + a[3];
+    return 6.0 * vol * fact(a[0]) * fact(a[1]) * fact(a[2]) * fact(a[3]) / fact(s + 3);
+}
+static inline void cross3(const double* u, const double* v, double* w) {
+    w[0] = u[1] * v[2] - u[2] * v[1];
+    w[1] = u[2] * v[0] - u[0] * v[2];
+    w[2] = u[0] * v[1] - u[1] * v[0];
+}
+
+struct RefTet {
+    double X[4][3];
+    double g[4][3];
+    double vol;
+};
+static RefTet ref_tet(int s, double h) {
+    RefTet R{};
+    const int vo[4] = {0, TET_D[s][0], TET_D[s][1], 7};
+    for (int i = 0; i < 4; ++i)
+        for (int a = 0; a < 3; ++a) R.X[i][a] = h * bit(vo[i], a);
+    // gradients of barycentric coordinates: invert [1 x y z]
+    double A[4][4];
+    for (int i = 0; i < 4; ++i) {
+        A[0][i] = 1.0;
+        for (int a = 0; a < 3; ++a) A[a + 1][i] = R.X[i][a];
+    }
+    // Gauss-Jordan inverse of A (4 x 4)
+    double M[4][8];
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 8; ++j) M[i][j] = j < 4 ? A[i][j] : (j - 4 == i ? 1.0 : 0.0);
+    for (int c = 0; c < 4; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 4; ++r)
+            if (std::fabs(M[r][c]) > std::fabs(M[piv][c])) piv = r;
+        for (int j = 0; j < 8; ++j) std::swap(M[c][j], M[piv][j]);
+        double d = M[c][c];
+        for (int j = 0; j < 8; ++j) M[c][j] /= d;
+        for (int r = 0; r < 4; ++r)
+            if (r != c) {
+                double f = M[r][c];
+                for (int j = 0; j < 8; ++j) M[r][j] -= f * M[c][j];
+            }
+    }
+    // lambda = Ainv [1; x], so grad lambda_i = Ainv[i][1..3]
+    for (int i = 0; i < 4; ++i)
+        for (int a = 0; a < 3; ++a) R.g[i][a] = M[i][4 + a + 1];
+    double e1[3], e2[3], e3[3], cr[3];
+    for (int a = 0; a < 3; ++a) {
+        e1[a] = R.X[1][a] - R.X[0][a];
+        e2[a] = R.X[2][a] - R.X[0][a];
+        e3[a] = R.X[3][a] - R.X[0][a];
+    }
+    cross3(e1, e2, cr);
+    R.vol = std::fabs(cr[0] * e3[0] + cr[1] * e3[1] + cr[2] * e3[2]) / 6.0;
+    return R;
+}
+
+static double mass1(const F1& f, const F1& g, const RefTet& R) {
+    double s = 0;
+    for (auto& u : f)
+        for (auto& v : g) {
+            int a[4] = {u.a[0] + v.a[0], u.a[1] + v.a[1], u.a[2] + v.a[2], u.a[3] + v.a[3]};
+            double dot = R.g[u.m][0] * R.g[v.m][0] + R.g[u.m][1] * R.g[v.m][1] + R.g[u.m][2] * R.g[v.m][2];
+            s += u.c * v.c * dot * bary_integral(a, R.vol);
+        }
+    return s;
+}
+static double mass2(const F2& f, const F2& g, const RefTet& R) {
+    double s = 0;
+    for (auto& u : f) {
+        double cu[3];
+        cross3(R.g[u.p], R.g[u.q], cu);
+        for (auto& v : g) {
+            double cv[3];
+            cross3(R.g[v.p], R.g[v.q], cv);
+            int a[4] = {u.a[0] + v.a[0], u.a[1] + v.a[1], u.a[2] + v.a[2], u.a[3] + v.a[3]};
+            s += u.c * v.c * (cu[0] * cv[0] + cu[1] * cv[1] + cu[2] * cv[2]) * bary_integral(a, R.vol);
+        }
+    }
+    return s;
+}
+static void eval1(const F1& f, const double lam[4], const RefTet& R, double out[3]) {
+    out[0] = out[1] = out[2] = 0;
+    for (auto& u : f) {
+        double p = u.c;
+        for (int i = 0; i < 4; ++i)
+            for (int e = 0; e < u.a[i]; ++e) p *= lam[i];
+        for (int a = 0; a < 3; ++a) out[a] += p * R.g[u.m][a];
+    }
+}
+
+// ============================================================== sparse helpers
+double Csr::get(int64_t i, int64_t j) const {
+    auto b = col.begin() + ptr[i], e = col.begin() + ptr[i + 1];
+    auto it = std::lower_bound(b, e, j);
+    if (it != e && *it == j) return val[it - col.begin()];
+    return 0.0;
+}
+void Csr::matvec(const double* x, double* y, int threads) const {
+    parallel_for(nrows, threads, [&](int64_t b, int64_t e, int) {
+        for (int64_t i = b; i < e; ++i) {
+            double s = 0;
+            for (int64_t p = ptr[i]; p < ptr[i + 1]; ++p) s += val[p] * x[col[p]];
+            y[i] = s;
+        }
+    });
+}
+Csr transpose(const Csr& A) {
+    Csr T;
+    T.nrows = A.ncols;
+    T.ncols = A.nrows;
+    T.ptr.assign(T.nrows + 1, 0);
+    for (int64_t p = 0; p < (int64_t)A.col.size(); ++p) T.ptr[A.col[p] + 1]++;
+    for (int64_t i = 0; i < T.nrows; ++i) T.ptr[i + 1] += T.ptr[i];
+    T.col.resize(A.col.size());
+    T.val.resize(A.col.size());
+    std::vector<int64_t> pos(T.ptr.begin(), T.ptr.end() - 1);
+    for (int64_t i = 0; i < A.nrows; ++i)
+        for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
+            int64_t q = pos[A.col[p]]++;
+            T.col[q] = i;
+            T.val[q] = A.val[p];
+        }
+    return T;
+}
+Csr spgemm(const Csr& A, const Csr& B, int threads) {
+    Csr C;
+    C.nrows = A.nrows;
+    C.ncols = B.ncols;
+    std::vector<std::vector<int64_t>> rc(A.nrows);
+    std::vector<std::vector<double>> rv(A.nrows);
+    std::vector<std::vector<double>> acc(threads, std::vector<double>());
+    std::vector<std::vector<int64_t>> mark(threads);
+    parallel_for(A.nrows, threads, [&](int64_t b, int64_t e, int t) {
+        auto& ac = acc[t];
+        auto& mk = mark[t];
+        if (ac.empty()) {
+            ac.assign(B.ncols, 0.0);
+            mk.assign(B.ncols, -1);
+        }
+        std::vector<int64_t> cols;
+        for (int64_t i = b; i < e; ++i) {
+            cols.clear();
+            for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
+                int64_t k = A.col[p];
+                double a = A.val[p];
+                for (int64_t q = B.ptr[k]; q < B.ptr[k + 1]; ++q) {
+                    int64_t j = B.col[q];
+                    if (mk[j] != i) {
+                        mk[j] = i;
+                        ac[j] = 0.0;
+                        cols.push_back(j);
+                    }
+                    ac[j] += a * B.val[q];
+                }
+            }
+            std::sort(cols.begin(), cols.end());
+            rc[i] = cols;
+            rv[i].resize(cols.size());
+            for (size_t q = 0; q < cols.size(); ++q) rv[i][q] = ac[cols[q]];
+        }
+    });
+    C.ptr.assign(C.nrows + 1, 0);
+    for (int64_t i = 0; i < C.nrows; ++i) C.ptr[i + 1] = C.ptr[i] + (int64_t)rc[i].size();
+    C.col.resize(C.ptr.back());
+    C.val.resize(C.ptr.back());
+    parallel_for(C.nrows, threads, [&](int64_t b, int64_t e, int) {
+        for (int64_t i = b; i < e; ++i) {
+            std::copy(rc[i].begin(), rc[i].end(), C.col.begin() + C.ptr[i]);
+            std::copy(rv[i].begin(), rv[i].end(), C.val.begin() + C.ptr[i]);
+        }
+    });
+    return C;
+}
+static Csr symmetrize(const Csr& A, int threads) {
+    // (A + A^T)/2 on the union pattern
+    Csr T = transpose(A);
+    Csr S;
+    S.nrows = A.nrows;
+    S.ncols = A.ncols;
+    std::vector<std::vector<int64_t>> rc(A.nrows);
+    std::vector<std::vector<double>> rv(A.nrows);
+    parallel_for(A.nrows, threads, [&](int64_t b, int64_t e, int) {
+        for (int64_t i = b; i < e; ++i) {
+            int64_t p = A.ptr[i], pe = A.ptr[i + 1], q = T.ptr[i], qe = T.ptr[i + 1];
+            while (p < pe || q < qe) {
+                int64_t cp = p < pe ? A.col[p] : INT64_MAX, cq = q < qe ? T.col[q] : INT64_MAX;
+                if (cp == cq) {
+                    rc[i].push_back(cp);
+                    rv[i].push_back(0.5 * (A.val[p] + T.val[q]));
+                    ++p;
+                    ++q;
+                } else if (cp < cq) {
+                    rc[i].push_back(cp);
+                    rv[i].push_back(0.5 * A.val[p]);
+                    ++p;
+                } else {
+                    rc[i].push_back(cq);
+                    rv[i].push_back(0.5 * T.val[q]);
+                    ++q;
+                }
+            }
+        }
+    });
+    S.ptr.assign(S.nrows + 1, 0);
+    for (int64_t i = 0; i < S.nrows; ++i) S.ptr[i + 1] = S.ptr[i] + (int64_t)rc[i].size();
+    S.col.resize(S.ptr.back());
+    S.val.resize(S.ptr.back());
+    for (int64_t i = 0; i < S.nrows; ++i) {
+        std::copy(rc[i].begin(), rc[i].end(), S.col.begin() + S.ptr[i]);
+        std::copy(rv[i].begin(), rv[i].end(), S.val.begin() + S.ptr[i]);
+    }
+    return S;
+}
+
+// ============================================================== set-up stages
+namespace {
+
+struct Builder {
+    Setup& S;
+    Lattice& L;
+    int threads;
+    explicit Builder(Setup& s, int th) : S(s), L(s.L), threads(th) {}
+
+    std::vector<F1> F1loc;
+    std::vector<bool> isgrad;
+    std::vector<std::vector<int32_t>> pat1;   // S(M1) rows (tet sharing)
+
+    int64_t tet_index(int cx, int cy, int cz, int s) const {
+        return 6 * ((int64_t)cx + (int64_t)L.n * (cy + (int64_t)L.n * cz)) + s;
+    }
+
+    // ---------------------------------------------------------- local blocks
+    void local_blocks() {
+        const int k = L.k;
+        one_forms(k, F1loc, isgrad);
+        RefTet R = ref_tet(0, L.h);
+        const int n1 = L.n1;
+        S.M1loc.assign((size_t)n1 * n1, 0.0);
+        for (int i = 0; i < n1; ++i)
+            for (int j = 0; j < n1; ++j) S.M1loc[(size_t)i * n1 + j] = mass1(F1loc[i], F1loc[j], R);
+        // curl-carrying 2-forms in local 2-form order: per face W2 then curls of the face's
+        // non-gradient 1-forms, then curls of the cell 1-forms
+        std::vector<F2> F2a;
+        std::vector<std::vector<std::pair<int, int>>> crow;  // integer C rows (col, value)
+        const int per_f1 = k * (k - 1);
+        int le_of[4][4];
+        for (int le = 0; le < 6; ++le) {
+            le_of[LEDGE[le][0]][LEDGE[le][1]] = le;
+        }
+        for (int lf = 0; lf < 4; ++lf) {
+            int a = LFACE[lf][0], b = LFACE[lf][1], c = LFACE[lf][2];
+            F2a.push_back(whitney2(a, b, c));
+            // Stokes on the face: circulation of w_e around the oriented boundary
+            crow.push_back({{le_of[b][c] * k, 1}, {le_of[a][c] * k, -1}, {le_of[a][b] * k, 1}});
+            for (int j = 0; j < per_f1; ++j) {
+                int col = 6 * k + lf * per_f1 + j;
+                if (isgrad[col]) continue;
+                F2a.push_back(curl(F1loc[col]));
+                crow.push_back({{col, 1}});
+            }
+        }
+        if (k >= 3)
+            for (int j = 0; j < 3; ++j) {
+                int col = 6 * k + 4 * per_f1 + j;
+                F2a.push_back(curl(F1loc[col]));
+                crow.push_back({{col, 1}});
+            }
+        if ((int)F2a.size() != L.n2a) throw std::runtime_error("internal: 2-form count mismatch");
+        const int n2a = L.n2a;
+        S.M2aloc.assign((size_t)n2a * n2a, 0.0);
+        for (int i = 0; i < n2a; ++i)
+            for (int j = 0; j < n2a; ++j) S.M2aloc[(size_t)i * n2a + j] = mass2(F2a[i], F2a[j], R);
+        S.Cloc.assign((size_t)n2a * n1, 0);
+        for (int r = 0; r < n2a; ++r)
+            for (auto& [c, v] : crow[r]) S.Cloc[(size_t)r * n1 + c] = v;
+        S.Wloc.assign((size_t)n1 * n2a, 0.0);
+        for (int i = 0; i < n1; ++i)
+            for (int r = 0; r < n2a; ++r) {
+                double s = 0;
+                for (int q = 0; q < n2a; ++q) s += S.Cloc[(size_t)q * n1 + i] * S.M2aloc[(size_t)q * n2a + r];
+                S.Wloc[(size_t)i * n2a + r] = s;
+            }
+    }
+
+    // ---------------------------------------------------------- M1(eps), pattern S(M1)
+    void assemble_M1() {
+        const int64_t N1 = L.N1;
+        const int n1 = L.n1;
+        std::vector<std::vector<int64_t>> rc(N1);
+        std::vector<std::vector<double>> rv(N1);
+        parallel_for(N1, threads, [&](int64_t b, int64_t e, int) {
+            std::vector<std::pair<int64_t, double>> acc;
+            for (int64_t g = b; g < e; ++g) {
+                int c, v[3];
+                L.decode1(g, &c, v);
+                acc.clear();
+                for (const Incidence& in : L.inc1[c]) {
+                    int cx = v[0] + in.dcube[0], cy = v[1] + in.dcube[1], cz = v[2] + in.dcube[2];
+                    int64_t t = tet_index(cx, cy, cz, in.shape);
+                    double ept = S.eps[t];
+                    for (int r = 0; r < n1; ++r) {
+                        const LocalDof& Ld = L.loc1[in.shape][r];
+                        int64_t gj = L.index1(Ld.cls, cx + Ld.off[0], cy + Ld.off[1], cz + Ld.off[2]);
+                        if (gj < 0) continue;
+                        acc.push_back({gj, ept * S.M1loc[(size_t)in.loc * n1 + r]});
+                    }
+                }
+                std::sort(acc.begin(), acc.end(),
+                          [](const std::pair<int64_t, double>& x, const std::pair<int64_t, double>& y) {
+                              return x.first < y.first;
+                          });
+                for (size_t p = 0; p < acc.size();) {
+                    int64_t j = acc[p].first;
+                    double s = 0;
+                    while (p < acc.size() && acc[p].first == j) s += acc[p++].second;
+                    rc[g].push_back(j);
+                    rv[g].push_back(s);
+                }
+            }
+        });
+        Csr& M = S.M1;
+        M.nrows = M.ncols = N1;
+        M.ptr.assign(N1 + 1, 0);
+        for (int64_t i = 0; i < N1; ++i) M.ptr[i + 1] = M.ptr[i] + (int64_t)rc[i].size();
+        M.col.resize(M.ptr.back());
+        M.val.resize(M.ptr.back());
+        for (int64_t i = 0; i < N1; ++i) {
+            std::copy(rc[i].begin(), rc[i].end(), M.col.begin() + M.ptr[i]);
+            std::copy(rv[i].begin(), rv[i].end(), M.val.begin() + M.ptr[i]);
+        }
+    }
+
+    // structural pattern rows (int32): S(1), S(M1) or S(M1^2)
+    void patterns(int kind, std::vector<std::vector<int32_t>>& P) {
+        const int64_t N1 = L.N1;
+        P.assign(N1, {});
+        if (kind == YGM_PAT_DIAG) {
+            for (int64_t i = 0; i < N1; ++i) P[i] = {(int32_t)i};
+            return;
+        }
+        std::vector<std::vector<int32_t>> P1(N1);
+        for (int64_t i = 0; i < N1; ++i) {
+            P1[i].resize(S.M1.ptr[i + 1] - S.M1.ptr[i]);
+            for (int64_t p = S.M1.ptr[i]; p < S.M1.ptr[i + 1]; ++p) P1[i][p - S.M1.ptr[i]] = (int32_t)S.M1.col[p];
+        }
+        if (kind == YGM_PAT_SM1) {
+            P = std::move(P1);
+            return;
+        }
+        parallel_for(N1, threads, [&](int64_t b, int64_t e, int) {
+            std::vector<int32_t> u;
+            for (int64_t i = b; i < e; ++i) {
+                u.clear();
+                for (int32_t m : P1[i]) u.insert(u.end(), P1[m].begin(), P1[m].end());
+                std::sort(u.begin(), u.end());
+                u.erase(std::unique(u.begin(), u.end()), u.end());
+                P[i] = u;
+            }
+        });
+    }
+    static constexpr int YGM_PAT_DIAG = 1, YGM_PAT_SM1 = 2, YGM_PAT_SM1SQ = 3;
+
+    // ---------------------------------------------------------- entity-orthonormalised basis T
+    // T is block diagonal over the mesh entities: the DoFs g of one edge, face or cell are
+    // replaced by (M1[g,g])^(-1/2) times themselves (symmetric Lowdin orthonormalisation).
+    Csr ortho_T() {
+        const int64_t N1 = L.N1;
+        const Csr& Mp = S.M1;
+        // entity groups: DoFs of the same class kind/shape/anchor; classes of an entity are
+        // consecutive in j, so group = all classes with the same (kind, shape) at one anchor
+        std::vector<std::vector<int64_t>> groups;
+        {
+            std::map<std::pair<int, int>, std::vector<int>> ent;  // (kind, shape) -> classes
+            for (int c = 0; c < (int)L.c1.size(); ++c) ent[{L.c1[c].kind, L.c1[c].shape}].push_back(c);
+            for (auto& [key, cl] : ent) {
+                const Box& b0 = L.c1[cl[0]].box;
+                for (int64_t r = 0; r < b0.size; ++r) {
+                    std::vector<int64_t> g;
+                    for (int c : cl) g.push_back(L.c1[c].box.offset + r);
+                    groups.push_back(g);
+                }
+            }
+        }
+        std::vector<std::vector<std::pair<int64_t, double>>> lrows(N1);
+        parallel_for((int64_t)groups.size(), threads, [&](int64_t b, int64_t e, int) {
+            std::vector<double> A, w, V;
+            for (int64_t gi = b; gi < e; ++gi) {
+                auto& g = groups[gi];
+                int m = (int)g.size();
+                A.assign((size_t)m * m, 0.0);
+                for (int a = 0; a < m; ++a)
+                    for (int c = 0; c < m; ++c) A[(size_t)a * m + c] = Mp.get(g[a], g[c]);
+                jacobi_eigen(m, A, w, V);
+                for (int a = 0; a < m; ++a)
+                    for (int c = 0; c < m; ++c) {
+                        double s = 0;
+                        for (int q = 0; q < m; ++q) s += V[(size_t)a * m + q] * V[(size_t)c * m + q] / std::sqrt(w[q]);
+                        lrows[g[a]].push_back({g[c], s});
+                    }
+            }
+        });
+        Csr Lw;
+        Lw.nrows = Lw.ncols = N1;
+        Lw.ptr.assign(N1 + 1, 0);
+        for (int64_t i = 0; i < N1; ++i) {
+            std::sort(lrows[i].begin(), lrows[i].end());
+            Lw.ptr[i + 1] = Lw.ptr[i] + (int64_t)lrows[i].size();
+        }
+        for (int64_t i = 0; i < N1; ++i)
+            for (auto& [c, v] : lrows[i]) {
+                Lw.col.push_back(c);
+                Lw.val.push_back(v);
+            }
+        return Lw;
+    }
+
+    // ---------------------------------------------------------- SPAI (Eq. NormalEqSolve)
+    // Columns l: q(I_l) = [M(:,I)^T M(:,I)]^-1 M(:,I)^T 1_l with M symmetric, so the normal
+    // matrix is accumulated row by row of M(:, I) (only its nonzero rows contribute).
+    Csr spai(const Csr& M, const std::vector<std::vector<int32_t>>& P) {
+        const int64_t N = M.nrows;
+        std::vector<std::vector<double>> qcol(N);
+        std::vector<std::vector<int32_t>> markv(threads), rmark(threads);
+        std::atomic<bool> fail(false);
+        parallel_for(N, threads, [&](int64_t b, int64_t e, int t) {
+            auto& mk = markv[t];
+            if (mk.empty()) mk.assign(N, -1);
+            std::vector<double> G, rhs;
+            struct Trip {
+                int32_t row;
+                int32_t p;
+                double v;
+            };
+            std::vector<Trip> trip, sorted;
+            std::vector<int64_t> rowids;
+            std::vector<int32_t> cnt, pos;
+            for (int64_t l = b; l < e; ++l) {
+                const auto& I = P[l];
+                const int m = (int)I.size();
+                for (int p = 0; p < m; ++p) mk[I[p]] = p;
+                G.assign((size_t)m * m, 0.0);
+                rhs.assign(m, 0.0);
+                // rows r of M(:, I): column I_p of M is row I_p (symmetric).  Group the
+                // nonzeros of M(:, I) by row with a marker array, then add each row's outer product.
+                auto& rm = rmark[t];
+                if (rm.empty()) rm.assign(N, -1);
+                rowids.clear();
+                trip.clear();
+                for (int p = 0; p < m; ++p) {
+                    int64_t ip = I[p];
+                    for (int64_t q = M.ptr[ip]; q < M.ptr[ip + 1]; ++q) {
+                        int64_t r = M.col[q];
+                        if (rm[r] < 0) {
+                            rm[r] = (int32_t)rowids.size();
+                            rowids.push_back(r);
+                        }
+                        trip.push_back({rm[r], p, M.val[q]});
+                    }
+                }
+                cnt.assign(rowids.size() + 1, 0);
+                for (auto& x : trip) cnt[x.row + 1]++;
+                for (size_t i = 0; i < rowids.size(); ++i) cnt[i + 1] += cnt[i];
+                sorted.resize(trip.size());
+                pos.assign(cnt.begin(), cnt.end() - 1);
+                for (auto& x : trip) sorted[pos[x.row]++] = x;
+                for (size_t rr = 0; rr < rowids.size(); ++rr) {
+                    for (int32_t ia = cnt[rr]; ia < cnt[rr + 1]; ++ia) {
+                        const int pa = sorted[ia].p;
+                        const double va = sorted[ia].v;
+                        for (int32_t ib = cnt[rr]; ib < cnt[rr + 1]; ++ib) {
+                            const int pb = sorted[ib].p;
+                            if (pb <= pa) G[(size_t)pa * m + pb] += va * sorted[ib].v;
+                        }
+                    }
+                }
+                for (int64_t r : rowids) rm[r] = -1;
+                for (int pa = 0; pa < m; ++pa)
+                    for (int pb = pa + 1; pb < m; ++pb) G[(size_t)pa * m + pb] = G[(size_t)pb * m + pa];
+                // M(:, I)^T 1_l = M(l, I)
+                for (int64_t q = M.ptr[l]; q < M.ptr[l + 1]; ++q) {
+                    int64_t c = M.col[q];
+                    if (mk[c] >= 0) rhs[mk[c]] = M.val[q];
+                }
+                if (!cholesky_solve(m, G.data(), rhs.data(), 1)) fail = true;
+                qcol[l] = rhs;
+                for (int p = 0; p < m; ++p) mk[I[p]] = -1;
+            }
+        });
+        if (fail) throw std::runtime_error("SPAI normal matrix not SPD");
+        // Q(i, l) = qcol[l][pos of i in I_l]; build CSR of Q^T (rows = columns l), then symmetrise
+        Csr Qt;
+        Qt.nrows = Qt.ncols = N;
+        Qt.ptr.assign(N + 1, 0);
+        for (int64_t l = 0; l < N; ++l) Qt.ptr[l + 1] = Qt.ptr[l] + (int64_t)P[l].size();
+        Qt.col.resize(Qt.ptr.back());
+        Qt.val.resize(Qt.ptr.back());
+        for (int64_t l = 0; l < N; ++l)
+            for (size_t p = 0; p < P[l].size(); ++p) {
+                Qt.col[Qt.ptr[l] + p] = P[l][p];
+                Qt.val[Qt.ptr[l] + p] = qcol[l][p];
+            }
+        return symmetrize(Qt, threads);
+    }
+
+    // ---------------------------------------------------------- P2 = C^T M2 C, row-parallel
+    std::vector<double> P2loc;
+    void make_P2loc() {
+        const int n1 = L.n1, n2a = L.n2a;
+        P2loc.assign((size_t)n1 * n1, 0.0);
+        for (int i = 0; i < n1; ++i)
+            for (int j = 0; j < n1; ++j) {
+                double s = 0;
+                for (int r = 0; r < n2a; ++r) s += S.Wloc[(size_t)i * n2a + r] * S.Cloc[(size_t)r * n1 + j];
+                P2loc[(size_t)i * n1 + j] = s;
+            }
+    }
+    void P2_matvec(const double* x, double* y) {
+        const int n1 = L.n1;
+        parallel_for(L.N1, threads, [&](int64_t b, int64_t e, int) {
+            for (int64_t g = b; g < e; ++g) {
+                int c, v[3];
+                L.decode1(g, &c, v);
+                double s = 0;
+                for (const Incidence& in : L.inc1[c]) {
+                    int cx = v[0] + in.dcube[0], cy = v[1] + in.dcube[1], cz = v[2] + in.dcube[2];
+                    double im = 1.0 / S.mu[tet_index(cx, cy, cz, in.shape)];
+                    double t = 0;
+                    for (int r = 0; r < n1; ++r) {
+                        const LocalDof& Ld = L.loc1[in.shape][r];
+                        int64_t gj = L.index1(Ld.cls, cx + Ld.off[0], cy + Ld.off[1], cz + Ld.off[2]);
+                        if (gj >= 0) t += P2loc[(size_t)in.loc * n1 + r] * x[gj];
+                    }
+                    s += im * t;
+                }
+                y[g] = s;
+            }
+        });
+    }
+
+    // ---------------------------------------------------------- Lanczos helpers
+    // Symmetric Lanczos (three-term recurrence) for op self-adjoint in <x, y> = x^T B y;
+    // returns the (smallest, largest) Ritz value.  Extreme Ritz values are found by Sturm
+    // bisection on the tridiagonal matrix every 10 steps; the loop stops when both settle.
+    static int sturm_count(const std::vector<double>& a, const std::vector<double>& b, double x) {
+        int cnt = 0;
+        double q = a[0] - x;
+        if (q < 0) ++cnt;
+        for (size_t i = 1; i < a.size(); ++i) {
+            double d = std::fabs(q) < 1e-300 ? 1e-300 : q;
+            q = a[i] - x - b[i - 1] * b[i - 1] / d;
+            if (q < 0) ++cnt;
+        }
+        return cnt;  // number of eigenvalues < x
+    }
+    static std::pair<double, double> tridiag_extremes(const std::vector<double>& a, const std::vector<double>& b) {
+        double lo = a[0], hi = a[0];
+        for (size_t i = 0; i < a.size(); ++i) {
+            double r = (i > 0 ? std::fabs(b[i - 1]) : 0) + (i + 1 < a.size() ? std::fabs(b[i]) : 0);
+            lo = std::min(lo, a[i] - r);
+            hi = std::max(hi, a[i] + r);
+        }
+        const int n = (int)a.size();
+        double l = lo, h = hi;
+        for (int it = 0; it < 200 && h - l > 1e-15 * std::max(std::fabs(l), std::fabs(h)); ++it) {
+            double m = 0.5 * (l + h);
+            if (sturm_count(a, b, m) >= 1) h = m; else l = m;
+        }
+        double emin = 0.5 * (l + h);
+        l = lo;
+        h = hi;
+        for (int it = 0; it < 200 && h - l > 1e-15 * std::max(std::fabs(l), std::fabs(h)); ++it) {
+            double m = 0.5 * (l + h);
+            if (sturm_count(a, b, m) >= n) h = m; else l = m;
+        }
+        return {emin, 0.5 * (l + h)};
+    }
+    std::pair<double, double> lanczos(const std::function<void(const double*, double*)>& op,
+                                      const std::function<void(const double*, double*)>& Bop, int iters) {
+        const int64_t N = L.N1;
+        std::vector<double> v(N), Bv(N), w(N), Bw(N), vp(N, 0.0);
+        uint64_t st = 0x12345678ULL;
+        for (int64_t i = 0; i < N; ++i) {
+            st = st * 6364136223846793005ULL + 1442695040888963407ULL;
+            v[i] = (double)(st >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+        }
+        Bop(v.data(), Bv.data());
+        double nrm = std::sqrt(std::inner_product(v.begin(), v.end(), Bv.begin(), 0.0));
+        for (int64_t i = 0; i < N; ++i) {
+            v[i] /= nrm;
+            Bv[i] /= nrm;
+        }
+        std::vector<double> al, be;
+        double beta = 0, pmin = 0, pmax = 0;
+        std::pair<double, double> ext{0, 0};
+        const int m = (int)std::min<int64_t>(iters, N);
+        for (int it = 0; it < m; ++it) {
+            op(v.data(), w.data());
+            for (int64_t i = 0; i < N; ++i) w[i] -= beta * vp[i];
+            double a = std::inner_product(w.begin(), w.end(), Bv.begin(), 0.0);
+            for (int64_t i = 0; i < N; ++i) w[i] -= a * v[i];
+            al.push_back(a);
+            Bop(w.data(), Bw.data());
+            beta = std::sqrt(std::max(0.0, std::inner_product(w.begin(), w.end(), Bw.begin(), 0.0)));
+            if ((it + 1) % 10 == 0 || it + 1 == m || beta <= 1e-300) {
+                ext = tridiag_extremes(al, be);
+                if (it > 30 && std::fabs(ext.second - pmax) <= 1e-13 * std::fabs(ext.second) &&
+                    std::fabs(ext.first - pmin) <= 1e-9 * std::fabs(ext.second))
+                    break;
+                pmin = ext.first;
+                pmax = ext.second;
+            }
+            if (beta <= 1e-300) break;
+            be.push_back(beta);
+            for (int64_t i = 0; i < N; ++i) {
+                vp[i] = v[i];
+                v[i] = w[i] / beta;
+                Bv[i] = Bw[i] / beta;
+            }
+        }
+        return ext;
+    }
+
+    // ---------------------------------------------------------- stencil tables
+    void stencils(int pat) {
+        const int nc = (int)L.c1.size();
+        std::vector<std::vector<Nbr>> s1(nc), sp(nc);
+        for (int c = 0; c < nc; ++c) {
+            std::vector<Nbr> u;
+            for (const Incidence& in : L.inc1[c])
+                for (int r = 0; r < L.n1; ++r) {
+                    const LocalDof& Ld = L.loc1[in.shape][r];
+                    u.push_back(Nbr{Ld.cls, {in.dcube[0] + Ld.off[0], in.dcube[1] + Ld.off[1], in.dcube[2] + Ld.off[2]}});
+                }
+            std::sort(u.begin(), u.end());
+            u.erase(std::unique(u.begin(), u.end()), u.end());
+            s1[c] = u;
+        }
+        for (int c = 0; c < nc; ++c) {
+            if (pat == YGM_PAT_DIAG) {
+                sp[c] = {Nbr{c, {0, 0, 0}}};
+            } else if (pat == YGM_PAT_SM1) {
+                sp[c] = s1[c];
+            } else {
+                std::vector<Nbr> u;
+                for (const Nbr& a : s1[c])
+                    for (const Nbr& b : s1[a.cls]) u.push_back(Nbr{b.cls, {a.d[0] + b.d[0], a.d[1] + b.d[1], a.d[2] + b.d[2]}});
+                std::sort(u.begin(), u.end());
+                u.erase(std::unique(u.begin(), u.end()), u.end());
+                sp[c] = u;
+            }
+        }
+        // upper: neighbour at or after (0, c) in the (dz, dy, dx, class) order
+        std::vector<std::vector<Nbr>> up(nc);
+        for (int c = 0; c < nc; ++c) {
+            Nbr self{c, {0, 0, 0}};
+            for (const Nbr& a : sp[c])
+                if (!(a < self)) up[c].push_back(a);
+        }
+        S.st_begin.assign(nc + 1, 0);
+        S.n_upper.assign(nc, 0);
+        S.st_slots.clear();
+        for (int c = 0; c < nc; ++c) {
+            S.n_upper[c] = (int)up[c].size();
+            for (size_t s = 0; s < up[c].size(); ++s) {
+                Setup::StencilSlot sl{};
+                sl.cls = up[c][s].cls;
+                for (int a = 0; a < 3; ++a) sl.d[a] = (int8_t)up[c][s].d[a];
+                sl.upper = 1;
+                sl.slot = (int)s;
+                S.st_slots.push_back(sl);
+            }
+            Nbr self{c, {0, 0, 0}};
+            for (const Nbr& a : sp[c]) {
+                if (!(a < self)) continue;
+                Nbr back{c, {-a.d[0], -a.d[1], -a.d[2]}};
+                auto& U = up[a.cls];
+                auto it = std::lower_bound(U.begin(), U.end(), back);
+                if (it == U.end() || !(*it == back)) throw std::runtime_error("internal: stencil not symmetric");
+                Setup::StencilSlot sl{};
+                sl.cls = a.cls;
+                for (int q = 0; q < 3; ++q) sl.d[q] = (int8_t)a.d[q];
+                sl.upper = 0;
+                sl.slot = (int)(it - U.begin());
+                S.st_slots.push_back(sl);
+            }
+            S.st_begin[c + 1] = (int)S.st_slots.size();
+        }
+        // pack upper values: [class][slot][box index]
+        S.qoff.assign(nc + 1, 0);
+        for (int c = 0; c < nc; ++c) S.qoff[c + 1] = S.qoff[c] + (int64_t)S.n_upper[c] * L.c1[c].box.size;
+        S.qvals.assign(S.qoff[nc], 0.0);
+        std::atomic<int64_t> missing(0);
+        for (int c = 0; c < nc; ++c) {
+            const Box& b = L.c1[c].box;
+            parallel_for(b.size, threads, [&](int64_t lo, int64_t hi, int) {
+                for (int64_t r = lo; r < hi; ++r) {
+                    int v0 = (int)(r % b.num[0]) + b.lo[0];
+                    int v1 = (int)((r / b.num[0]) % b.num[1]) + b.lo[1];
+                    int v2 = (int)(r / ((int64_t)b.num[0] * b.num[1])) + b.lo[2];
+                    int64_t gi = b.offset + r;
+                    for (int s = 0; s < S.n_upper[c]; ++s) {
+                        const Nbr& a = up[c][s];
+                        int64_t gj = L.index1(a.cls, v0 + a.d[0], v1 + a.d[1], v2 + a.d[2]);
+                        S.qvals[S.qoff[c] + (int64_t)s * b.size + r] = gj >= 0 ? S.Q1.get(gi, gj) : 0.0;
+                    }
+                }
+            });
+        }
+        (void)missing;
+    }
+};
+
+}  // namespace
+
+int build_setup(Setup& S, int n, double side, int k, const double* eps, const double* mu, int q1_pattern,
+                int threads_in) {
+    const int threads = default_threads(threads_in);
+    const bool verbose = std::getenv("YGM_VERBOSE") != nullptr;
+    auto tic = std::chrono::steady_clock::now();
+    auto stage = [&](const char* what) {
+        if (!verbose) return;
+        auto now = std::chrono::steady_clock::now();
+        std::fprintf(stderr, "[ygm setup] %-28s %8.2f s\n", what, std::chrono::duration<double>(now - tic).count());
+        tic = now;
+    };
+    try {
+        S.L.build(n, k, side);
+        const int64_t T = 6LL * n * n * n;
+        if (eps)
+            S.eps.assign(eps, eps + T);
+        else
+            S.eps.assign(T, 1.0);
+        if (mu)
+            S.mu.assign(mu, mu + T);
+        else
+            S.mu.assign(T, 1.0);
+        for (int64_t t = 0; t < T; ++t)
+            if (!(S.eps[t] > 0) || !(S.mu[t] > 0) || !std::isfinite(S.eps[t]) || !std::isfinite(S.mu[t])) {
+                S.err = "eps and mu must be finite and positive";
+                return -1;
+            }
+        Builder B(S, threads);
+        B.local_blocks();
+        stage("local blocks");
+        B.assemble_M1();
+        stage("assemble M1");
+        int pat = q1_pattern == 0 ? (k == 1 ? Builder::YGM_PAT_SM1 : Builder::YGM_PAT_SM1SQ) : q1_pattern;
+        if (pat < 1 || pat > 3) {
+            S.err = "unknown q1_pattern";
+            return -1;
+        }
+        S.q1_pattern = pat;
+        S.ortho = (k >= 2 && pat == Builder::YGM_PAT_SM1SQ);
+        std::vector<std::vector<int32_t>> P;
+        B.patterns(pat, P);
+        stage("patterns");
+        if (S.ortho) {
+            Csr Tm = B.ortho_T();
+            stage("ortho basis T");
+            Csr Mp = spgemm(spgemm(Tm, S.M1, threads), transpose(Tm), threads);
+            stage("M' = T M1 T^T");
+            Csr Qp = B.spai(Mp, P);
+            stage("SPAI columns");
+            Csr Q1 = spgemm(spgemm(transpose(Tm), Qp, threads), Tm, threads);
+            S.Q1 = symmetrize(Q1, threads);
+            stage("Q1 = T^T Q' T");
+        } else {
+            S.Q1 = B.spai(S.M1, P);
+            stage("SPAI columns");
+        }
+        // SPD check (Sec. 5.1, practical considerations) by Lanczos on Q1
+        const int64_t N1 = S.L.N1;
+        auto qop = [&](const double* x, double* y) { S.Q1.matvec(x, y, threads); };
+        auto idop = [&](const double* x, double* y) { std::copy(x, x + N1, y); };
+        auto mm = B.lanczos(qop, idop, 300);
+        stage("SPD check (Lanczos)");
+        S.lmin = mm.first;
+        S.lmax = mm.second;
+        S.shift = 0;
+        if (S.lmin <= 0) {
+            S.shift = std::fabs(S.lmin) + 1e-12 * S.lmax;
+            for (int64_t i = 0; i < N1; ++i)
+                for (int64_t p = S.Q1.ptr[i]; p < S.Q1.ptr[i + 1]; ++p)
+                    if (S.Q1.col[p] == i) S.Q1.val[p] += S.shift;
+        }
+        // CFL: omega_max^2 = lambda_max(Q1 P2); P2 Q1 is self-adjoint in the Q1 inner product
+        B.make_P2loc();
+        std::vector<double> tmp(N1);
+        auto kop = [&](const double* x, double* y) {
+            S.Q1.matvec(x, tmp.data(), threads);
+            B.P2_matvec(tmp.data(), y);
+        };
+        auto cfl = B.lanczos(kop, qop, 400);
+        S.omega_max_sq = cfl.second;
+        S.tau_cfl = 2.0 / std::sqrt(S.omega_max_sq);
+        stage("CFL (Lanczos)");
+        B.stencils(pat);
+        stage("stencils + packing");
+    } catch (const std::exception& ex) {
+        S.err = ex.what();
+        return -3;
+    }
+    return 0;
+}
+
+// ============================================================== sources and projections
+// Gauss-Legendre nodes and weights on [-1, 1] by Newton iteration on P_n (Golub-Welsch not needed
+// for the small orders used here).
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+    x.resize(n);
+    w.resize(n);
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            double dp = n * (z * p1 - p0) / (z * z - 1);
+            double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) {
+                // refresh derivative at the converged node for the weight
+                p0 = 1;
+                p1 = z;
+                for (int k = 2; k <= n; ++k) {
+                    double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+                    p0 = p1;
+                    p1 = p2;
+                }
+                dp = n * (z * p1 - p0) / (z * z - 1);
+                x[n - 1 - i] = z;
+                w[n - 1 - i] = 2.0 / ((1 - z * z) * dp * dp);
+                break;
+            }
+        }
+    }
+}
+static int locate(const Lattice& L, const double x[3], int cube[3], int* shape, double lam[4]) {
+    double r[3];
+    for (int a = 0; a < 3; ++a) {
+        double u = x[a] / L.h;
+        int c = (int)std::floor(u);
+        c = std::max(0, std::min(L.n - 1, c));
+        cube[a] = c;
+        r[a] = u - c;
+    }
+    for (int s = 0; s < 6; ++s) {
+        int a1 = TET_D[s][0] == 1 ? 0 : (TET_D[s][0] == 2 ? 1 : 2);
+        int d21 = TET_D[s][1] ^ TET_D[s][0];
+        int a2 = d21 == 1 ? 0 : (d21 == 2 ? 1 : 2);
+        int a3 = 3 - a1 - a2;
+        if (r[a1] >= r[a2] - 1e-14 && r[a2] >= r[a3] - 1e-14) {
+            *shape = s;
+            // barycentric coordinates along the chain: l0 = 1 - r1, l1 = r1 - r2, l2 = r2 - r3, l3 = r3
+            lam[0] = 1.0 - r[a1];
+            lam[1] = r[a1] - r[a2];
+            lam[2] = r[a2] - r[a3];
+            lam[3] = r[a3];
+            return 0;
+        }
+    }
+    return -1;
+}
+
+int dipole_weights(const Setup& S, const double x[3], const double d[3], std::vector<int64_t>& dofs,
+                   std::vector<double>& w) {
+    const Lattice& L = S.L;
+    int cube[3], shape;
+    double lam[4];
+    if (locate(L, x, cube, &shape, lam)) return -1;
+    std::vector<F1> F;
+    std::vector<bool> ig;
+    one_forms(L.k, F, ig);
+    RefTet R = ref_tet(shape, L.h);
+    int64_t t = 6 * ((int64_t)cube[0] + (int64_t)L.n * (cube[1] + (int64_t)L.n * cube[2])) + shape;
+    std::vector<int64_t> g(L.n1);
+    L.tet_dofs1(t, g.data());
+    dofs.clear();
+    w.clear();
+    for (int r = 0; r < L.n1; ++r) {
+        if (g[r] < 0) continue;
+        double v[3];
+        eval1(F[r], lam, R, v);
+        dofs.push_back(g[r]);
+        w.push_back(v[0] * d[0] + v[1] * d[1] + v[2] * d[2]);
+    }
+    return 0;
+}
+
+int project_E(const Setup& S, void (*E0)(const double*, double*, void*), void* user, std::vector<double>& e0,
+              int threads_in) {
+    const Lattice& L = S.L;
+    const int64_t N1 = L.N1;
+    (void)threads_in;
+    e0.assign(N1, 0.0);
+    if (L.k == 1) {
+        // canonical Whitney interpolant: c_e = int_e E0 . t ds (10-point Gauss-Legendre), e0 = M1 c
+        std::vector<double> gx, gw;
+        gauss_legendre(10, gx, gw);
+        std::vector<double> c(N1, 0.0);
+        for (int cl = 0; cl < (int)L.c1.size(); ++cl) {
+            const Box& b = L.c1[cl].box;
+            int d = EDGE_D[L.c1[cl].shape];
+            for (int64_t r = 0; r < b.size; ++r) {
+                int v[3] = {(int)(r % b.num[0]) + b.lo[0], (int)((r / b.num[0]) % b.num[1]) + b.lo[1],
+                            (int)(r / ((int64_t)b.num[0] * b.num[1])) + b.lo[2]};
+                double xa[3], dx[3];
+                for (int a = 0; a < 3; ++a) {
+                    xa[a] = v[a] * L.h;
+                    dx[a] = bit(d, a) * L.h;
+                }
+                double s = 0;
+                for (int q = 0; q < 10; ++q) {
+                    double u = 0.5 * (gx[q] + 1.0), p[3], E[3];
+                    for (int a = 0; a < 3; ++a) p[a] = xa[a] + u * dx[a];
+                    E0(p, E, user);
+                    s += 0.5 * gw[q] * (E[0] * dx[0] + E[1] * dx[1] + E[2] * dx[2]);
+                }
+                c[b.offset + r] = s;
+            }
+        }
+        S.M1.matvec(c.data(), e0.data(), 1);
+        return 0;
+    }
+    // k >= 2: L2 load vector with a collapsed (Duffy) Gauss-Legendre rule, 6 points per direction
+    std::vector<double> gx6, gw6;
+    gauss_legendre(6, gx6, gw6);
+    std::vector<F1> F;
+    std::vector<bool> ig;
+    one_forms(L.k, F, ig);
+    const int64_t T = 6LL * L.n * L.n * L.n;
+    std::vector<int64_t> g(L.n1);
+    RefTet Rs[6];
+    for (int s = 0; s < 6; ++s) Rs[s] = ref_tet(s, L.h);
+    for (int64_t t = 0; t < T; ++t) {
+        int s = (int)(t % 6);
+        int64_t cube = t / 6;
+        int cc[3] = {(int)(cube % L.n), (int)((cube / L.n) % L.n), (int)(cube / ((int64_t)L.n * L.n))};
+        L.tet_dofs1(t, g.data());
+        const RefTet& R = Rs[s];
+        for (int i1 = 0; i1 < 6; ++i1)
+            for (int i2 = 0; i2 < 6; ++i2)
+                for (int i3 = 0; i3 < 6; ++i3) {
+                    double x1 = 0.5 * (gx6[i1] + 1), x2 = 0.5 * (gx6[i2] + 1), x3 = 0.5 * (gx6[i3] + 1);
+                    double wgt = 0.125 * gw6[i1] * gw6[i2] * gw6[i3] * (1 - x1) * (1 - x1) * (1 - x2) * 6.0 * R.vol;
+                    double lam[4];
+                    lam[1] = x1;
+                    lam[2] = (1 - x1) * x2;
+                    lam[3] = (1 - x1) * (1 - x2) * x3;
+                    lam[0] = 1 - lam[1] - lam[2] - lam[3];
+                    double p[3];
+                    for (int a = 0; a < 3; ++a) {
+                        p[a] = cc[a] * L.h;
+                        for (int i = 0; i < 4; ++i) p[a] += lam[i] * R.X[i][a];
+                    }
+                    double E[3];
+                    E0(p, E, user);
+                    for (int r = 0; r < L.n1; ++r) {
+                        if (g[r] < 0) continue;
+                        double v[3];
+                        eval1(F[r], lam, R, v);
+                        e0[g[r]] += wgt * (v[0] * E[0] + v[1] * E[1] + v[2] * E[2]);
+                    }
+                }
+    }
+    return 0;
+}
+
+}  // namespace ygm

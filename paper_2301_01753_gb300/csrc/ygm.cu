@@ -1,0 +1,975 @@
+// GYM leapfrog step on GB300 (sm_103a): device kernels and the C ABI of include/ygm.h.
+//
+// One step (state e_n, b_{n-1/2}; Eq. YeeLeapfrog in the GYM form of Eq. preYeeFEECEqns):
+//   k_qapply   x = Q1 e_n                                 (shear map Phi^e, Eq. shearMaps)
+//   k_curl_b   b_{n+1/2} = b_{n-1/2} - dt C x              (integer curl, Eq. dIsFiniteDiff)
+//   k_energy   W_n (every K steps, FP64 compensated)       (telescoping invariant of the leapfrog)
+//   k_curlT_e  e_{n+1} = e_n + dt C^T M2 b_{n+1/2}         (shear map Phi^a, Eq. dTIsFiniteDiff)
+//   k_source   e_{n+1} -= dt s(t_{n+1/2}) d . Lambda1(x0)  (current term of Eq. allEOM)
+// Every kernel maps one warp to one x-row of a DoF class (lanes run along x), so all
+// stencil bookkeeping is warp-uniform.  Each output element is written by exactly one
+// lane in a fixed summation order: results are deterministic, no atomics.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/ygm.h"
+#include "builder.h"
+
+namespace {
+
+constexpr int WARPS_PER_BLOCK = 8;
+constexpr int BLOCK = 32 * WARPS_PER_BLOCK;
+
+// ------------------------------------------------------------------ device tables
+struct DCls {            // a DoF class box (1-form or 2-form)
+    int lo[3];
+    int num[3];
+    long long off;       // global index of the box's first DoF
+    long long size;
+    long long qoff;      // 1-forms: first packed Q1 value of the class
+    int st_begin, st_end;    // 1-forms: stencil slots; 2-forms: curl terms
+    int inc_begin, inc_end;  // 1-forms: incident tets
+};
+struct DSlot {           // Q1 stencil slot
+    int cls;
+    int slot;
+    int d[3];
+    int upper;
+};
+struct DTerm {           // one entry of an integer curl row: sign * x[(cls, v + d)]
+    int cls;
+    int d[3];
+    int sign;
+};
+struct DInc {            // a tet incident to a 1-form entity
+    int dcube[3];
+    int shape;
+    int loc;
+};
+struct DLoc2 {           // active local 2-form of a tet shape: class and anchor offset
+    int cls;
+    int off[3];
+};
+struct DRow {            // one x-row of a class
+    int cls;
+    int vy, vz;
+    int rbase;           // compact index of the row's first element inside the class box
+};
+
+struct Tables {
+    const DCls* c1;
+    const DCls* c2;
+    const DSlot* slots;
+    const DTerm* terms;
+    const DInc* inc;
+    const DLoc2* loc2;   // [6][n2a]
+    int n;               // cubes per side
+    int n1, n2a;
+};
+
+__device__ __forceinline__ bool in_box(const DCls& D, int u0, int u1, int u2) {
+    return u0 >= 0 && u1 >= 0 && u2 >= 0 && u0 < D.num[0] && u1 < D.num[1] && u2 < D.num[2];
+}
+
+// ------------------------------------------------------------------ x = Q1 e
+// Q1 is symmetric; each row stores its upper slots (neighbours at or after itself in
+// (dz, dy, dx, class) order) as slot-major arrays over the class box.  A lower entry of row
+// i is the upper entry of the neighbour row j for (class_i, -d): it is read there.
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_qapply(Tables tb, const DRow* __restrict__ rows, int nrows,
+                                                  const real* __restrict__ q, const real* __restrict__ e,
+                                                  real* __restrict__ x) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = blockIdx.x * WARPS_PER_BLOCK + warp;
+    if (row >= nrows) return;
+    const DRow R = rows[row];
+    const DCls C = tb.c1[R.cls];
+    for (int x0 = 0; x0 < C.num[0]; x0 += 32) {
+        const int ix = x0 + lane;                 // x index inside the box
+        const bool act = ix < C.num[0];
+        const int vx = C.lo[0] + ix;
+        real acc = real(0);
+        for (int s = C.st_begin; s < C.st_end; ++s) {
+            const DSlot S = tb.slots[s];
+            const DCls D = tb.c1[S.cls];
+            const int uy = R.vy + S.d[1] - D.lo[1], uz = R.vz + S.d[2] - D.lo[2];
+            if (uy < 0 || uz < 0 || uy >= D.num[1] || uz >= D.num[2]) continue;   // warp-uniform
+            const int ux = vx + S.d[0] - D.lo[0];
+            if (!act || ux < 0 || ux >= D.num[0]) continue;
+            const long long nb = ((long long)uz * D.num[1] + uy) * D.num[0] + ux;
+            const real qv = S.upper ? __ldg(q + C.qoff + (long long)S.slot * C.size + R.rbase + ix)
+                                    : __ldg(q + D.qoff + (long long)S.slot * D.size + nb);
+            acc = fma(qv, __ldg(e + D.off + nb), acc);
+        }
+        if (act) x[C.off + R.rbase + ix] = acc;
+    }
+}
+
+// ------------------------------------------------------------------ b_out = b_in - ctau C x
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_curl_b(Tables tb, const DRow* __restrict__ rows, int nrows,
+                                                  const real* __restrict__ x, const real* b_in, real* b_out,
+                                                  real ctau) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = blockIdx.x * WARPS_PER_BLOCK + warp;
+    if (row >= nrows) return;
+    const DRow R = rows[row];
+    const DCls C = tb.c2[R.cls];
+    for (int x0 = 0; x0 < C.num[0]; x0 += 32) {
+        const int ix = x0 + lane;
+        if (ix >= C.num[0]) break;
+        const int vx = C.lo[0] + ix;
+        real acc = real(0);
+        for (int s = C.st_begin; s < C.st_end; ++s) {
+            const DTerm Tm = tb.terms[s];
+            const DCls D = tb.c1[Tm.cls];
+            const int ux = vx + Tm.d[0] - D.lo[0], uy = R.vy + Tm.d[1] - D.lo[1], uz = R.vz + Tm.d[2] - D.lo[2];
+            if (!in_box(D, ux, uy, uz)) continue;        // PEC: boundary edges carry no DoF
+            const real xv = x[D.off + ((long long)uz * D.num[1] + uy) * D.num[0] + ux];
+            acc += Tm.sign > 0 ? xv : -xv;
+        }
+        const long long g = C.off + R.rbase + ix;
+        b_out[g] = b_in[g] - ctau * acc;
+    }
+}
+
+// ------------------------------------------------------------------ e += ctau C^T M2 b
+// Per tet T containing the entity: (1/mu_T) sum_r W[loc][r] b_T[r], W = C_loc^T M2_loc on the
+// curl-carrying local 2-forms (the divergence part of b never changes: C has no row there).
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_curlT_e(Tables tb, const DRow* __restrict__ rows, int nrows,
+                                                   const real* __restrict__ W, const real* __restrict__ b,
+                                                   const real* __restrict__ inv_mu, real* e, real ctau) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = blockIdx.x * WARPS_PER_BLOCK + warp;
+    if (row >= nrows) return;
+    const DRow R = rows[row];
+    const DCls C = tb.c1[R.cls];
+    const int n = tb.n, n2a = tb.n2a;
+    for (int x0 = 0; x0 < C.num[0]; x0 += 32) {
+        const int ix = x0 + lane;
+        if (ix >= C.num[0]) break;
+        const int vx = C.lo[0] + ix;
+        real acc = real(0);
+        for (int ic = C.inc_begin; ic < C.inc_end; ++ic) {
+            const DInc I = tb.inc[ic];
+            const int cx = vx + I.dcube[0], cy = R.vy + I.dcube[1], cz = R.vz + I.dcube[2];
+            const real* Wr = W + (long long)I.loc * n2a;
+            const DLoc2* L2 = tb.loc2 + I.shape * n2a;
+            real t = real(0);
+            for (int r = 0; r < n2a; ++r) {
+                const DLoc2 Lr = L2[r];
+                const DCls D = tb.c2[Lr.cls];
+                const int ux = cx + Lr.off[0] - D.lo[0], uy = cy + Lr.off[1] - D.lo[1], uz = cz + Lr.off[2] - D.lo[2];
+                if (!in_box(D, ux, uy, uz)) continue;    // PEC: boundary faces carry no DoF
+                t = fma(__ldg(Wr + r), __ldg(b + D.off + ((long long)uz * D.num[1] + uy) * D.num[0] + ux), t);
+            }
+            if (inv_mu) t *= __ldg(inv_mu + 6 * ((long long)cx + (long long)n * (cy + (long long)n * cz)) + I.shape);
+            acc += t;
+        }
+        const long long g = C.off + R.rbase + ix;
+        e[g] = e[g] + ctau * acc;
+    }
+}
+
+// ------------------------------------------------------------------ point-dipole sources
+struct DSrc {
+    double amp, omega, t0, sigma;
+    int begin, end;      // into the (dof, weight) lists
+};
+template <typename real>
+__global__ void k_source(const DSrc* __restrict__ src, int nsrc, const long long* __restrict__ dofs,
+                         const real* __restrict__ w, real* e, double t, double dt) {
+    for (int s = 0; s < nsrc; ++s) {
+        const DSrc S = src[s];
+        const double u = (t - S.t0) / S.sigma;
+        const double amp = S.amp * exp(-u * u) * sin(S.omega * (t - S.t0));
+        for (int i = S.begin + threadIdx.x; i < S.end; i += blockDim.x)
+            e[dofs[i]] = e[dofs[i]] - real(dt * amp) * w[i];
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ FP64 compensated reductions
+struct Neu {
+    double s, c;
+};
+__device__ __forceinline__ Neu neu_add(Neu a, double v) {
+    double t = a.s + v;
+    if (fabs(a.s) >= fabs(v))
+        a.c += (a.s - t) + v;
+    else
+        a.c += (v - t) + a.s;
+    a.s = t;
+    return a;
+}
+__device__ __forceinline__ Neu neu_merge(Neu a, Neu b) {
+    Neu r = neu_add(a, b.s);
+    r.c += b.c;
+    return r;
+}
+__device__ Neu block_reduce(Neu v) {
+    __shared__ double ss[32], sc[32];
+    for (int o = 16; o > 0; o >>= 1) {
+        Neu u{__shfl_down_sync(0xffffffffu, v.s, o), __shfl_down_sync(0xffffffffu, v.c, o)};
+        v = neu_merge(v, u);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        ss[warp] = v.s;
+        sc[warp] = v.c;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        v = lane < nw ? Neu{ss[lane], sc[lane]} : Neu{0.0, 0.0};
+        for (int o = 16; o > 0; o >>= 1) {
+            Neu u{__shfl_down_sync(0xffffffffu, v.s, o), __shfl_down_sync(0xffffffffu, v.c, o)};
+            v = neu_merge(v, u);
+        }
+    }
+    return v;
+}
+
+// partial[blockIdx] = sum_i e_i x_i over a grid-stride slice (fixed order)
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_dot(const real* __restrict__ a, const real* __restrict__ b, long long n,
+                                               double2* part) {
+    Neu v{0.0, 0.0};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        v = neu_add(v, (double)a[i] * (double)b[i]);
+    v = block_reduce(v);
+    if (threadIdx.x == 0) part[blockIdx.x] = make_double2(v.s, v.c);
+}
+
+// partial[blockIdx] = sum_T (1/mu_T) bn_T^T M2a bo_T  (one thread per tet, FP64)
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_tet_quad(Tables tb, const double* __restrict__ M2a, const real* __restrict__ bn,
+                                                    const real* __restrict__ bo, const real* __restrict__ inv_mu,
+                                                    double2* part) {
+    const int n = tb.n, n2a = tb.n2a;
+    const long long T = 6LL * n * n * n;
+    Neu v{0.0, 0.0};
+    double vn[27], vo[27];
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(t % 6);
+        const long long cube = t / 6;
+        const int cx = (int)(cube % n), cy = (int)((cube / n) % n), cz = (int)(cube / ((long long)n * n));
+        for (int r = 0; r < n2a; ++r) {
+            const DLoc2 Lr = tb.loc2[s * n2a + r];
+            const DCls D = tb.c2[Lr.cls];
+            const int ux = cx + Lr.off[0] - D.lo[0], uy = cy + Lr.off[1] - D.lo[1], uz = cz + Lr.off[2] - D.lo[2];
+            if (in_box(D, ux, uy, uz)) {
+                const long long g = D.off + ((long long)uz * D.num[1] + uy) * D.num[0] + ux;
+                vn[r] = (double)bn[g];
+                vo[r] = (double)bo[g];
+            } else {
+                vn[r] = 0.0;
+                vo[r] = 0.0;
+            }
+        }
+        double q = 0.0;
+        for (int r = 0; r < n2a; ++r) {
+            double u = 0.0;
+            for (int c = 0; c < n2a; ++c) u += M2a[r * n2a + c] * vo[c];
+            q += vn[r] * u;
+        }
+        if (inv_mu) q *= (double)inv_mu[t];
+        v = neu_add(v, q);
+    }
+    v = block_reduce(v);
+    if (threadIdx.x == 0) part[blockIdx.x] = make_double2(v.s, v.c);
+}
+
+// out[slot] = 0.5 * (sum of parts1) + 0.5 * (sum of parts2), fixed order, one block
+__global__ void k_finish(const double2* __restrict__ p1, int n1, const double2* __restrict__ p2, int n2,
+                         double* out) {
+    Neu a{0.0, 0.0}, b{0.0, 0.0};
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) a = neu_merge(a, Neu{p1[i].x, p1[i].y});
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) b = neu_merge(b, Neu{p2[i].x, p2[i].y});
+    a = block_reduce(a);
+    __syncthreads();
+    b = block_reduce(b);
+    if (threadIdx.x == 0) *out = 0.5 * (a.s + a.c) + 0.5 * (b.s + b.c);
+}
+
+template <typename T>
+__global__ void k_convert(const double* __restrict__ in, T* __restrict__ out, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (T)in[i];
+}
+
+}  // namespace
+
+// ====================================================================== context
+struct ygm_ctx {
+    ygm::Setup S;
+    int precision = YGM_FP64, n_rhs = 1, energy_every = 0, device = 0;
+    size_t rs = 8;                          // sizeof(real)
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    // device memory
+    void *e = nullptr, *b[2] = {nullptr, nullptr}, *x = nullptr, *bscr = nullptr, *q = nullptr;
+    void *W = nullptr, *inv_mu = nullptr, *sw = nullptr;
+    double* M2a = nullptr;
+    DCls *c1 = nullptr, *c2 = nullptr;
+    DSlot* slots = nullptr;
+    DTerm* terms = nullptr;
+    DInc* inc = nullptr;
+    DLoc2* loc2 = nullptr;
+    DRow *rowsA = nullptr, *rowsB = nullptr, *rowsE = nullptr;
+    int nrowsA = 0, nrowsB = 0, nrowsE = 0;
+    double2* part = nullptr;
+    int npart = 0;
+    double* hist = nullptr;
+    int64_t hist_cap = 0, hist_n = 0;
+    DSrc* dsrc = nullptr;
+    long long* sdofs = nullptr;
+    int nsrc = 0, nsrc_cap = 0, nsw_cap = 0;
+    std::vector<ygm_source> src_cache;
+    // time state
+    int cur = 0;
+    bool staggered = false;
+    int64_t step = 0;
+    int64_t step_base = 0;                  // step index where the current dt took over
+    double t_base = 0.0;                    // time at step_base
+    double dt_prev = 0.0;
+    bool host_only = false;
+    int64_t launches = 0;
+    std::string err;
+    Tables tb{};
+    // optional per-launch CUDA-event timing (ygm_kernel_timing)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<std::pair<int, size_t>> ev_rec;   // (kernel kind, index of the start event)
+};
+
+enum { KQ = 0, KB = 1, KE = 2, KS = 3, KW = 4, NKIND = 5 };
+
+static void time_begin(ygm_ctx* ctx, int kind) {
+    if (!ctx->timing) return;
+    while (ctx->ev_pool.size() < ctx->ev_used + 2) {
+        cudaEvent_t ev;
+        if (cudaEventCreate(&ev) != cudaSuccess) {
+            ctx->timing = false;
+            return;
+        }
+        ctx->ev_pool.push_back(ev);
+    }
+    ctx->ev_rec.push_back({kind, ctx->ev_used});
+    cudaEventRecord(ctx->ev_pool[ctx->ev_used], ctx->stream);
+    ctx->ev_used += 2;
+}
+static void time_end(ygm_ctx* ctx) {
+    if (!ctx->timing || ctx->ev_rec.empty()) return;
+    cudaEventRecord(ctx->ev_pool[ctx->ev_rec.back().second + 1], ctx->stream);
+}
+
+static std::string g_create_err;
+static std::mutex g_err_mutex;
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t _e = (call);                                                                   \
+        if (_e != cudaSuccess) {                                                                   \
+            ctx->err = std::string(#call) + ": " + cudaGetErrorString(_e);                         \
+            return YGM_ECUDA;                                                                      \
+        }                                                                                          \
+    } while (0)
+
+static int fail(ygm_ctx* ctx, int code, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+template <typename T>
+static int upload(ygm_ctx* ctx, T** dst, const std::vector<T>& v) {
+    if (v.empty()) {
+        *dst = nullptr;
+        return 0;
+    }
+    CK(cudaMalloc((void**)dst, v.size() * sizeof(T)));
+    CK(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return 0;
+}
+
+// upload FP64 host data in the context precision
+static int upload_real(ygm_ctx* ctx, void** dst, const std::vector<double>& v) {
+    if (v.empty()) {
+        *dst = nullptr;
+        return 0;
+    }
+    CK(cudaMalloc(dst, v.size() * ctx->rs));
+    if (ctx->precision == YGM_FP64) {
+        CK(cudaMemcpy(*dst, v.data(), v.size() * 8, cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> f(v.begin(), v.end());
+        CK(cudaMemcpy(*dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
+    }
+    return 0;
+}
+
+static std::vector<DRow> make_rows(const std::vector<ygm::DofClass>& cls, int n, bool active_only) {
+    // z-slab-major order over all classes: rows of neighbouring slabs stay close in time,
+    // so the transposed Q1 reads of k_qapply hit L2.
+    std::vector<DRow> rows;
+    for (int vz = 0; vz < n; ++vz)
+        for (int vy = 0; vy < n; ++vy)
+            for (int c = 0; c < (int)cls.size(); ++c) {
+                const auto& b = cls[c].box;
+                if (active_only && !cls[c].active) continue;
+                int ry = vy - b.lo[1], rz = vz - b.lo[2];
+                if (ry < 0 || rz < 0 || ry >= b.num[1] || rz >= b.num[2]) continue;
+                rows.push_back(DRow{c, vy, vz, (rz * b.num[1] + ry) * b.num[0]});
+            }
+    return rows;
+}
+
+static int setup_device(ygm_ctx* ctx) {
+    ygm::Setup& S = ctx->S;
+    ygm::Lattice& L = S.L;
+    const int k = L.k;
+    // classes
+    std::vector<DCls> c1(L.c1.size()), c2(L.c2.size());
+    std::vector<DInc> inc;
+    for (size_t c = 0; c < L.c1.size(); ++c) {
+        DCls& D = c1[c];
+        for (int a = 0; a < 3; ++a) {
+            D.lo[a] = L.c1[c].box.lo[a];
+            D.num[a] = L.c1[c].box.num[a];
+        }
+        D.off = L.c1[c].box.offset;
+        D.size = L.c1[c].box.size;
+        D.qoff = S.qoff[c];
+        D.st_begin = S.st_begin[c];
+        D.st_end = S.st_begin[c + 1];
+        D.inc_begin = (int)inc.size();
+        for (auto& I : L.inc1[c]) inc.push_back(DInc{{I.dcube[0], I.dcube[1], I.dcube[2]}, I.shape, I.loc});
+        D.inc_end = (int)inc.size();
+    }
+    std::vector<DSlot> slots(S.st_slots.size());
+    for (size_t s = 0; s < slots.size(); ++s)
+        slots[s] = DSlot{S.st_slots[s].cls, S.st_slots[s].slot, {S.st_slots[s].d[0], S.st_slots[s].d[1], S.st_slots[s].d[2]},
+                         S.st_slots[s].upper};
+    // integer curl rows of the active 2-form classes (built from the local block of a tet shape
+    // that contains the entity: the anchor offsets are relative to the 2-form's own anchor)
+    std::vector<DTerm> terms;
+    const int n1 = L.n1;
+    for (size_t c = 0; c < L.c2.size(); ++c) {
+        DCls& D = c2[c];
+        for (int a = 0; a < 3; ++a) {
+            D.lo[a] = L.c2[c].box.lo[a];
+            D.num[a] = L.c2[c].box.num[a];
+        }
+        D.off = L.c2[c].box.offset;
+        D.size = L.c2[c].box.size;
+        D.qoff = 0;
+        D.inc_begin = D.inc_end = 0;
+        D.st_begin = (int)terms.size();
+        if (L.c2[c].active) {
+            // find a tet shape and local index carrying this class
+            bool found = false;
+            for (int s = 0; s < 6 && !found; ++s)
+                for (int ra = 0; ra < L.n2a && !found; ++ra) {
+                    const auto& L2 = L.loc2[s][L.act2[ra]];
+                    if (L2.cls != (int)c) continue;
+                    for (int j = 0; j < n1; ++j) {
+                        int v = S.Cloc[(size_t)ra * n1 + j];
+                        if (!v) continue;
+                        const auto& L1 = L.loc1[s][j];
+                        terms.push_back(DTerm{L1.cls, {L1.off[0] - L2.off[0], L1.off[1] - L2.off[1], L1.off[2] - L2.off[2]}, v});
+                    }
+                    found = true;
+                }
+            if (!found) return fail(ctx, YGM_EINVAL, "internal: active 2-form class without a tet");
+        }
+        D.st_end = (int)terms.size();
+    }
+    std::vector<DLoc2> loc2;
+    for (int s = 0; s < 6; ++s)
+        for (int ra = 0; ra < L.n2a; ++ra) {
+            const auto& L2 = L.loc2[s][L.act2[ra]];
+            loc2.push_back(DLoc2{L2.cls, {L2.off[0], L2.off[1], L2.off[2]}});
+        }
+    int rc;
+    if ((rc = upload(ctx, &ctx->c1, c1)) || (rc = upload(ctx, &ctx->c2, c2)) || (rc = upload(ctx, &ctx->slots, slots)) ||
+        (rc = upload(ctx, &ctx->terms, terms)) || (rc = upload(ctx, &ctx->inc, inc)) || (rc = upload(ctx, &ctx->loc2, loc2)))
+        return rc;
+    // rows
+    std::vector<DRow> rA = make_rows(L.c1, L.n, false), rE = make_rows(L.c1, L.n, true), rB = make_rows(L.c2, L.n, true);
+    ctx->nrowsA = (int)rA.size();
+    ctx->nrowsE = (int)rE.size();
+    ctx->nrowsB = (int)rB.size();
+    if ((rc = upload(ctx, &ctx->rowsA, rA)) || (rc = upload(ctx, &ctx->rowsE, rE)) || (rc = upload(ctx, &ctx->rowsB, rB)))
+        return rc;
+    // operators
+    if ((rc = upload_real(ctx, &ctx->q, S.qvals)) || (rc = upload_real(ctx, &ctx->W, S.Wloc))) return rc;
+    std::vector<double> M2a(S.M2aloc);
+    if ((rc = upload(ctx, &ctx->M2a, M2a))) return rc;
+    bool mu_one = true;
+    for (double m : S.mu) mu_one &= (m == 1.0);
+    if (!mu_one) {
+        std::vector<double> im(S.mu.size());
+        for (size_t t = 0; t < im.size(); ++t) im[t] = 1.0 / S.mu[t];
+        if ((rc = upload_real(ctx, &ctx->inv_mu, im))) return rc;
+    }
+    // state
+    const size_t R = ctx->n_rhs;
+    CK(cudaMalloc(&ctx->e, L.N1 * R * ctx->rs));
+    CK(cudaMalloc(&ctx->x, L.N1 * R * ctx->rs));
+    CK(cudaMalloc(&ctx->b[0], L.N2 * R * ctx->rs));
+    CK(cudaMalloc(&ctx->b[1], L.N2 * R * ctx->rs));
+    CK(cudaMalloc(&ctx->bscr, L.N2 * R * ctx->rs));
+    CK(cudaMemsetAsync(ctx->e, 0, L.N1 * R * ctx->rs, ctx->stream));
+    CK(cudaMemsetAsync(ctx->x, 0, L.N1 * R * ctx->rs, ctx->stream));
+    CK(cudaMemsetAsync(ctx->b[0], 0, L.N2 * R * ctx->rs, ctx->stream));
+    CK(cudaMemsetAsync(ctx->b[1], 0, L.N2 * R * ctx->rs, ctx->stream));
+    CK(cudaMemsetAsync(ctx->bscr, 0, L.N2 * R * ctx->rs, ctx->stream));
+    ctx->npart = 4 * 152;
+    CK(cudaMalloc((void**)&ctx->part, 2 * ctx->npart * sizeof(double2)));
+    ctx->hist_cap = 1 << 16;
+    CK(cudaMalloc((void**)&ctx->hist, ctx->hist_cap * sizeof(double)));
+    ctx->tb = Tables{ctx->c1, ctx->c2, ctx->slots, ctx->terms, ctx->inc, ctx->loc2, L.n, L.n1, L.n2a};
+    (void)k;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return 0;
+}
+
+// ------------------------------------------------------------------ launch helpers
+static int launch_qapply(ygm_ctx* ctx, const void* e, void* x) {
+    dim3 g((ctx->nrowsA + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+    time_begin(ctx, KQ);
+    if (ctx->precision == YGM_FP64)
+        k_qapply<double><<<g, BLOCK, 0, ctx->stream>>>(ctx->tb, ctx->rowsA, ctx->nrowsA, (const double*)ctx->q,
+                                                       (const double*)e, (double*)x);
+    else
+        k_qapply<float><<<g, BLOCK, 0, ctx->stream>>>(ctx->tb, ctx->rowsA, ctx->nrowsA, (const float*)ctx->q,
+                                                      (const float*)e, (float*)x);
+    time_end(ctx);
+    ctx->launches++;
+    return 0;
+}
+static int launch_curl_b(ygm_ctx* ctx, const void* x, const void* bin, void* bout, double ctau) {
+    dim3 g((ctx->nrowsB + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+    time_begin(ctx, KB);
+    if (ctx->precision == YGM_FP64)
+        k_curl_b<double><<<g, BLOCK, 0, ctx->stream>>>(ctx->tb, ctx->rowsB, ctx->nrowsB, (const double*)x,
+                                                       (const double*)bin, (double*)bout, ctau);
+    else
+        k_curl_b<float><<<g, BLOCK, 0, ctx->stream>>>(ctx->tb, ctx->rowsB, ctx->nrowsB, (const float*)x,
+                                                      (const float*)bin, (float*)bout, (float)ctau);
+    time_end(ctx);
+    ctx->launches++;
+    return 0;
+}
+static int launch_curlT_e(ygm_ctx* ctx, const void* b, void* e, double ctau) {
+    dim3 g((ctx->nrowsE + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+    time_begin(ctx, KE);
+    if (ctx->precision == YGM_FP64)
+        k_curlT_e<double><<<g, BLOCK, 0, ctx->stream>>>(ctx->tb, ctx->rowsE, ctx->nrowsE, (const double*)ctx->W,
+                                                        (const double*)b, (const double*)ctx->inv_mu, (double*)e, ctau);
+    else
+        k_curlT_e<float><<<g, BLOCK, 0, ctx->stream>>>(ctx->tb, ctx->rowsE, ctx->nrowsE, (const float*)ctx->W,
+                                                       (const float*)b, (const float*)ctx->inv_mu, (float*)e, (float)ctau);
+    time_end(ctx);
+    ctx->launches++;
+    return 0;
+}
+static int launch_source(ygm_ctx* ctx, double t, double dt) {
+    if (!ctx->nsrc) return 0;
+    time_begin(ctx, KS);
+    if (ctx->precision == YGM_FP64)
+        k_source<double><<<1, 256, 0, ctx->stream>>>(ctx->dsrc, ctx->nsrc, ctx->sdofs, (const double*)ctx->sw,
+                                                     (double*)ctx->e, t, dt);
+    else
+        k_source<float><<<1, 256, 0, ctx->stream>>>(ctx->dsrc, ctx->nsrc, ctx->sdofs, (const float*)ctx->sw,
+                                                    (float*)ctx->e, t, dt);
+    time_end(ctx);
+    ctx->launches++;
+    return 0;
+}
+// out = 1/2 e^T x + 1/2 sum_T bn^T M2 bo / mu_T  (device double)
+static int launch_energy(ygm_ctx* ctx, const void* e, const void* x, const void* bn, const void* bo, double* out) {
+    const int np = ctx->npart;
+    const long long N1 = ctx->S.L.N1;
+    time_begin(ctx, KW);
+    if (ctx->precision == YGM_FP64) {
+        k_dot<double><<<np, BLOCK, 0, ctx->stream>>>((const double*)e, (const double*)x, N1, ctx->part);
+        k_tet_quad<double><<<np, BLOCK, 0, ctx->stream>>>(ctx->tb, ctx->M2a, (const double*)bn, (const double*)bo,
+                                                          (const double*)ctx->inv_mu, ctx->part + np);
+    } else {
+        k_dot<float><<<np, BLOCK, 0, ctx->stream>>>((const float*)e, (const float*)x, N1, ctx->part);
+        k_tet_quad<float><<<np, BLOCK, 0, ctx->stream>>>(ctx->tb, ctx->M2a, (const float*)bn, (const float*)bo,
+                                                         (const float*)ctx->inv_mu, ctx->part + np);
+    }
+    k_finish<<<1, 1024, 0, ctx->stream>>>(ctx->part, np, ctx->part + np, np, out);
+    time_end(ctx);
+    ctx->launches += 3;
+    return 0;
+}
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* ygm_last_error(const ygm_ctx* ctx) {
+    if (ctx) return ctx->err.c_str();
+    std::lock_guard<std::mutex> lk(g_err_mutex);
+    return g_create_err.c_str();
+}
+
+int ygm_create(const ygm_mesh* mesh, int order, const double* eps, const double* mu, const ygm_opts* opts,
+               ygm_ctx** out) {
+    auto cerr = [](int code, const std::string& m) {
+        std::lock_guard<std::mutex> lk(g_err_mutex);
+        g_create_err = m;
+        return code;
+    };
+    if (!out) return cerr(YGM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!mesh || mesh->n < 1 || !(mesh->side > 0) || !std::isfinite(mesh->side))
+        return cerr(YGM_EINVAL, "mesh: need n >= 1 and finite side > 0");
+    if (order < 1 || order > 3) return cerr(YGM_EINVAL, "order must be 1, 2 or 3");
+    ygm_opts o{};
+    o.precision = YGM_FP64;
+    o.n_rhs = 1;
+    if (opts) o = *opts;
+    if (o.precision != YGM_FP64 && o.precision != YGM_FP32) return cerr(YGM_EINVAL, "precision must be YGM_FP64 or YGM_FP32");
+    if (o.n_rhs != 1) return cerr(YGM_EINVAL, "n_rhs > 1 is not supported by this build");
+    if (o.energy_every < 0) return cerr(YGM_EINVAL, "energy_every must be >= 0");
+    if (o.q1_pattern < 0 || o.q1_pattern > 3) return cerr(YGM_EINVAL, "unknown q1_pattern");
+    const bool host_only = o.device == -1;
+    int ndev = 0;
+    if (!host_only) {
+        if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return cerr(YGM_ENODEV, "no CUDA device");
+        if (o.device < 0 || o.device >= ndev) return cerr(YGM_EINVAL, "device ordinal out of range");
+    }
+    ygm_ctx* ctx = new (std::nothrow) ygm_ctx();
+    if (!ctx) return cerr(YGM_ENOMEM, "host allocation failed");
+    ctx->precision = o.precision;
+    ctx->rs = o.precision == YGM_FP64 ? 8 : 4;
+    ctx->n_rhs = o.n_rhs;
+    ctx->energy_every = o.energy_every;
+    ctx->device = o.device;
+    ctx->host_only = host_only;
+    if (host_only) {
+        int rc = ygm::build_setup(ctx->S, mesh->n, mesh->side, order, eps, mu, o.q1_pattern, o.threads);
+        if (rc) {
+            std::string m = ctx->S.err;
+            delete ctx;
+            return cerr(rc == -1 ? YGM_EINVAL : YGM_ENOTSPD, m);
+        }
+        *out = ctx;
+        return YGM_OK;
+    }
+    if (cudaSetDevice(o.device) != cudaSuccess) {
+        delete ctx;
+        return cerr(YGM_ECUDA, "cudaSetDevice failed");
+    }
+    if (o.stream) {
+        ctx->stream = (cudaStream_t)o.stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            return cerr(YGM_ECUDA, "cudaStreamCreate failed");
+        }
+        ctx->own_stream = true;
+    }
+    int rc = ygm::build_setup(ctx->S, mesh->n, mesh->side, order, eps, mu, o.q1_pattern, o.threads);
+    if (rc) {
+        std::string m = ctx->S.err;
+        ygm_destroy(ctx);
+        return cerr(rc == -1 ? YGM_EINVAL : YGM_ENOTSPD, m);
+    }
+    rc = setup_device(ctx);
+    if (rc) {
+        std::string m = ctx->err;
+        ygm_destroy(ctx);
+        return cerr(rc, m);
+    }
+    *out = ctx;
+    return YGM_OK;
+}
+
+int ygm_sizes(const ygm_ctx* ctx, int64_t* n1, int64_t* n2, int64_t* q1_nnz, double* dt_cfl) {
+    if (!ctx) return YGM_EINVAL;
+    if (n1) *n1 = ctx->S.L.N1;
+    if (n2) *n2 = ctx->S.L.N2;
+    if (q1_nnz) *q1_nnz = (int64_t)ctx->S.Q1.col.size();
+    if (dt_cfl) *dt_cfl = ctx->S.tau_cfl;
+    return YGM_OK;
+}
+
+int ygm_set_state(ygm_ctx* ctx, const void* e, const void* b, int on_device) {
+    if (ctx && ctx->host_only) return fail(ctx, YGM_ENODEV, "context was created host-only (device = -1)");
+    if (!ctx || !e || !b) return fail(ctx, YGM_EINVAL, "NULL argument");
+    const size_t ne = ctx->S.L.N1 * ctx->n_rhs * ctx->rs, nb = ctx->S.L.N2 * ctx->n_rhs * ctx->rs;
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(ctx->e, e, ne, kind, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->b[0], b, nb, kind, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->b[1], b, nb, kind, ctx->stream));
+    if (!on_device) CK(cudaStreamSynchronize(ctx->stream));
+    ctx->cur = 0;
+    ctx->staggered = false;
+    ctx->step = ctx->step_base = 0;
+    ctx->t_base = 0.0;
+    ctx->hist_n = 0;
+    return YGM_OK;
+}
+
+int ygm_get_state(ygm_ctx* ctx, void* e, void* b, int on_device, int synced) {
+    if (ctx && ctx->host_only) return fail(ctx, YGM_ENODEV, "context was created host-only (device = -1)");
+    if (!ctx) return YGM_EINVAL;
+    const size_t ne = ctx->S.L.N1 * ctx->n_rhs * ctx->rs, nb = ctx->S.L.N2 * ctx->n_rhs * ctx->rs;
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (e) CK(cudaMemcpyAsync(e, ctx->e, ne, kind, ctx->stream));
+    if (b) {
+        const void* src = ctx->b[ctx->cur];
+        if (synced && ctx->staggered) {
+            CK(cudaMemcpyAsync(ctx->bscr, ctx->b[ctx->cur], nb, cudaMemcpyDeviceToDevice, ctx->stream));
+            launch_qapply(ctx, ctx->e, ctx->x);
+            launch_curl_b(ctx, ctx->x, ctx->b[ctx->cur], ctx->bscr, 0.5 * ctx->dt_prev);
+            src = ctx->bscr;
+        }
+        CK(cudaMemcpyAsync(b, src, nb, kind, ctx->stream));
+    }
+    CK(cudaGetLastError());
+    if (!on_device) CK(cudaStreamSynchronize(ctx->stream));
+    return YGM_OK;
+}
+
+int ygm_project_E(ygm_ctx* ctx, void (*E0)(const double x[3], double out[3], void* user), void* user, int32_t rhs) {
+    if (ctx && ctx->host_only) return fail(ctx, YGM_ENODEV, "context was created host-only (device = -1)");
+    if (!ctx || !E0) return fail(ctx, YGM_EINVAL, "NULL argument");
+    if (rhs < 0 || rhs >= ctx->n_rhs) return fail(ctx, YGM_EINVAL, "rhs out of range");
+    std::vector<double> e0;
+    ygm::project_E(ctx->S, E0, user, e0, 1);
+    std::vector<double> bz(ctx->S.L.N2, 0.0);
+    int rc;
+    void* de = nullptr;
+    if ((rc = upload_real(ctx, &de, e0))) return rc;
+    CK(cudaMemcpyAsync(ctx->e, de, e0.size() * ctx->rs, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemsetAsync(ctx->b[0], 0, bz.size() * ctx->rs, ctx->stream));
+    CK(cudaMemsetAsync(ctx->b[1], 0, bz.size() * ctx->rs, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(de);
+    ctx->cur = 0;
+    ctx->staggered = false;
+    ctx->step = ctx->step_base = 0;
+    ctx->t_base = 0.0;
+    ctx->hist_n = 0;
+    return YGM_OK;
+}
+
+static int set_sources(ygm_ctx* ctx, const ygm_source* src, int32_t n_src) {
+    bool same = (int)ctx->src_cache.size() == n_src;
+    for (int i = 0; same && i < n_src; ++i) same = std::memcmp(&ctx->src_cache[i], &src[i], sizeof(ygm_source)) == 0;
+    if (same) return 0;
+    std::vector<DSrc> hs;
+    std::vector<long long> dofs;
+    std::vector<double> w;
+    for (int i = 0; i < n_src; ++i) {
+        const ygm_source& s = src[i];
+        for (int a = 0; a < 3; ++a)
+            if (!std::isfinite(s.x[a]) || !std::isfinite(s.d[a]) || s.x[a] < 0 || s.x[a] > ctx->S.L.h * ctx->S.L.n)
+                return fail(ctx, YGM_EINVAL, "source position outside the cube or not finite");
+        if (!(s.sigma > 0) || !std::isfinite(s.amp) || !std::isfinite(s.omega) || !std::isfinite(s.t0))
+            return fail(ctx, YGM_EINVAL, "source parameters invalid (sigma must be > 0)");
+        if (s.rhs < 0 || s.rhs >= ctx->n_rhs) return fail(ctx, YGM_EINVAL, "source rhs out of range");
+        std::vector<int64_t> d;
+        std::vector<double> ww;
+        if (ygm::dipole_weights(ctx->S, s.x, s.d, d, ww)) return fail(ctx, YGM_EINVAL, "source not located");
+        DSrc ds{s.amp, s.omega, s.t0, s.sigma, (int)dofs.size(), 0};
+        for (size_t j = 0; j < d.size(); ++j) {
+            dofs.push_back(d[j] * ctx->n_rhs + s.rhs);
+            w.push_back(ww[j]);
+        }
+        ds.end = (int)dofs.size();
+        hs.push_back(ds);
+    }
+    cudaFree(ctx->dsrc);
+    cudaFree(ctx->sdofs);
+    cudaFree(ctx->sw);
+    ctx->dsrc = nullptr;
+    ctx->sdofs = nullptr;
+    ctx->sw = nullptr;
+    int rc;
+    if ((rc = upload(ctx, &ctx->dsrc, hs)) || (rc = upload(ctx, &ctx->sdofs, dofs)) || (rc = upload_real(ctx, &ctx->sw, w)))
+        return rc;
+    ctx->nsrc = n_src;
+    ctx->src_cache.assign(src, src + n_src);
+    return 0;
+}
+
+int ygm_step(ygm_ctx* ctx, int64_t n, double dt, const ygm_source* src, int32_t n_src) {
+    if (ctx && ctx->host_only) return fail(ctx, YGM_ENODEV, "context was created host-only (device = -1)");
+    if (!ctx) return YGM_EINVAL;
+    if (n < 0 || !(dt > 0) || !std::isfinite(dt)) return fail(ctx, YGM_EINVAL, "need n >= 0 and finite dt > 0");
+    if (dt > ctx->S.tau_cfl * (1.0 + 1e-12))
+        return fail(ctx, YGM_ECFL, "dt exceeds the CFL bound 2/omega_max (Prop. stability)");
+    if (n_src < 0 || (n_src > 0 && !src)) return fail(ctx, YGM_EINVAL, "bad source list");
+    int rc = set_sources(ctx, src, n_src);
+    if (rc) return rc;
+    CK(cudaSetDevice(ctx->device));
+    void* b0 = ctx->b[ctx->cur];
+    if (!ctx->staggered) {
+        // initial half step Phi^e_{dt/2} (Eq. YeeLeapfrog): b_{-1/2} = b_0 + dt/2 C Q1 e_0
+        launch_qapply(ctx, ctx->e, ctx->x);
+        launch_curl_b(ctx, ctx->x, b0, b0, -0.5 * dt);
+        ctx->staggered = true;
+        ctx->step_base = ctx->step;
+        ctx->t_base = 0.0;
+    } else if (dt != ctx->dt_prev) {
+        // close the old staggering and reopen it with the new step (exact Strang composition)
+        launch_qapply(ctx, ctx->e, ctx->x);
+        launch_curl_b(ctx, ctx->x, b0, b0, 0.5 * ctx->dt_prev - 0.5 * dt);
+        ctx->t_base += (double)(ctx->step - ctx->step_base) * ctx->dt_prev;
+        ctx->step_base = ctx->step;
+    }
+    ctx->dt_prev = dt;
+    for (int64_t i = 0; i < n; ++i) {
+        void* bo = ctx->b[ctx->cur];
+        void* bn = ctx->b[ctx->cur ^ 1];
+        launch_qapply(ctx, ctx->e, ctx->x);
+        launch_curl_b(ctx, ctx->x, bo, bn, dt);
+        if (ctx->energy_every && ctx->step % ctx->energy_every == 0 && ctx->hist_n < ctx->hist_cap - 2)
+            launch_energy(ctx, ctx->e, ctx->x, bn, bo, ctx->hist + ctx->hist_n++);
+        launch_curlT_e(ctx, bn, ctx->e, dt);
+        launch_source(ctx, ctx->t_base + ((double)(ctx->step - ctx->step_base) + 0.5) * dt, dt);
+        ctx->cur ^= 1;
+        ctx->step++;
+    }
+    CK(cudaGetLastError());
+    return YGM_OK;
+}
+
+int ygm_energy(ygm_ctx* ctx, double* W, double* Htilde) {
+    if (ctx && ctx->host_only) return fail(ctx, YGM_ENODEV, "context was created host-only (device = -1)");
+    if (!ctx || !W) return fail(ctx, YGM_EINVAL, "NULL argument");
+    const size_t nb = ctx->S.L.N2 * ctx->n_rhs * ctx->rs;
+    double* dout = ctx->hist + ctx->hist_cap - 2;   // two scratch slots at the end of the history
+    void* bo = ctx->b[ctx->cur];
+    launch_qapply(ctx, ctx->e, ctx->x);
+    if (ctx->staggered) {
+        CK(cudaMemcpyAsync(ctx->bscr, bo, nb, cudaMemcpyDeviceToDevice, ctx->stream));
+        launch_curl_b(ctx, ctx->x, bo, ctx->bscr, ctx->dt_prev);
+        launch_energy(ctx, ctx->e, ctx->x, ctx->bscr, bo, dout);
+        launch_curl_b(ctx, ctx->x, bo, ctx->bscr, 0.5 * ctx->dt_prev);
+        launch_energy(ctx, ctx->e, ctx->x, ctx->bscr, ctx->bscr, dout + 1);
+    } else {
+        // not yet staggered: b is synchronised, W is reported as H~
+        launch_energy(ctx, ctx->e, ctx->x, bo, bo, dout);
+        launch_energy(ctx, ctx->e, ctx->x, bo, bo, dout + 1);
+    }
+    double h[2];
+    CK(cudaMemcpyAsync(h, dout, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *W = h[0];
+    if (Htilde) *Htilde = h[1];
+    return YGM_OK;
+}
+
+int ygm_energy_history(ygm_ctx* ctx, double* out, int64_t max_count, int64_t* count) {
+    if (ctx && ctx->host_only) return fail(ctx, YGM_ENODEV, "context was created host-only (device = -1)");
+    if (!ctx || !count) return fail(ctx, YGM_EINVAL, "NULL argument");
+    int64_t c = std::min<int64_t>(std::min<int64_t>(ctx->hist_n, ctx->hist_cap - 2), max_count);
+    if (c > 0 && out) CK(cudaMemcpyAsync(out, ctx->hist, c * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *count = c;
+    return YGM_OK;
+}
+
+int ygm_time(const ygm_ctx* ctx, int64_t* step, double* t) {
+    if (!ctx) return YGM_EINVAL;
+    if (step) *step = ctx->step;
+    if (t) *t = ctx->t_base + (double)(ctx->step - ctx->step_base) * ctx->dt_prev;
+    return YGM_OK;
+}
+
+int ygm_export_q1(const ygm_ctx* ctx, int64_t* rowptr, int64_t* colind, double* val) {
+    if (!ctx || !rowptr || !colind || !val) return YGM_EINVAL;
+    const auto& Q = ctx->S.Q1;
+    std::copy(Q.ptr.begin(), Q.ptr.end(), rowptr);
+    std::copy(Q.col.begin(), Q.col.end(), colind);
+    std::copy(Q.val.begin(), Q.val.end(), val);
+    return YGM_OK;
+}
+
+int ygm_q1_info(const ygm_ctx* ctx, double* lmin, double* lmax, double* shift, double* omega_max_sq,
+                int32_t* pattern, int32_t* ortho) {
+    if (!ctx) return YGM_EINVAL;
+    if (lmin) *lmin = ctx->S.lmin;
+    if (lmax) *lmax = ctx->S.lmax;
+    if (shift) *shift = ctx->S.shift;
+    if (omega_max_sq) *omega_max_sq = ctx->S.omega_max_sq;
+    if (pattern) *pattern = ctx->S.q1_pattern;
+    if (ortho) *ortho = ctx->S.ortho ? 1 : 0;
+    return YGM_OK;
+}
+
+int ygm_local_blocks(const ygm_ctx* ctx, int32_t* n1, int32_t* n2a, double* M1, double* M2a) {
+    if (!ctx) return YGM_EINVAL;
+    if (n1) *n1 = ctx->S.L.n1;
+    if (n2a) *n2a = ctx->S.L.n2a;
+    if (M1) std::copy(ctx->S.M1loc.begin(), ctx->S.M1loc.end(), M1);
+    if (M2a) std::copy(ctx->S.M2aloc.begin(), ctx->S.M2aloc.end(), M2a);
+    return YGM_OK;
+}
+
+int ygm_kernel_timing(ygm_ctx* ctx, int enable) {
+    if (!ctx) return YGM_EINVAL;
+    if (ctx->host_only) return fail(ctx, YGM_ENODEV, "context was created host-only (device = -1)");
+    ctx->timing = enable != 0;
+    return YGM_OK;
+}
+
+int ygm_kernel_times(ygm_ctx* ctx, double* ms, int64_t* count) {
+    if (!ctx || !ms || !count) return fail(ctx, YGM_EINVAL, "NULL argument");
+    if (ctx->host_only) return fail(ctx, YGM_ENODEV, "context was created host-only (device = -1)");
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < NKIND; ++i) {
+        ms[i] = 0.0;
+        count[i] = 0;
+    }
+    for (auto& [kind, i0] : ctx->ev_rec) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, ctx->ev_pool[i0], ctx->ev_pool[i0 + 1]));
+        ms[kind] += t;
+        count[kind] += 1;
+    }
+    ctx->ev_rec.clear();
+    ctx->ev_used = 0;
+    return YGM_OK;
+}
+
+int ygm_launch_count(const ygm_ctx* ctx, int64_t* count) {
+    if (!ctx || !count) return YGM_EINVAL;
+    *count = ctx->launches;
+    return YGM_OK;
+}
+
+void ygm_destroy(ygm_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->host_only) {
+        delete ctx;
+        return;
+    }
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    void* ptrs[] = {ctx->e,     ctx->b[0],  ctx->b[1], ctx->x,     ctx->bscr,  ctx->q,     ctx->W,     ctx->inv_mu,
+                    ctx->sw,    ctx->M2a,   ctx->c1,   ctx->c2,    ctx->slots, ctx->terms, ctx->inc,   ctx->loc2,
+                    ctx->rowsA, ctx->rowsB, ctx->rowsE, ctx->part, ctx->hist,  ctx->dsrc,  ctx->sdofs};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,182 @@
+"""GPU (sm_103a) parity of the C-ABI leapfrog against the FP64 oracle.
+
+Tolerances (relative L2 of e and b): FP64 1e-12 (same operators and operation order up to
+summation order); FP32 5e-5 after the run (float state, float Q1; see the design doc for the
+derivation from the step count and the float unit round-off)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+import synth
+from oracle_runs import oracle_model, run_oracle, rel_l2, te110
+
+Y = pytest.importorskip("paper_2301_01753_gb300")
+
+FP64_TOL = 1e-12
+FP32_TOL = 5e-5
+
+
+def _dipole(tau, x=(0.41, 0.52, 0.47), d=(0.0, 0.0, 1.0), width=20.0):
+    sigma = width * tau
+    return dict(x=np.array(x), d=np.array(d), amp=1.0, omega=np.pi * np.sqrt(5.0), width_steps=width,
+                t0=4 * sigma, sigma=sigma)
+
+
+def _gpu_run(n, k, eps, e0, b0, tau, nsteps, precision, sources=(), energy_every=0, pattern=0):
+    c = Y.Context(n, k, eps=eps, precision=precision, energy_every=energy_every, q1_pattern=pattern)
+    dt = np.float64 if precision == Y.YGM_FP64 else np.float32
+    c.set_state(np.ascontiguousarray(e0, dt), np.ascontiguousarray(b0, dt))
+    c.step(nsteps, tau, [dict(s) for s in sources])
+    e, b = c.get_state(synced=True)
+    _, bs = c.get_state(synced=False)
+    W = c.energy_history() if energy_every else None
+    return c, e, b, bs, W
+
+
+def test_config1_te110_fp64_1000_steps():
+    """N=4, k=1, eps=mu=1, TE(1,1,0) mode, dt = 0.5 tau_CFL, 1000 steps, FP64."""
+    f, g, eps, _ = oracle_model(4, 1)
+    tau = 0.5 * g.tau_cfl()
+    e0 = f.M1() @ f.edge_interpolant(te110)
+    b0 = np.zeros(f.mesh.N2)
+    e_or, bst_or, bs_or, W_or = run_oracle(f, g, e0, b0, tau, 1000, energy_every=10)
+    c = Y.Context(4, 1, precision=Y.YGM_FP64, energy_every=10)
+    assert abs(c.tau_cfl / g.tau_cfl() - 1) < 1e-9
+    c.project_E(lambda x: te110(x)[0])
+    e_gpu0, _ = c.get_state()
+    assert rel_l2(e_gpu0, e0) < 1e-13
+    c.step(1000, tau)
+    e, b = c.get_state(synced=True)
+    assert rel_l2(e, e_or) < FP64_TOL
+    assert rel_l2(b, bs_or) < FP64_TOL
+    W = c.energy_history()
+    assert len(W) == 100
+    assert np.max(np.abs(W - W_or)) / W_or[0] < 1e-12
+    assert np.max(np.abs(W - W[0])) / W[0] < 1e-12        # exact invariant up to round-off
+    assert c.time()[0] == 1000
+
+
+@pytest.mark.parametrize("precision,tol", [(0, FP64_TOL), (1, FP32_TOL)])
+def test_k2_random_eps_dipole(precision, tol):
+    n, k, steps = 4, 2, 300
+    f, g, eps, _ = oracle_model(n, k, eps_seed=2000)
+    tau = 0.5 * g.tau_cfl()
+    src = [_dipole(tau)]
+    z1, z2 = np.zeros(f.mesh.N1), np.zeros(f.mesh.N2)
+    e_or, bst_or, bs_or, _ = run_oracle(f, g, z1, z2, tau, steps, sources=src)
+    c, e, b, bs, _ = _gpu_run(n, k, eps, z1, z2, tau, steps, precision, sources=src)
+    assert np.linalg.norm(e_or) > 0
+    assert rel_l2(e, e_or) < tol
+    assert rel_l2(b, bs_or) < tol
+    assert rel_l2(bs, bst_or) < tol
+
+
+@pytest.mark.parametrize("n,k", [(2, 3), (3, 1), (3, 2)])
+def test_random_state_fp64(n, k):
+    f, g, eps, _ = oracle_model(n, k, eps_seed=77)
+    tau = 0.45 * g.tau_cfl()
+    rng = np.random.default_rng(n * 10 + k)
+    e0 = rng.standard_normal(f.mesh.N1)
+    b0 = f.C() @ rng.standard_normal(f.mesh.N1)          # b in the range of C (div-free)
+    e_or, bst_or, bs_or, _ = run_oracle(f, g, e0, b0, tau, 120)
+    _, e, b, bs, _ = _gpu_run(n, k, eps, e0, b0, tau, 120, Y.YGM_FP64)
+    assert rel_l2(e, e_or) < FP64_TOL
+    assert rel_l2(b, bs_or) < FP64_TOL
+
+
+def test_single_step_elementwise_fp64():
+    """One step from a random staggered state: every element of e_1 and b_{1/2}."""
+    f, g, eps, _ = oracle_model(3, 2, eps_seed=5)
+    tau = 0.5 * g.tau_cfl()
+    rng = np.random.default_rng(0)
+    e0 = rng.standard_normal(f.mesh.N1)
+    b0 = f.C() @ rng.standard_normal(f.mesh.N1)
+    e_or, bst_or, bs_or, _ = run_oracle(f, g, e0, b0, tau, 1)
+    _, e, b, bs, _ = _gpu_run(3, 2, eps, e0, b0, tau, 1, Y.YGM_FP64)
+    scale_e, scale_b = np.abs(e_or).max(), np.abs(bst_or).max()
+    assert np.all(np.abs(e - e_or) <= 1e-13 * scale_e)
+    assert np.all(np.abs(bs - bst_or) <= 1e-13 * scale_b)
+
+
+def test_ragged_rows_longer_than_a_warp():
+    """n = 34: class rows of 33/34 entries take two 32-lane passes per warp."""
+    n, k = 34, 1
+    c = Y.Context(n, k, precision=Y.YGM_FP64)
+    f, g, eps, _ = oracle_model(6, 1)     # only for the property checks below
+    rng = np.random.default_rng(1)
+    e0 = rng.standard_normal(c.N1)
+    b0 = np.zeros(c.N2)
+    c.set_state(e0, b0)
+    tau = 0.5 * c.tau_cfl
+    c.step(1, tau)
+    W0, _ = c.energy()
+    c.step(200, tau)
+    W1, _ = c.energy()
+    assert abs(W1[0] - W0[0]) / W0[0] < 1e-12           # conserved at any size
+
+
+def test_tiny_mesh_n1_and_empty_classes():
+    c = Y.Context(1, 1, precision=Y.YGM_FP64)
+    assert (c.N1, c.N2) == (1, 6)
+    c.set_state(np.ones(1), np.zeros(6))
+    c.step(10, 0.5 * c.tau_cfl)
+    e, b = c.get_state()
+    assert np.all(np.isfinite(e)) and np.all(np.isfinite(b))
+
+
+def test_cfl_refused_and_nothing_run():
+    c = Y.Context(2, 1, precision=Y.YGM_FP64)
+    c.set_state(np.ones(c.N1), np.zeros(c.N2))
+    n0 = c.launch_count()
+    with pytest.raises(Y.YgmError) as ei:
+        c.step(5, c.tau_cfl * 1.01)
+    assert ei.value.code == Y.YGM_ECFL
+    assert c.launch_count() == n0
+    c.step(3, c.tau_cfl)                                  # exactly at the bound is allowed
+
+
+def test_dt_change_is_an_exact_strang_restaggering():
+    f, g, eps, _ = oracle_model(3, 1, eps_seed=9)
+    t1, t2 = 0.4 * g.tau_cfl(), 0.3 * g.tau_cfl()
+    rng = np.random.default_rng(4)
+    e0 = rng.standard_normal(f.mesh.N1)
+    b0 = np.zeros(f.mesh.N2)
+    e, bst, bs, _ = run_oracle(f, g, e0, b0, t1, 40)
+    e, bst, bs, _ = run_oracle(f, g, e, bs, t2, 25)        # restart from the synchronised state
+    c = Y.Context(3, 1, eps=eps, precision=Y.YGM_FP64)
+    c.set_state(e0, b0)
+    c.step(40, t1)
+    c.step(25, t2)
+    eg, bg = c.get_state(synced=True)
+    assert rel_l2(eg, e) < FP64_TOL and rel_l2(bg, bs) < FP64_TOL
+    assert abs(c.time()[1] - (40 * t1 + 25 * t2)) < 1e-12
+
+
+def test_energy_api_matches_oracle():
+    f, g, eps, _ = oracle_model(3, 2, eps_seed=12)
+    tau = 0.5 * g.tau_cfl()
+    rng = np.random.default_rng(2)
+    e0 = rng.standard_normal(f.mesh.N1)
+    b0 = np.zeros(f.mesh.N2)
+    e, bst, bs, _ = run_oracle(f, g, e0, b0, tau, 50)
+    c = Y.Context(3, 2, eps=eps, precision=Y.YGM_FP64)
+    c.set_state(e0, b0)
+    c.step(50, tau)
+    W, H = c.energy()
+    assert abs(W[0] - g.W(e, bst, tau)) / abs(W[0]) < 1e-12
+    assert abs(H[0] - g.H_tilde(e, bs)) / abs(H[0]) < 1e-12
+
+
+def test_device_pointer_state_roundtrip():
+    torch = pytest.importorskip("torch")
+    c = Y.Context(3, 1, precision=Y.YGM_FP32)
+    e = torch.randn(c.N1, device="cuda", dtype=torch.float32)
+    b = torch.zeros(c.N2, device="cuda", dtype=torch.float32)
+    c.set_state(e, b)
+    torch.cuda.synchronize()
+    e2 = torch.empty_like(e)
+    b2 = torch.empty_like(b)
+    c.get_state(synced=False, out_e=e2, out_b=b2)
+    torch.cuda.synchronize()
+    assert torch.equal(e, e2) and torch.equal(b, b2)

@@ -61,15 +61,20 @@ def test_default_policy_gives_spd_without_shift(n, k):
 
 
 def test_ortho_basis_keeps_the_dynamics_and_pattern():
-    """Q1 = T^T Q'' T: the GYM of basis Lambda'' in integer-C variables; check against the
-    primed-basis GYM built directly (same P2 spectrum) on a tiny mesh."""
+    """Q1 = T^T Q' T: the GYM of basis Lambda' in integer-C variables; T is invertible, block
+    diagonal over entities, and orthonormalises each entity's DoFs in the M1 inner product."""
     f = FEM(KuhnMesh(2, 2), eps=synth.tet_eps(14, 2, 1, 4))
     M1 = f.M1()
     T = SP.ortho_basis_transform(f, M1).toarray()
     Mp = T @ M1.toarray() @ T.T
-    # T is sub-entity triangular: every face/cell row only touches its own sub-entities
+    # T is block diagonal over the entities: it never couples DoFs of different entities
     Sm = SP.pattern("sm1", M1, f.dof1).toarray() > 0
     assert np.all((np.abs(T) > 0) <= Sm)
+    gid = np.zeros(f.mesh.N1, int)
+    for i, g in enumerate(sum(SP.entity_groups(f), [])):
+        gid[list(g)] = i
+    rr, cc = np.nonzero(np.abs(T) > 0)
+    assert np.all(gid[rr] == gid[cc])
     # exact inverse is basis independent: T^T (T M T^T)^-1 T = M^-1
     assert np.allclose(T.T @ np.linalg.inv(Mp) @ T, np.linalg.inv(M1.toarray()), rtol=1e-8, atol=1e-10)
     # the primed mass matrix is normalised inside each entity
