@@ -150,6 +150,21 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ replica aggregation
+def aggregate(units_per_rank, seconds_local, dist=None, device="cpu"):
+    """Whole-job throughput of independent replicas: every rank did `units_per_rank`; the job
+    time is the maximum over ranks.  Returns (value, job seconds)."""
+    import torch
+    t = float(seconds_local)
+    world = 1
+    if dist is not None and dist.is_available() and dist.is_initialized():
+        world = dist.get_world_size()
+        tt = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return world * units_per_rank / t, t
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -199,12 +214,7 @@ def run_ours(args, rank, world, local_rank):
     kt = ctx.kernel_times()
     ctx.kernel_timing(False)
     ms = ms_total / args.steps
-    t_max = ms_total
-    if dist:
-        tt = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * units * args.steps / (t_max * 1e-3)
+    value, t_job = aggregate(units * args.steps, ms_total * 1e-3, dist, device="cuda")
 
     # end to end through the public API with host buffers (pinned): H2D state in, D2H state out
     he = torch.zeros(ctx.N1, dtype=tdt).pin_memory().numpy()
@@ -218,11 +228,7 @@ def run_ours(args, rank, world, local_rank):
         ctx.step(W["steps"], dt, src)
         ctx.get_state(synced=True, out_e=oe, out_b=ob)
     e2e_s = (time.perf_counter() - t0) / args.steps
-    e2e_val = units / e2e_s
-    if dist:
-        tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_val = world * units / float(tt.item())
+    e2e_val, _ = aggregate(units, e2e_s, dist, device="cuda")
     rs = 4 if prec == Y.YGM_FP32 else 8
 
     # roofline of the dominant kernel (Q1 apply): algorithmic bytes = unique symmetric Q1 values

@@ -146,6 +146,14 @@ int ygm_time(const ygm_ctx* ctx, int64_t* step, double* t);
  * set-up; columns sorted).  rowptr: N1 + 1 entries, colind / val: q1_nnz entries (host). */
 int ygm_export_q1(const ygm_ctx* ctx, int64_t* rowptr, int64_t* colind, double* val);
 
+/* Install a caller-supplied symmetric Q1 (CSR over the global numbering, FP64 host arrays,
+ * columns sorted; rowptr has N1 + 1 entries) in place of the SPAI: any symmetric Q1 keeps the
+ * map symplectic (Theorem symplecticity); it must be SPD for stability (Prop. stability).  Its
+ * pattern must lie inside this context's stencil (S(1), S(M1) or S(M1^2) of q1_pattern).  The
+ * SPD check and tau_CFL are recomputed; the state is kept.  Errors: YGM_EINVAL (pattern,
+ * symmetry, sizes), YGM_ENOTSPD.  Synchronises the context stream. */
+int ygm_set_q1(ygm_ctx* ctx, const int64_t* rowptr, const int64_t* colind, const double* val);
+
 /* SPD check of Q1 (Sec. 5.1, practical considerations): Lanczos estimates of the smallest and
  * largest eigenvalue before any shift, the diagonal shift applied (0 if none), lambda_max(Q1 P2),
  * and which pattern / basis was used (YGM_Q1_*, ortho = 1 for the orthogonalised basis). */

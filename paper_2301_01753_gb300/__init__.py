@@ -18,7 +18,7 @@ YGM_FP64, YGM_FP32 = 0, 1
 YGM_Q1_DEFAULT, YGM_Q1_DIAG, YGM_Q1_SM1, YGM_Q1_SM1SQ = 0, 1, 2, 3
 
 EXPORTED = ["ygm_create", "ygm_sizes", "ygm_set_state", "ygm_get_state", "ygm_project_E", "ygm_step",
-            "ygm_energy", "ygm_energy_history", "ygm_time", "ygm_export_q1", "ygm_q1_info",
+            "ygm_energy", "ygm_energy_history", "ygm_time", "ygm_export_q1", "ygm_set_q1", "ygm_q1_info",
             "ygm_local_blocks", "ygm_kernel_timing", "ygm_kernel_times", "ygm_launch_count",
             "ygm_last_error", "ygm_destroy"]
 KERNEL_KINDS = ["k_qapply", "k_curl_b", "k_curlT_e", "k_source", "k_energy"]
@@ -66,6 +66,7 @@ def load_library(path=LIB_PATH):
         "ygm_energy_history": (C.c_int, [P, pD, I64, pI64]),
         "ygm_time": (C.c_int, [P, pI64, pD]),
         "ygm_export_q1": (C.c_int, [P, pI64, pI64, pD]),
+        "ygm_set_q1": (C.c_int, [P, pI64, pI64, pD]),
         "ygm_q1_info": (C.c_int, [P, pD, pD, pD, pD, pI32, pI32]),
         "ygm_local_blocks": (C.c_int, [P, pI32, pI32, pD, pD]),
         "ygm_kernel_timing": (C.c_int, [P, C.c_int]),
@@ -207,6 +208,19 @@ class Context:
                                        ci.ctypes.data_as(C.POINTER(C.c_int64)),
                                        va.ctypes.data_as(C.POINTER(C.c_double))))
         return rp, ci, va
+
+    def set_q1(self, Q):
+        """Install a symmetric scipy.sparse Q1 (global numbering) in place of the SPAI."""
+        import scipy.sparse as sp
+        Q = sp.csr_matrix(Q)
+        Q.sort_indices()
+        rp = np.ascontiguousarray(Q.indptr, np.int64)
+        ci = np.ascontiguousarray(Q.indices, np.int64)
+        va = np.ascontiguousarray(Q.data, np.float64)
+        self._check(_lib.ygm_set_q1(self._h, rp.ctypes.data_as(C.POINTER(C.c_int64)),
+                                    ci.ctypes.data_as(C.POINTER(C.c_int64)),
+                                    va.ctypes.data_as(C.POINTER(C.c_double))))
+        self.N1, self.N2, self.q1_nnz, self.tau_cfl = self.sizes()
 
     def q1_info(self):
         lmin, lmax, sh, w2 = C.c_double(), C.c_double(), C.c_double(), C.c_double()

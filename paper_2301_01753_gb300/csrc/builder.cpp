@@ -46,6 +46,14 @@ static int default_threads(int t) {
     return h ? (int)h : 4;
 }
 
+// Two-wide double vectors (GCC vector extension: SSE2 on x86-64, NEON on aarch64).
+typedef double v2d __attribute__((vector_size(16)));
+static inline v2d ld2(const double* p) {
+    v2d v;
+    std::memcpy(&v, p, sizeof(v));
+    return v;
+}
+
 // Dense symmetric positive definite solve by Cholesky (in place); returns false if not SPD.
 // Row-major storage; the factor L overwrites the lower triangle (row i of L is contiguous).
 // The trailing update of each 4-column panel is done in 4 x 4 register tiles of dot products
@@ -63,18 +71,27 @@ static bool cholesky_solve(int m, double* A, double* b, int nrhs) {
                 const double* Li1 = Li0 + m;
                 const double* Li2 = Li1 + m;
                 const double* Li3 = Li2 + m;
-                double a00 = 0, a01 = 0, a02 = 0, a03 = 0, a10 = 0, a11 = 0, a12 = 0, a13 = 0;
-                double a20 = 0, a21 = 0, a22 = 0, a23 = 0, a30 = 0, a31 = 0, a32 = 0, a33 = 0;
-                for (int k = 0; k < j0; ++k) {
-                    const double b0 = Lj[0][k], b1 = Lj[1][k], b2 = Lj[2][k], b3 = Lj[3][k];
-                    const double x0 = Li0[k], x1 = Li1[k], x2 = Li2[k], x3 = Li3[k];
-                    a00 += x0 * b0; a01 += x0 * b1; a02 += x0 * b2; a03 += x0 * b3;
-                    a10 += x1 * b0; a11 += x1 * b1; a12 += x1 * b2; a13 += x1 * b3;
-                    a20 += x2 * b0; a21 += x2 * b1; a22 += x2 * b2; a23 += x2 * b3;
-                    a30 += x3 * b0; a31 += x3 * b1; a32 += x3 * b2; a33 += x3 * b3;
+                // 4 x 4 tile of dot products over k, two k at a time in 2-wide vectors
+                v2d c00 = {0, 0}, c01 = c00, c02 = c00, c03 = c00, c10 = c00, c11 = c00, c12 = c00, c13 = c00;
+                v2d c20 = c00, c21 = c00, c22 = c00, c23 = c00, c30 = c00, c31 = c00, c32 = c00, c33 = c00;
+                int k = 0;
+                for (; k + 2 <= j0; k += 2) {
+                    const v2d b0 = ld2(Lj[0] + k), b1 = ld2(Lj[1] + k), b2 = ld2(Lj[2] + k), b3 = ld2(Lj[3] + k);
+                    const v2d x0 = ld2(Li0 + k), x1 = ld2(Li1 + k), x2 = ld2(Li2 + k), x3 = ld2(Li3 + k);
+                    c00 += x0 * b0; c01 += x0 * b1; c02 += x0 * b2; c03 += x0 * b3;
+                    c10 += x1 * b0; c11 += x1 * b1; c12 += x1 * b2; c13 += x1 * b3;
+                    c20 += x2 * b0; c21 += x2 * b1; c22 += x2 * b2; c23 += x2 * b3;
+                    c30 += x3 * b0; c31 += x3 * b1; c32 += x3 * b2; c33 += x3 * b3;
                 }
-                const double acc[4][4] = {{a00, a01, a02, a03}, {a10, a11, a12, a13},
-                                          {a20, a21, a22, a23}, {a30, a31, a32, a33}};
+                double acc[4][4] = {{c00[0] + c00[1], c01[0] + c01[1], c02[0] + c02[1], c03[0] + c03[1]},
+                                    {c10[0] + c10[1], c11[0] + c11[1], c12[0] + c12[1], c13[0] + c13[1]},
+                                    {c20[0] + c20[1], c21[0] + c21[1], c22[0] + c22[1], c23[0] + c23[1]},
+                                    {c30[0] + c30[1], c31[0] + c31[1], c32[0] + c32[1], c33[0] + c33[1]}};
+                for (; k < j0; ++k) {
+                    const double xs[4] = {Li0[k], Li1[k], Li2[k], Li3[k]};
+                    for (int r = 0; r < 4; ++r)
+                        for (int c = 0; c < 4; ++c) acc[r][c] += xs[r] * Lj[c][k];
+                }
                 for (int r = 0; r < 4; ++r)
                     for (int c = 0; c < jb; ++c)
                         if (i0 + r >= j0 + c) A[(int64_t)(i0 + r) * m + j0 + c] -= acc[r][c];
@@ -1241,6 +1258,110 @@ int build_setup(Setup& S, int n, double side, int k, const double* eps, const do
         return -3;
     }
     return 0;
+}
+
+int refresh_spectrum(Setup& S, int threads_in) {
+    const int threads = default_threads(threads_in);
+    try {
+        Builder B(S, threads);
+        const int64_t N1 = S.L.N1;
+        auto qop = [&](const double* x, double* y) { S.Q1.matvec(x, y, threads); };
+        auto idop = [&](const double* x, double* y) { std::copy(x, x + N1, y); };
+        auto mm = B.lanczos(qop, idop, 300);
+        S.lmin = mm.first;
+        S.lmax = mm.second;
+        S.shift = 0;
+        if (!(S.lmin > 0)) {
+            S.err = "Q1 is not positive definite (Prop. stability needs SPD)";
+            return -3;
+        }
+        B.make_P2loc();
+        std::vector<double> tmp(N1);
+        auto kop = [&](const double* x, double* y) {
+            S.Q1.matvec(x, tmp.data(), threads);
+            B.P2_matvec(tmp.data(), y);
+        };
+        auto cfl = B.lanczos(kop, qop, 400);
+        S.omega_max_sq = cfl.second;
+        S.tau_cfl = 2.0 / std::sqrt(S.omega_max_sq);
+    } catch (const std::exception& ex) {
+        S.err = ex.what();
+        return -3;
+    }
+    return 0;
+}
+
+// ============================================================== user-supplied Q1
+int install_q1(Setup& S, const int64_t* rowptr, const int64_t* colind, const double* val, int threads_in) {
+    const int threads = default_threads(threads_in);
+    const Lattice& L = S.L;
+    const int64_t N1 = L.N1;
+    // slot lookup per class: (neighbour class, offset) -> present in the stencil
+    std::vector<std::map<std::array<int, 4>, int>> slot_of(L.c1.size());
+    for (size_t c = 0; c < L.c1.size(); ++c)
+        for (int s = S.st_begin[c]; s < S.st_begin[c + 1]; ++s) {
+            const auto& st = S.st_slots[s];
+            slot_of[c][{st.cls, st.d[0], st.d[1], st.d[2]}] = s;
+        }
+    Csr Q;
+    Q.nrows = Q.ncols = N1;
+    Q.ptr.assign(rowptr, rowptr + N1 + 1);
+    if (Q.ptr[0] != 0) {
+        S.err = "rowptr[0] must be 0";
+        return -1;
+    }
+    for (int64_t i = 0; i < N1; ++i)
+        if (Q.ptr[i + 1] < Q.ptr[i]) {
+            S.err = "rowptr must be non-decreasing";
+            return -1;
+        }
+    const int64_t nnz = Q.ptr[N1];
+    Q.col.assign(colind, colind + nnz);
+    Q.val.assign(val, val + nnz);
+    double vmax = 0;
+    for (int64_t i = 0; i < N1; ++i) {
+        int ci, vi[3];
+        L.decode1(i, &ci, vi);
+        for (int64_t p = Q.ptr[i]; p < Q.ptr[i + 1]; ++p) {
+            const int64_t j = Q.col[p];
+            if (j < 0 || j >= N1 || (p > Q.ptr[i] && Q.col[p - 1] >= j) || !std::isfinite(Q.val[p])) {
+                S.err = "Q1: column indices must be sorted, unique, in range; values finite";
+                return -1;
+            }
+            int cj, vj[3];
+            L.decode1(j, &cj, vj);
+            if (!slot_of[ci].count({cj, vj[0] - vi[0], vj[1] - vi[1], vj[2] - vi[2]})) {
+                S.err = "Q1 has an entry outside the stencil pattern of this context";
+                return -1;
+            }
+            vmax = std::max(vmax, std::fabs(Q.val[p]));
+        }
+    }
+    for (int64_t i = 0; i < N1; ++i)
+        for (int64_t p = Q.ptr[i]; p < Q.ptr[i + 1]; ++p)
+            if (std::fabs(Q.val[p] - Q.get(Q.col[p], i)) > 1e-14 * vmax) {
+                S.err = "Q1 must be symmetric";
+                return -1;
+            }
+    S.Q1 = std::move(Q);
+    // repack the stencil values
+    for (size_t c = 0; c < L.c1.size(); ++c) {
+        const Box& b = L.c1[c].box;
+        parallel_for(b.size, threads, [&](int64_t lo, int64_t hi, int) {
+            for (int64_t r = lo; r < hi; ++r) {
+                int v0 = (int)(r % b.num[0]) + b.lo[0];
+                int v1 = (int)((r / b.num[0]) % b.num[1]) + b.lo[1];
+                int v2 = (int)(r / ((int64_t)b.num[0] * b.num[1])) + b.lo[2];
+                for (int s = S.st_begin[c]; s < S.st_begin[c + 1]; ++s) {
+                    const auto& st = S.st_slots[s];
+                    if (!st.upper) continue;
+                    int64_t gj = L.index1(st.cls, v0 + st.d[0], v1 + st.d[1], v2 + st.d[2]);
+                    S.qvals[S.qoff[c] + (int64_t)st.slot * b.size + r] = gj >= 0 ? S.Q1.get(b.offset + r, gj) : 0.0;
+                }
+            }
+        });
+    }
+    return refresh_spectrum(S, threads);
 }
 
 // ============================================================== sources and projections

@@ -6,6 +6,7 @@
 // only ever see the packed tables produced at the end.
 #pragma once
 #include <array>
+#include <map>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -119,6 +120,11 @@ struct Setup {
 
 int build_setup(Setup& S, int n, double side, int k, const double* eps, const double* mu,
                 int q1_pattern, int threads);
+
+// Replace Q1 by a caller's symmetric matrix on this context's stencil pattern, repack the
+// device-facing values and recompute the SPD check and the CFL bound.
+int install_q1(Setup& S, const int64_t* rowptr, const int64_t* colind, const double* val, int threads);
+int refresh_spectrum(Setup& S, int threads);
 
 // Source vector of one dipole: tet index and the n1 weights d . Lambda1_i(x0) (global DoFs).
 int dipole_weights(const Setup& S, const double x[3], const double d[3], std::vector<int64_t>& dofs,

@@ -15,7 +15,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -112,6 +114,129 @@ __global__ void __launch_bounds__(BLOCK) k_qapply(Tables tb, const DRow* __restr
     }
 }
 
+// ------------------------------------------------------------------ x = Q1 e, tiled version
+// A warp owns a tile of TY consecutive y-rows (same class, same z) x 32 lanes along x.  Slot
+// descriptors carry everything warp-uniform (neighbour box, base offsets), so the per-lane
+// work per slot is one range check, two coalesced loads and one FMA per row of the tile.
+constexpr int TY = 4;
+struct QSlot {
+    int ux0, uy0, uz0;   // slot offset minus the neighbour box origin
+    int nx, ny, nz;      // neighbour box
+    long long ebase;     // first e index of the neighbour class
+    long long qbase;     // upper: own qoff + slot * own size; lower: neighbour qoff + slot * its size
+    int upper;
+    int pad;
+};
+struct QTile {
+    int cls;
+    int vy0, vz;         // first row of the tile (lattice coordinates)
+    int nrows;           // rows in the tile (<= TY)
+};
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_qapply_t(const DCls* __restrict__ c1, const QSlot* __restrict__ slots,
+                                                    const QTile* __restrict__ tiles, int ntiles,
+                                                    const real* __restrict__ q, const real* __restrict__ e,
+                                                    real* __restrict__ x) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile = blockIdx.x * WARPS_PER_BLOCK + warp;
+    if (tile >= ntiles) return;
+    const QTile Tl = tiles[tile];
+    const DCls C = c1[Tl.cls];
+    const int ry0 = Tl.vy0 - C.lo[1], rz = Tl.vz - C.lo[2];
+    for (int x0 = 0; x0 < C.num[0]; x0 += 32) {
+        const int ix = x0 + lane;
+        const bool act = ix < C.num[0];
+        const int vx = C.lo[0] + ix;
+        long long rb[TY];
+#pragma unroll
+        for (int t = 0; t < TY; ++t) rb[t] = ((long long)rz * C.num[1] + ry0 + t) * C.num[0] + ix;
+        real acc[TY];
+#pragma unroll
+        for (int t = 0; t < TY; ++t) acc[t] = real(0);
+        for (int s = C.st_begin; s < C.st_end; ++s) {
+            const QSlot S = slots[s];
+            const int uz = Tl.vz + S.uz0;
+            if (uz < 0 || uz >= S.nz) continue;                       // warp-uniform
+            const int ux = vx + S.ux0;
+            const bool xok = act && (unsigned)ux < (unsigned)S.nx;
+            real qv[TY], ev[TY];
+#pragma unroll
+            for (int t = 0; t < TY; ++t) {
+                const int uy = Tl.vy0 + t + S.uy0;
+                const bool ok = xok && t < Tl.nrows && (unsigned)uy < (unsigned)S.ny;
+                const long long nb = ((long long)uz * S.ny + uy) * S.nx + ux;
+                const long long qi = S.upper ? S.qbase + rb[t] : S.qbase + nb;
+                const long long ei = S.ebase + nb;
+                qv[t] = ok ? __ldg(q + qi) : real(0);
+                ev[t] = ok ? __ldg(e + ei) : real(0);
+            }
+#pragma unroll
+            for (int t = 0; t < TY; ++t) acc[t] = fma(qv[t], ev[t], acc[t]);
+        }
+        if (act) {
+#pragma unroll
+            for (int t = 0; t < TY; ++t)
+                if (t < Tl.nrows) x[C.off + rb[t]] = acc[t];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ e += ctau C^T M2 b, merged stencil
+// With a uniform permeability, C^T M2 is a constant-coefficient stencil from the curl-carrying
+// 2-forms to each 1-form class: the contributions of all tets around the entity are summed on
+// the host into one weight per (2-form class, offset).
+template <typename real>
+struct PTerm {
+    int ux0, uy0, uz0;
+    int nx, ny, nz;
+    long long bbase;
+    real w;
+};
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_curlT_e_t(const DCls* __restrict__ c1, const int* __restrict__ pbeg,
+                                                     const PTerm<real>* __restrict__ terms, const QTile* __restrict__ tiles,
+                                                     int ntiles, const real* __restrict__ b, real* e, real ctau) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile = blockIdx.x * WARPS_PER_BLOCK + warp;
+    if (tile >= ntiles) return;
+    const QTile Tl = tiles[tile];
+    const DCls C = c1[Tl.cls];
+    const int ry0 = Tl.vy0 - C.lo[1], rz = Tl.vz - C.lo[2];
+    const int tb = pbeg[Tl.cls], te = pbeg[Tl.cls + 1];
+    for (int x0 = 0; x0 < C.num[0]; x0 += 32) {
+        const int ix = x0 + lane;
+        const bool act = ix < C.num[0];
+        const int vx = C.lo[0] + ix;
+        real acc[TY];
+#pragma unroll
+        for (int t = 0; t < TY; ++t) acc[t] = real(0);
+        for (int s = tb; s < te; ++s) {
+            const PTerm<real> P = terms[s];
+            const int uz = Tl.vz + P.uz0;
+            if (uz < 0 || uz >= P.nz) continue;
+            const int ux = vx + P.ux0;
+            const bool xok = act && (unsigned)ux < (unsigned)P.nx;
+            real bv[TY];
+#pragma unroll
+            for (int t = 0; t < TY; ++t) {
+                const int uy = Tl.vy0 + t + P.uy0;
+                const bool ok = xok && t < Tl.nrows && (unsigned)uy < (unsigned)P.ny;
+                bv[t] = ok ? __ldg(b + P.bbase + ((long long)uz * P.ny + uy) * P.nx + ux) : real(0);
+            }
+#pragma unroll
+            for (int t = 0; t < TY; ++t) acc[t] = fma(P.w, bv[t], acc[t]);
+        }
+        if (act) {
+#pragma unroll
+            for (int t = 0; t < TY; ++t)
+                if (t < Tl.nrows) {
+                    const long long g = C.off + ((long long)rz * C.num[1] + ry0 + t) * C.num[0] + ix;
+                    e[g] = e[g] + ctau * acc[t];
+                }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ b_out = b_in - ctau C x
 template <typename real>
 __global__ void __launch_bounds__(BLOCK) k_curl_b(Tables tb, const DRow* __restrict__ rows, int nrows,
@@ -180,19 +305,17 @@ __global__ void __launch_bounds__(BLOCK) k_curlT_e(Tables tb, const DRow* __rest
 }
 
 // ------------------------------------------------------------------ point-dipole sources
+// amp[s] = dt * s_s(t_{n+1/2}) is computed on the host in FP64 for every step of a call.
 struct DSrc {
-    double amp, omega, t0, sigma;
     int begin, end;      // into the (dof, weight) lists
 };
 template <typename real>
 __global__ void k_source(const DSrc* __restrict__ src, int nsrc, const long long* __restrict__ dofs,
-                         const real* __restrict__ w, real* e, double t, double dt) {
+                         const real* __restrict__ w, const double* __restrict__ amp, real* e) {
     for (int s = 0; s < nsrc; ++s) {
         const DSrc S = src[s];
-        const double u = (t - S.t0) / S.sigma;
-        const double amp = S.amp * exp(-u * u) * sin(S.omega * (t - S.t0));
-        for (int i = S.begin + threadIdx.x; i < S.end; i += blockDim.x)
-            e[dofs[i]] = e[dofs[i]] - real(dt * amp) * w[i];
+        const real a = (real)amp[s];
+        for (int i = S.begin + threadIdx.x; i < S.end; i += blockDim.x) e[dofs[i]] = e[dofs[i]] - a * w[i];
         __syncthreads();
     }
 }
@@ -334,6 +457,17 @@ struct ygm_ctx {
     long long* sdofs = nullptr;
     int nsrc = 0, nsrc_cap = 0, nsw_cap = 0;
     std::vector<ygm_source> src_cache;
+    double* damp[2] = {nullptr, nullptr};    // per-step source amplitudes, double-buffered
+    double* hamp[2] = {nullptr, nullptr};    // pinned host staging of the same
+    size_t damp_cap[2] = {0, 0};
+    cudaEvent_t damp_ev[2] = {nullptr, nullptr};
+    int damp_cur = 0;
+    // tiled kernels
+    QSlot* qslots = nullptr;
+    QTile *tilesA = nullptr, *tilesE = nullptr;
+    int ntilesA = 0, ntilesE = 0;
+    void* pterms = nullptr;                  // PTerm<real> merged C^T M2 stencil (uniform mu)
+    int* pbeg = nullptr;
     // time state
     int cur = 0;
     bool staggered = false;
@@ -539,20 +673,103 @@ static int setup_device(ygm_ctx* ctx) {
     CK(cudaMalloc((void**)&ctx->hist, ctx->hist_cap * sizeof(double)));
     ctx->tb = Tables{ctx->c1, ctx->c2, ctx->slots, ctx->terms, ctx->inc, ctx->loc2, L.n, L.n1, L.n2a};
     (void)k;
+    // flattened Q1 slot descriptors
+    std::vector<QSlot> qs(S.st_slots.size());
+    for (size_t c = 0; c < L.c1.size(); ++c)
+        for (int sidx = S.st_begin[c]; sidx < S.st_begin[c + 1]; ++sidx) {
+            const auto& st = S.st_slots[sidx];
+            const auto& D = L.c1[st.cls].box;
+            QSlot& Q = qs[sidx];
+            Q.ux0 = st.d[0] - D.lo[0];
+            Q.uy0 = st.d[1] - D.lo[1];
+            Q.uz0 = st.d[2] - D.lo[2];
+            Q.nx = D.num[0];
+            Q.ny = D.num[1];
+            Q.nz = D.num[2];
+            Q.ebase = D.offset;
+            Q.qbase = st.upper ? S.qoff[c] + (int64_t)st.slot * L.c1[c].box.size : S.qoff[st.cls] + (int64_t)st.slot * D.size;
+            Q.upper = st.upper;
+            Q.pad = 0;
+        }
+    if ((rc = upload(ctx, &ctx->qslots, qs))) return rc;
+    auto make_tiles = [&](bool active_only) {
+        std::vector<QTile> t;
+        for (int vz = 0; vz < L.n; ++vz)
+            for (int j = 0; j * TY < L.n; ++j)
+                for (int c = 0; c < (int)L.c1.size(); ++c) {
+                    const auto& b = L.c1[c].box;
+                    if (active_only && !L.c1[c].active) continue;
+                    if (vz < b.lo[2] || vz >= b.lo[2] + b.num[2] || b.num[0] == 0) continue;
+                    int vy0 = b.lo[1] + j * TY;
+                    if (vy0 >= b.lo[1] + b.num[1]) continue;
+                    t.push_back(QTile{c, vy0, vz, std::min(TY, b.lo[1] + b.num[1] - vy0)});
+                }
+        return t;
+    };
+    std::vector<QTile> tA = make_tiles(false), tE = make_tiles(true);
+    ctx->ntilesA = (int)tA.size();
+    ctx->ntilesE = (int)tE.size();
+    if ((rc = upload(ctx, &ctx->tilesA, tA)) || (rc = upload(ctx, &ctx->tilesE, tE))) return rc;
+    // merged C^T M2 stencil when mu is uniform
+    double mu0 = S.mu.empty() ? 1.0 : S.mu[0];
+    bool mu_uniform = true;
+    for (double m : S.mu) mu_uniform &= (m == mu0);
+    if (mu_uniform) {
+        std::vector<int> pbeg(L.c1.size() + 1, 0);
+        std::vector<std::pair<ygm::Nbr, double>> all;
+        std::vector<std::vector<std::pair<ygm::Nbr, double>>> per(L.c1.size());
+        for (size_t c = 0; c < L.c1.size(); ++c) {
+            if (!L.c1[c].active) continue;
+            std::map<ygm::Nbr, double> acc;
+            for (auto& I : L.inc1[c])
+                for (int ra = 0; ra < L.n2a; ++ra) {
+                    const auto& L2 = L.loc2[I.shape][L.act2[ra]];
+                    ygm::Nbr nb{L2.cls, {I.dcube[0] + L2.off[0], I.dcube[1] + L2.off[1], I.dcube[2] + L2.off[2]}};
+                    acc[nb] += S.Wloc[(size_t)I.loc * L.n2a + ra] / mu0;
+                }
+            for (auto& kv : acc) per[c].push_back(kv);
+        }
+        for (size_t c = 0; c < L.c1.size(); ++c) {
+            pbeg[c] = (int)all.size();
+            all.insert(all.end(), per[c].begin(), per[c].end());
+        }
+        pbeg[L.c1.size()] = (int)all.size();
+        auto fill = [&](auto* dummy) {
+            using R = std::remove_pointer_t<decltype(dummy)>;
+            std::vector<PTerm<R>> pt(all.size());
+            for (size_t i = 0; i < all.size(); ++i) {
+                const auto& nb = all[i].first;
+                const auto& D = L.c2[nb.cls].box;
+                pt[i] = PTerm<R>{nb.d[0] - D.lo[0], nb.d[1] - D.lo[1], nb.d[2] - D.lo[2], D.num[0], D.num[1], D.num[2],
+                                 (long long)D.offset, (R)all[i].second};
+            }
+            PTerm<R>* d = nullptr;
+            int r2 = upload(ctx, &d, pt);
+            ctx->pterms = d;
+            return r2;
+        };
+        if (ctx->precision == YGM_FP64) {
+            if ((rc = fill((double*)nullptr))) return rc;
+        } else {
+            if ((rc = fill((float*)nullptr))) return rc;
+        }
+        if ((rc = upload(ctx, &ctx->pbeg, pbeg))) return rc;
+    }
+    for (int i = 0; i < 2; ++i) CK(cudaEventCreateWithFlags(&ctx->damp_ev[i], cudaEventDisableTiming));
     CK(cudaStreamSynchronize(ctx->stream));
     return 0;
 }
 
 // ------------------------------------------------------------------ launch helpers
 static int launch_qapply(ygm_ctx* ctx, const void* e, void* x) {
-    dim3 g((ctx->nrowsA + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+    dim3 g((ctx->ntilesA + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
     time_begin(ctx, KQ);
     if (ctx->precision == YGM_FP64)
-        k_qapply<double><<<g, BLOCK, 0, ctx->stream>>>(ctx->tb, ctx->rowsA, ctx->nrowsA, (const double*)ctx->q,
-                                                       (const double*)e, (double*)x);
+        k_qapply_t<double><<<g, BLOCK, 0, ctx->stream>>>(ctx->c1, ctx->qslots, ctx->tilesA, ctx->ntilesA,
+                                                         (const double*)ctx->q, (const double*)e, (double*)x);
     else
-        k_qapply<float><<<g, BLOCK, 0, ctx->stream>>>(ctx->tb, ctx->rowsA, ctx->nrowsA, (const float*)ctx->q,
-                                                      (const float*)e, (float*)x);
+        k_qapply_t<float><<<g, BLOCK, 0, ctx->stream>>>(ctx->c1, ctx->qslots, ctx->tilesA, ctx->ntilesA,
+                                                        (const float*)ctx->q, (const float*)e, (float*)x);
     time_end(ctx);
     ctx->launches++;
     return 0;
@@ -571,27 +788,39 @@ static int launch_curl_b(ygm_ctx* ctx, const void* x, const void* bin, void* bou
     return 0;
 }
 static int launch_curlT_e(ygm_ctx* ctx, const void* b, void* e, double ctau) {
-    dim3 g((ctx->nrowsE + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
     time_begin(ctx, KE);
-    if (ctx->precision == YGM_FP64)
-        k_curlT_e<double><<<g, BLOCK, 0, ctx->stream>>>(ctx->tb, ctx->rowsE, ctx->nrowsE, (const double*)ctx->W,
-                                                        (const double*)b, (const double*)ctx->inv_mu, (double*)e, ctau);
-    else
-        k_curlT_e<float><<<g, BLOCK, 0, ctx->stream>>>(ctx->tb, ctx->rowsE, ctx->nrowsE, (const float*)ctx->W,
-                                                       (const float*)b, (const float*)ctx->inv_mu, (float*)e, (float)ctau);
+    if (ctx->pterms) {
+        dim3 g((ctx->ntilesE + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+        if (ctx->precision == YGM_FP64)
+            k_curlT_e_t<double><<<g, BLOCK, 0, ctx->stream>>>(ctx->c1, ctx->pbeg, (const PTerm<double>*)ctx->pterms,
+                                                              ctx->tilesE, ctx->ntilesE, (const double*)b, (double*)e, ctau);
+        else
+            k_curlT_e_t<float><<<g, BLOCK, 0, ctx->stream>>>(ctx->c1, ctx->pbeg, (const PTerm<float>*)ctx->pterms,
+                                                             ctx->tilesE, ctx->ntilesE, (const float*)b, (float*)e,
+                                                             (float)ctau);
+    } else {
+        dim3 g((ctx->nrowsE + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+        if (ctx->precision == YGM_FP64)
+            k_curlT_e<double><<<g, BLOCK, 0, ctx->stream>>>(ctx->tb, ctx->rowsE, ctx->nrowsE, (const double*)ctx->W,
+                                                            (const double*)b, (const double*)ctx->inv_mu, (double*)e, ctau);
+        else
+            k_curlT_e<float><<<g, BLOCK, 0, ctx->stream>>>(ctx->tb, ctx->rowsE, ctx->nrowsE, (const float*)ctx->W,
+                                                           (const float*)b, (const float*)ctx->inv_mu, (float*)e,
+                                                           (float)ctau);
+    }
     time_end(ctx);
     ctx->launches++;
     return 0;
 }
-static int launch_source(ygm_ctx* ctx, double t, double dt) {
+static int launch_source(ygm_ctx* ctx, const double* amp_dev) {
     if (!ctx->nsrc) return 0;
     time_begin(ctx, KS);
     if (ctx->precision == YGM_FP64)
-        k_source<double><<<1, 256, 0, ctx->stream>>>(ctx->dsrc, ctx->nsrc, ctx->sdofs, (const double*)ctx->sw,
-                                                     (double*)ctx->e, t, dt);
+        k_source<double><<<1, 256, 0, ctx->stream>>>(ctx->dsrc, ctx->nsrc, ctx->sdofs, (const double*)ctx->sw, amp_dev,
+                                                     (double*)ctx->e);
     else
-        k_source<float><<<1, 256, 0, ctx->stream>>>(ctx->dsrc, ctx->nsrc, ctx->sdofs, (const float*)ctx->sw,
-                                                    (float*)ctx->e, t, dt);
+        k_source<float><<<1, 256, 0, ctx->stream>>>(ctx->dsrc, ctx->nsrc, ctx->sdofs, (const float*)ctx->sw, amp_dev,
+                                                    (float*)ctx->e);
     time_end(ctx);
     ctx->launches++;
     return 0;
@@ -786,7 +1015,7 @@ static int set_sources(ygm_ctx* ctx, const ygm_source* src, int32_t n_src) {
         std::vector<int64_t> d;
         std::vector<double> ww;
         if (ygm::dipole_weights(ctx->S, s.x, s.d, d, ww)) return fail(ctx, YGM_EINVAL, "source not located");
-        DSrc ds{s.amp, s.omega, s.t0, s.sigma, (int)dofs.size(), 0};
+        DSrc ds{(int)dofs.size(), 0};
         for (size_t j = 0; j < d.size(); ++j) {
             dofs.push_back(d[j] * ctx->n_rhs + s.rhs);
             w.push_back(ww[j]);
@@ -834,6 +1063,40 @@ int ygm_step(ygm_ctx* ctx, int64_t n, double dt, const ygm_source* src, int32_t 
         ctx->step_base = ctx->step;
     }
     ctx->dt_prev = dt;
+    // source amplitudes dt * s(t_{n+1/2}) for every step of this call (host, FP64); steps whose
+    // amplitudes are all exactly 0.0 need no source launch (the update would add 0)
+    const double* amp_dev = nullptr;
+    std::vector<char> src_on;
+    if (ctx->nsrc && n > 0) {
+        const int nsrc = ctx->nsrc;
+        const size_t namp = (size_t)n * nsrc;
+        int bsel = ctx->damp_cur;
+        ctx->damp_cur ^= 1;
+        CK(cudaEventSynchronize(ctx->damp_ev[bsel]));   // the buffer's previous readers are done
+        if (ctx->damp_cap[bsel] < namp) {
+            cudaFree(ctx->damp[bsel]);
+            cudaFreeHost(ctx->hamp[bsel]);
+            ctx->damp[bsel] = nullptr;
+            ctx->hamp[bsel] = nullptr;
+            CK(cudaMalloc((void**)&ctx->damp[bsel], namp * sizeof(double)));
+            CK(cudaMallocHost((void**)&ctx->hamp[bsel], namp * sizeof(double)));
+            ctx->damp_cap[bsel] = namp;
+        }
+        double* amp = ctx->hamp[bsel];
+        src_on.assign(n, 0);
+        for (int64_t i = 0; i < n; ++i) {
+            const double t = ctx->t_base + ((double)(ctx->step + i - ctx->step_base) + 0.5) * dt;
+            for (int q = 0; q < nsrc; ++q) {
+                const ygm_source& S0 = ctx->src_cache[q];
+                const double u = (t - S0.t0) / S0.sigma;
+                const double a = dt * S0.amp * std::exp(-u * u) * std::sin(S0.omega * (t - S0.t0));
+                amp[(size_t)i * nsrc + q] = a;
+                if (a != 0.0) src_on[i] = 1;
+            }
+        }
+        CK(cudaMemcpyAsync(ctx->damp[bsel], amp, namp * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        amp_dev = ctx->damp[bsel];
+    }
     for (int64_t i = 0; i < n; ++i) {
         void* bo = ctx->b[ctx->cur];
         void* bn = ctx->b[ctx->cur ^ 1];
@@ -842,10 +1105,11 @@ int ygm_step(ygm_ctx* ctx, int64_t n, double dt, const ygm_source* src, int32_t 
         if (ctx->energy_every && ctx->step % ctx->energy_every == 0 && ctx->hist_n < ctx->hist_cap - 2)
             launch_energy(ctx, ctx->e, ctx->x, bn, bo, ctx->hist + ctx->hist_n++);
         launch_curlT_e(ctx, bn, ctx->e, dt);
-        launch_source(ctx, ctx->t_base + ((double)(ctx->step - ctx->step_base) + 0.5) * dt, dt);
+        if (amp_dev && src_on[i]) launch_source(ctx, amp_dev + (size_t)i * ctx->nsrc);
         ctx->cur ^= 1;
         ctx->step++;
     }
+    if (amp_dev) CK(cudaEventRecord(ctx->damp_ev[ctx->damp_cur ^ 1], ctx->stream));
     CK(cudaGetLastError());
     return YGM_OK;
 }
@@ -899,6 +1163,19 @@ int ygm_export_q1(const ygm_ctx* ctx, int64_t* rowptr, int64_t* colind, double* 
     std::copy(Q.ptr.begin(), Q.ptr.end(), rowptr);
     std::copy(Q.col.begin(), Q.col.end(), colind);
     std::copy(Q.val.begin(), Q.val.end(), val);
+    return YGM_OK;
+}
+
+int ygm_set_q1(ygm_ctx* ctx, const int64_t* rowptr, const int64_t* colind, const double* val) {
+    if (!ctx || !rowptr || !colind || !val) return fail(ctx, YGM_EINVAL, "NULL argument");
+    int rc = ygm::install_q1(ctx->S, rowptr, colind, val, 0);
+    if (rc) return fail(ctx, rc == -1 ? YGM_EINVAL : YGM_ENOTSPD, ctx->S.err);
+    if (!ctx->host_only) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        cudaFree(ctx->q);
+        ctx->q = nullptr;
+        if ((rc = upload_real(ctx, &ctx->q, ctx->S.qvals))) return rc;
+    }
     return YGM_OK;
 }
 
@@ -968,6 +1245,14 @@ void ygm_destroy(ygm_ctx* ctx) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
+    for (int i = 0; i < 2; ++i) {
+        if (ctx->damp_ev[i]) cudaEventDestroy(ctx->damp_ev[i]);
+        if (ctx->damp[i]) cudaFree(ctx->damp[i]);
+        if (ctx->hamp[i]) cudaFreeHost(ctx->hamp[i]);
+    }
+    void* more[] = {ctx->qslots, ctx->tilesA, ctx->tilesE, ctx->pterms, ctx->pbeg};
+    for (void* p : more)
+        if (p) cudaFree(p);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
