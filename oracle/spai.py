@@ -179,3 +179,116 @@ def gym_q1(fem, M1=None, pattern_kind=None, basis_kind=None):
         raise ValueError(basis_kind)
     Q, lmin, lmax, shift = spd_shift(Q)
     return Q, dict(lmin=lmin, lmax=lmax, shift=shift, nnz=Q.nnz, pattern=pattern_kind, basis=basis_kind)
+
+
+# ----------------------------------------------------------------------------
+# Sampled rows of Q1 on large meshes (the same definitions, evaluated locally)
+# ----------------------------------------------------------------------------
+
+class LocalQ1:
+    """Rows of the default-policy Q1 computed one by one from their neighbourhood, for meshes
+    where the whole SPAI is too slow in Python.  Same steps as gym_q1: structural pattern,
+    entity Lowdin basis (k >= 2 with S(M1^2)), column SPAI (Eq. NormalEqSolve), symmetrisation."""
+
+    def __init__(self, fem, M1, pattern_kind=None):
+        self.fem = fem
+        self.M1 = sp.csr_matrix(M1)
+        k = fem.mesh.k
+        self.kind = pattern_kind or default_policy(k)[0]
+        self.ortho = basis_for(k, self.kind) == "ortho"
+        # entity group of every DoF (tuple of the entity's DoFs)
+        self.group = {}
+        for g in sum(entity_groups(fem), []):
+            for i in g:
+                self.group[i] = g
+        self._T = {}
+        self._col = {}
+        self._mp = {}
+
+    def s1(self, i):
+        M = self.M1
+        return M.indices[M.indptr[i]:M.indptr[i + 1]]
+
+    def pattern_row(self, i):
+        if self.kind == "diag":
+            return np.array([i])
+        if self.kind == "sm1":
+            return np.sort(self.s1(i))
+        return np.unique(np.concatenate([self.s1(m) for m in self.s1(i)]))
+
+    def T_block(self, g):
+        if g not in self._T:
+            if self.ortho:
+                w, V = np.linalg.eigh(self.M1[list(g)][:, list(g)].toarray())
+                self._T[g] = (V / np.sqrt(w)) @ V.T
+            else:
+                self._T[g] = np.eye(len(g))
+        return self._T[g]
+
+    def Mp_col(self, c):
+        """Column c of M' = T M1 T^T as a dict {row: value} (cached)."""
+        if c in self._mp:
+            return self._mp[c]
+        gc = self.group[c]
+        Tc = self.T_block(gc)
+        jc = gc.index(c)
+        # M1 T^T column c: sum_b M1[:, b] T[c, b] over b in the group of c
+        col = {}
+        for bb, b in enumerate(gc):
+            t = Tc[jc, bb]
+            if t == 0.0:
+                continue
+            M = self.M1
+            for p in range(M.indptr[b], M.indptr[b + 1]):
+                col[M.indices[p]] = col.get(M.indices[p], 0.0) + M.data[p] * t
+        out = {}
+        for r0, v in col.items():
+            g = self.group[r0]
+            Tg = self.T_block(g)
+            j0 = g.index(r0)
+            for aa, a in enumerate(g):
+                out[a] = out.get(a, 0.0) + Tg[aa, j0] * v
+        self._mp[c] = out
+        return out
+
+    def column(self, l):
+        """q'_l on its pattern (dict row -> value), Eq. NormalEqSolve in the primed basis."""
+        if l not in self._col:
+            I = self.pattern_row(l)
+            cols = [self.Mp_col(int(i)) for i in I]
+            rows = sorted(set().union(*[c.keys() for c in cols]))
+            ridx = {r: n for n, r in enumerate(rows)}
+            A = np.zeros((len(rows), len(I)))
+            for p, c in enumerate(cols):
+                for r, v in c.items():
+                    A[ridx[r], p] = v
+            rhs = np.zeros(len(rows))
+            if l in ridx:
+                rhs[ridx[l]] = 1.0
+            q = np.linalg.solve(A.T @ A, A.T @ rhs)
+            self._col[l] = dict(zip((int(i) for i in I), q))
+        return self._col[l]
+
+    def qp(self, a, b):
+        """Symmetrised primed entry Q'(a, b) = (q'_b[a] + q'_a[b]) / 2."""
+        return 0.5 * (self.column(b).get(a, 0.0) + self.column(a).get(b, 0.0))
+
+    def row(self, i):
+        """Row i of Q1 = T^T Q' T as a dict {column: value}."""
+        gi = self.group[i]
+        Ti = self.T_block(gi)
+        ji = gi.index(i)
+        out = {}
+        for aa, a in enumerate(gi):
+            ta = Ti[aa, ji]
+            for b in self.pattern_row(a):
+                b = int(b)
+                gb = self.group[b]
+                Tb = self.T_block(gb)
+                v = ta * self.qp(a, b)
+                if v == 0.0:
+                    continue
+                jb = gb.index(b)
+                for cc, c in enumerate(gb):
+                    out[c] = out.get(c, 0.0) + v * Tb[jb, cc]
+        return out
