@@ -181,6 +181,86 @@ __global__ void __launch_bounds__(BLOCK) k_qapply_t(const DCls* __restrict__ c1,
     }
 }
 
+// ------------------------------------------------------------------ x = Q1 e, block per (z, class)
+// A block owns one z-plane of one class; its warps take y-tiles of TY rows (32 lanes along x).
+// The class's slot descriptors are staged in shared memory once; the slot loop is straight
+// line (validity folded into predicates) and unrolled, so many independent loads are in
+// flight per thread -- the kernel is meant to stream Q1 at HBM speed.
+struct QBlock {
+    int cls;
+    int vz;
+};
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_qapply_b(const DCls* __restrict__ c1, const QSlot* __restrict__ slots,
+                                                    const QBlock* __restrict__ blocks, int max_slots,
+                                                    const real* __restrict__ q, const real* __restrict__ e,
+                                                    real* __restrict__ x) {
+    extern __shared__ long long smem_q[];
+    long long (*s_l)[2] = reinterpret_cast<long long (*)[2]>(smem_q);            // ebase, qbase
+    int (*s_i)[8] = reinterpret_cast<int (*)[8]>(smem_q + 2 * (size_t)max_slots); // ux0 uy0 uz0 nx ny nz upper -
+    const QBlock Bk = blocks[blockIdx.x];
+    const DCls C = c1[Bk.cls];
+    const int ns = C.st_end - C.st_begin;
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+        const QSlot S = slots[C.st_begin + s];
+        s_i[s][0] = S.ux0;
+        s_i[s][1] = S.uy0;
+        s_i[s][2] = S.uz0;
+        s_i[s][3] = S.nx;
+        s_i[s][4] = S.ny;
+        s_i[s][5] = S.nz;
+        s_i[s][6] = S.upper;
+        s_i[s][7] = 0;
+        s_l[s][0] = S.ebase;
+        s_l[s][1] = S.qbase;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const int rz = Bk.vz - C.lo[2];
+    const int cnx = C.num[0];
+    for (int ry0 = warp * TY; ry0 < C.num[1]; ry0 += nwarps * TY) {
+        const int vy0 = C.lo[1] + ry0;
+        const int nrows = min(TY, C.num[1] - ry0);
+        for (int x0 = 0; x0 < cnx; x0 += 32) {
+            const int ix = x0 + lane;
+            const bool act = ix < cnx;
+            const int vx = C.lo[0] + ix;
+            const long long own0 = ((long long)rz * C.num[1] + ry0) * cnx + ix;   // own index, row t = 0
+            real acc[TY];
+#pragma unroll
+            for (int t = 0; t < TY; ++t) acc[t] = real(0);
+#pragma unroll 4
+            for (int s = 0; s < ns; ++s) {
+                const int4 a0 = *reinterpret_cast<const int4*>(&s_i[s][0]);     // ux0 uy0 uz0 nx
+                const int4 a1 = *reinterpret_cast<const int4*>(&s_i[s][4]);     // ny nz upper -
+                const longlong2 bb = *reinterpret_cast<const longlong2*>(&s_l[s][0]);
+                const int uz = Bk.vz + a0.z;
+                const int uy0 = vy0 + a0.y;
+                const int tlo = -uy0, thi = min(nrows, a1.x - uy0);           // valid rows: tlo <= t < thi
+                const int ux = vx + a0.x;
+                const bool okl = act && (unsigned)ux < (unsigned)a0.w && (unsigned)uz < (unsigned)a1.y;
+                const long long nb0 = ((long long)uz * a1.x + uy0) * a0.w + ux;
+                const long long qi0 = a1.z ? bb.y + own0 : bb.y + nb0;
+                const long long qst = a1.z ? cnx : a0.w;
+                const long long ei0 = bb.x + nb0;
+#pragma unroll
+                for (int t = 0; t < TY; ++t) {
+                    const bool ok = okl && t >= tlo && t < thi;
+                    const real qv = ok ? __ldg(q + qi0 + t * qst) : real(0);
+                    const real ev = ok ? __ldg(e + ei0 + (long long)t * a0.w) : real(0);
+                    acc[t] = fma(qv, ev, acc[t]);
+                }
+            }
+            if (act) {
+#pragma unroll
+                for (int t = 0; t < TY; ++t)
+                    if (t < nrows) x[C.off + own0 + (long long)t * cnx] = acc[t];
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ e += ctau C^T M2 b, merged stencil
 // With a uniform permeability, C^T M2 is a constant-coefficient stencil from the curl-carrying
 // 2-forms to each 1-form class: the contributions of all tets around the entity are summed on
@@ -301,6 +381,124 @@ __global__ void __launch_bounds__(BLOCK) k_curlT_e(Tables tb, const DRow* __rest
         }
         const long long g = C.off + R.rbase + ix;
         e[g] = e[g] + ctau * acc;
+    }
+}
+
+// ------------------------------------------------------------------ e += ctau C^T M2 b, block per (z, class)
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_curlT_e_b(const DCls* __restrict__ c1, const int* __restrict__ pbeg,
+                                                     const PTerm<real>* __restrict__ terms, const QBlock* __restrict__ blocks,
+                                                     int max_terms, const real* __restrict__ b, real* e, real ctau) {
+    extern __shared__ long long smem_p[];
+    long long* s_b = smem_p;                                               // bbase
+    real* s_w = reinterpret_cast<real*>(smem_p + max_terms);                // weight
+    int (*s_i)[6] = reinterpret_cast<int (*)[6]>(s_w + max_terms + (max_terms & 1));
+    const QBlock Bk = blocks[blockIdx.x];
+    const DCls C = c1[Bk.cls];
+    const int tb = pbeg[Bk.cls], nt = pbeg[Bk.cls + 1] - tb;
+    for (int s = threadIdx.x; s < nt; s += blockDim.x) {
+        const PTerm<real> P = terms[tb + s];
+        s_b[s] = P.bbase;
+        s_w[s] = P.w;
+        s_i[s][0] = P.ux0;
+        s_i[s][1] = P.uy0;
+        s_i[s][2] = P.uz0;
+        s_i[s][3] = P.nx;
+        s_i[s][4] = P.ny;
+        s_i[s][5] = P.nz;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rz = Bk.vz - C.lo[2];
+    for (int ry0 = warp * TY; ry0 < C.num[1]; ry0 += WARPS_PER_BLOCK * TY) {
+        const int vy0 = C.lo[1] + ry0;
+        const int nrows = min(TY, C.num[1] - ry0);
+        for (int x0 = 0; x0 < C.num[0]; x0 += 32) {
+            const int ix = x0 + lane;
+            const bool act = ix < C.num[0];
+            const int vx = C.lo[0] + ix;
+            real acc[TY];
+#pragma unroll
+            for (int t = 0; t < TY; ++t) acc[t] = real(0);
+#pragma unroll 4
+            for (int s = 0; s < nt; ++s) {
+                const int ux = vx + s_i[s][0];
+                const int uz = Bk.vz + s_i[s][2];
+                const int nx = s_i[s][3], ny = s_i[s][4];
+                const bool okxz = act && (unsigned)ux < (unsigned)nx && (unsigned)uz < (unsigned)s_i[s][5];
+                const long long nb0 = s_b[s] + ((long long)uz * ny + vy0 + s_i[s][1]) * nx + ux;
+                const real w = s_w[s];
+#pragma unroll
+                for (int t = 0; t < TY; ++t) {
+                    const int uy = vy0 + t + s_i[s][1];
+                    const bool ok = okxz && t < nrows && (unsigned)uy < (unsigned)ny;
+                    const real bv = ok ? __ldg(b + nb0 + (long long)t * nx) : real(0);
+                    acc[t] = fma(w, bv, acc[t]);
+                }
+            }
+            if (act) {
+                const long long g0 = C.off + ((long long)rz * C.num[1] + ry0) * C.num[0] + ix;
+#pragma unroll
+                for (int t = 0; t < TY; ++t)
+                    if (t < nrows) {
+                        const long long g = g0 + (long long)t * C.num[0];
+                        e[g] = e[g] + ctau * acc[t];
+                    }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ b_out = b_in - ctau C x, block per (z, class)
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_curl_b_b(const DCls* __restrict__ c1, const DCls* __restrict__ c2,
+                                                    const DTerm* __restrict__ terms, const QBlock* __restrict__ blocks,
+                                                    const real* __restrict__ x, const real* b_in, real* b_out, real ctau) {
+    const QBlock Bk = blocks[blockIdx.x];
+    const DCls C = c2[Bk.cls];
+    const int nt = C.st_end - C.st_begin;
+    // at most three signed terms per row (Whitney incidence) or one (curl of a higher-order 1-form)
+    int t_ux0[3], t_uy0[3], t_uz0[3], t_nx[3], t_ny[3], t_nz[3], t_sg[3];
+    long long t_off[3];
+    for (int s = 0; s < 3; ++s) {
+        if (s < nt) {
+            const DTerm Tm = terms[C.st_begin + s];
+            const DCls D = c1[Tm.cls];
+            t_ux0[s] = Tm.d[0] - D.lo[0];
+            t_uy0[s] = Tm.d[1] - D.lo[1];
+            t_uz0[s] = Tm.d[2] - D.lo[2];
+            t_nx[s] = D.num[0];
+            t_ny[s] = D.num[1];
+            t_nz[s] = D.num[2];
+            t_off[s] = D.off;
+            t_sg[s] = Tm.sign;
+        } else {
+            t_ux0[s] = t_uy0[s] = t_uz0[s] = 0;
+            t_nx[s] = t_ny[s] = t_nz[s] = 0;      // never valid
+            t_off[s] = 0;
+            t_sg[s] = 0;
+        }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rz = Bk.vz - C.lo[2];
+    for (int ry = warp; ry < C.num[1]; ry += WARPS_PER_BLOCK) {
+        const int vy = C.lo[1] + ry;
+        for (int x0 = 0; x0 < C.num[0]; x0 += 32) {
+            const int ix = x0 + lane;
+            if (ix >= C.num[0]) break;
+            const int vx = C.lo[0] + ix;
+            real acc = real(0);
+#pragma unroll
+            for (int s = 0; s < 3; ++s) {
+                const int ux = vx + t_ux0[s], uy = vy + t_uy0[s], uz = Bk.vz + t_uz0[s];
+                const bool ok = (unsigned)ux < (unsigned)t_nx[s] && (unsigned)uy < (unsigned)t_ny[s] &&
+                                (unsigned)uz < (unsigned)t_nz[s];
+                const real xv = ok ? __ldg(x + t_off[s] + ((long long)uz * t_ny[s] + uy) * t_nx[s] + ux) : real(0);
+                acc += t_sg[s] > 0 ? xv : -xv;
+            }
+            const long long g = C.off + ((long long)rz * C.num[1] + ry) * C.num[0] + ix;
+            b_out[g] = b_in[g] - ctau * acc;
+        }
     }
 }
 
@@ -464,6 +662,10 @@ struct ygm_ctx {
     int damp_cur = 0;
     // tiled kernels
     QSlot* qslots = nullptr;
+    QBlock* qblocks = nullptr;
+    int nqblocks = 0, max_slots = 0, qthreads = BLOCK;
+    QBlock *eblocks = nullptr, *bblocks = nullptr;
+    int neblocks = 0, nbblocks = 0, max_terms = 0;
     QTile *tilesA = nullptr, *tilesE = nullptr;
     int ntilesA = 0, ntilesE = 0;
     void* pterms = nullptr;                  // PTerm<real> merged C^T M2 stencil (uniform mu)
@@ -509,6 +711,11 @@ static void time_end(ygm_ctx* ctx) {
 
 static std::string g_create_err;
 static std::mutex g_err_mutex;
+// largest dynamic shared memory each block kernel has been opted in to, per precision
+// (cudaFuncSetAttribute limits are per kernel and process-wide; only ever raised); single-device
+// use assumed for the bookkeeping (the attribute is set on the current device)
+static std::mutex g_smem_mutex;
+static size_t g_smem_q[2] = {48 * 1024, 48 * 1024}, g_smem_e[2] = {48 * 1024, 48 * 1024};
 
 #define CK(call)                                                                                   \
     do {                                                                                           \
@@ -706,6 +913,34 @@ static int setup_device(ygm_ctx* ctx) {
                 }
         return t;
     };
+    std::vector<QBlock> qb;
+    for (int vz = 0; vz < L.n; ++vz)
+        for (int c = 0; c < (int)L.c1.size(); ++c) {
+            const auto& b = L.c1[c].box;
+            if (vz < b.lo[2] || vz >= b.lo[2] + b.num[2] || b.num[0] == 0 || b.num[1] == 0) continue;
+            qb.push_back(QBlock{c, vz});
+        }
+    ctx->nqblocks = (int)qb.size();
+    // k_qapply_b: one warp per TY y-rows of the class box, at most 8 warps per block
+    ctx->qthreads = 32 * std::max(1, std::min(WARPS_PER_BLOCK, (L.n + TY - 1) / TY));
+    if ((rc = upload(ctx, &ctx->qblocks, qb))) return rc;
+    for (size_t c = 0; c < L.c1.size(); ++c) ctx->max_slots = std::max(ctx->max_slots, S.st_begin[c + 1] - S.st_begin[c]);
+    std::vector<QBlock> eb, bb;
+    for (int vz = 0; vz < L.n; ++vz) {
+        for (int c = 0; c < (int)L.c1.size(); ++c) {
+            const auto& b = L.c1[c].box;
+            if (!L.c1[c].active || vz < b.lo[2] || vz >= b.lo[2] + b.num[2] || b.num[0] == 0 || b.num[1] == 0) continue;
+            eb.push_back(QBlock{c, vz});
+        }
+        for (int c = 0; c < (int)L.c2.size(); ++c) {
+            const auto& b = L.c2[c].box;
+            if (!L.c2[c].active || vz < b.lo[2] || vz >= b.lo[2] + b.num[2] || b.num[0] == 0 || b.num[1] == 0) continue;
+            bb.push_back(QBlock{c, vz});
+        }
+    }
+    ctx->neblocks = (int)eb.size();
+    ctx->nbblocks = (int)bb.size();
+    if ((rc = upload(ctx, &ctx->eblocks, eb)) || (rc = upload(ctx, &ctx->bblocks, bb))) return rc;
     std::vector<QTile> tA = make_tiles(false), tE = make_tiles(true);
     ctx->ntilesA = (int)tA.size();
     ctx->ntilesE = (int)tE.size();
@@ -754,35 +989,67 @@ static int setup_device(ygm_ctx* ctx) {
             if ((rc = fill((float*)nullptr))) return rc;
         }
         if ((rc = upload(ctx, &ctx->pbeg, pbeg))) return rc;
+        for (size_t c = 0; c < L.c1.size(); ++c) ctx->max_terms = std::max(ctx->max_terms, pbeg[c + 1] - pbeg[c]);
     }
     for (int i = 0; i < 2; ++i) CK(cudaEventCreateWithFlags(&ctx->damp_ev[i], cudaEventDisableTiming));
+    // dynamic shared memory of the block kernels (slot / term tables of one class); above 48 KB
+    // the kernels must opt in, up to the 227 KB per-CTA limit of sm_103a
+    const size_t smem_q = (size_t)ctx->max_slots * (2 * sizeof(long long) + 8 * sizeof(int));
+    const size_t smem_e = (size_t)ctx->max_terms * sizeof(long long) + (size_t)(ctx->max_terms + 1) * ctx->rs +
+                          (size_t)ctx->max_terms * 6 * sizeof(int);
+    if (smem_q > 227 * 1024 || smem_e > 227 * 1024) return fail(ctx, YGM_EINVAL, "stencil too wide for shared memory");
+    // raise-only: the limit is process-wide per kernel, shared by every context (a smaller value
+    // set by one context would make another context's launches invalid)
+    {
+        std::lock_guard<std::mutex> lk(g_smem_mutex);
+        if (smem_q > g_smem_q[ctx->precision]) {
+            if (smem_q > 48 * 1024) {
+                if (ctx->precision == YGM_FP64)
+                    CK(cudaFuncSetAttribute(k_qapply_b<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_q));
+                else
+                    CK(cudaFuncSetAttribute(k_qapply_b<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_q));
+            }
+            g_smem_q[ctx->precision] = smem_q;
+        }
+        if (smem_e > g_smem_e[ctx->precision]) {
+            if (smem_e > 48 * 1024) {
+                if (ctx->precision == YGM_FP64)
+                    CK(cudaFuncSetAttribute(k_curlT_e_b<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_e));
+                else
+                    CK(cudaFuncSetAttribute(k_curlT_e_b<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_e));
+            }
+            g_smem_e[ctx->precision] = smem_e;
+        }
+    }
     CK(cudaStreamSynchronize(ctx->stream));
     return 0;
 }
 
 // ------------------------------------------------------------------ launch helpers
 static int launch_qapply(ygm_ctx* ctx, const void* e, void* x) {
-    dim3 g((ctx->ntilesA + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+    if (!ctx->nqblocks) return 0;
     time_begin(ctx, KQ);
+    const size_t smem = (size_t)ctx->max_slots * (2 * sizeof(long long) + 8 * sizeof(int));
     if (ctx->precision == YGM_FP64)
-        k_qapply_t<double><<<g, BLOCK, 0, ctx->stream>>>(ctx->c1, ctx->qslots, ctx->tilesA, ctx->ntilesA,
-                                                         (const double*)ctx->q, (const double*)e, (double*)x);
+        k_qapply_b<double><<<ctx->nqblocks, ctx->qthreads, smem, ctx->stream>>>(ctx->c1, ctx->qslots, ctx->qblocks, ctx->max_slots,
+                                                                        (const double*)ctx->q, (const double*)e, (double*)x);
     else
-        k_qapply_t<float><<<g, BLOCK, 0, ctx->stream>>>(ctx->c1, ctx->qslots, ctx->tilesA, ctx->ntilesA,
-                                                        (const float*)ctx->q, (const float*)e, (float*)x);
+        k_qapply_b<float><<<ctx->nqblocks, ctx->qthreads, smem, ctx->stream>>>(ctx->c1, ctx->qslots, ctx->qblocks, ctx->max_slots,
+                                                                       (const float*)ctx->q, (const float*)e, (float*)x);
     time_end(ctx);
     ctx->launches++;
     return 0;
 }
 static int launch_curl_b(ygm_ctx* ctx, const void* x, const void* bin, void* bout, double ctau) {
-    dim3 g((ctx->nrowsB + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+    if (!ctx->nbblocks) return 0;
     time_begin(ctx, KB);
     if (ctx->precision == YGM_FP64)
-        k_curl_b<double><<<g, BLOCK, 0, ctx->stream>>>(ctx->tb, ctx->rowsB, ctx->nrowsB, (const double*)x,
-                                                       (const double*)bin, (double*)bout, ctau);
+        k_curl_b_b<double><<<ctx->nbblocks, BLOCK, 0, ctx->stream>>>(ctx->c1, ctx->c2, ctx->terms, ctx->bblocks,
+                                                                     (const double*)x, (const double*)bin, (double*)bout, ctau);
     else
-        k_curl_b<float><<<g, BLOCK, 0, ctx->stream>>>(ctx->tb, ctx->rowsB, ctx->nrowsB, (const float*)x,
-                                                      (const float*)bin, (float*)bout, (float)ctau);
+        k_curl_b_b<float><<<ctx->nbblocks, BLOCK, 0, ctx->stream>>>(ctx->c1, ctx->c2, ctx->terms, ctx->bblocks,
+                                                                    (const float*)x, (const float*)bin, (float*)bout,
+                                                                    (float)ctau);
     time_end(ctx);
     ctx->launches++;
     return 0;
@@ -790,14 +1057,17 @@ static int launch_curl_b(ygm_ctx* ctx, const void* x, const void* bin, void* bou
 static int launch_curlT_e(ygm_ctx* ctx, const void* b, void* e, double ctau) {
     time_begin(ctx, KE);
     if (ctx->pterms) {
-        dim3 g((ctx->ntilesE + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
-        if (ctx->precision == YGM_FP64)
-            k_curlT_e_t<double><<<g, BLOCK, 0, ctx->stream>>>(ctx->c1, ctx->pbeg, (const PTerm<double>*)ctx->pterms,
-                                                              ctx->tilesE, ctx->ntilesE, (const double*)b, (double*)e, ctau);
-        else
-            k_curlT_e_t<float><<<g, BLOCK, 0, ctx->stream>>>(ctx->c1, ctx->pbeg, (const PTerm<float>*)ctx->pterms,
-                                                             ctx->tilesE, ctx->ntilesE, (const float*)b, (float*)e,
-                                                             (float)ctau);
+        const int mt = ctx->max_terms;
+        const size_t smem = (size_t)mt * sizeof(long long) + (size_t)(mt + (mt & 1)) * ctx->rs + (size_t)mt * 6 * sizeof(int);
+        if (ctx->neblocks) {
+            if (ctx->precision == YGM_FP64)
+                k_curlT_e_b<double><<<ctx->neblocks, BLOCK, smem, ctx->stream>>>(
+                    ctx->c1, ctx->pbeg, (const PTerm<double>*)ctx->pterms, ctx->eblocks, mt, (const double*)b, (double*)e, ctau);
+            else
+                k_curlT_e_b<float><<<ctx->neblocks, BLOCK, smem, ctx->stream>>>(
+                    ctx->c1, ctx->pbeg, (const PTerm<float>*)ctx->pterms, ctx->eblocks, mt, (const float*)b, (float*)e,
+                    (float)ctau);
+        }
     } else {
         dim3 g((ctx->nrowsE + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
         if (ctx->precision == YGM_FP64)
@@ -1250,7 +1520,7 @@ void ygm_destroy(ygm_ctx* ctx) {
         if (ctx->damp[i]) cudaFree(ctx->damp[i]);
         if (ctx->hamp[i]) cudaFreeHost(ctx->hamp[i]);
     }
-    void* more[] = {ctx->qslots, ctx->tilesA, ctx->tilesE, ctx->pterms, ctx->pbeg};
+    void* more[] = {ctx->qslots, ctx->qblocks, ctx->eblocks, ctx->bblocks, ctx->tilesA, ctx->tilesE, ctx->pterms, ctx->pbeg};
     for (void* p : more)
         if (p) cudaFree(p);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
