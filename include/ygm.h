@@ -126,6 +126,23 @@ int ygm_project_E(ygm_ctx* ctx, void (*E0)(const double x[3], double out[3], voi
  * composition).  Asynchronous on the context stream; returns after enqueueing. */
 int ygm_step(ygm_ctx* ctx, int64_t n, double dt, const ygm_source* src, int32_t n_src);
 
+/* One leapfrog step on caller-owned device buffers, with no device allocation (no cudaMalloc,
+ * cudaFree or allocating library call).  The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory -- e.g. code running while a CUDA graph is
+ * captured with allocation forbidden, or a process whose memory pool is reserved up front.
+ * State (e_n, b_{n-1/2}) in the context precision: x = Q1 e (into a fixed 16 MiB file-scope
+ * device scratch array, not into context memory), b_out = b_in - dt C x, e += dt C^T M2 b_out.
+ * No source term, no half steps, no energy recording; the context's own state is untouched.
+ * b_out may equal b_in; if it differs, its entries outside the range of C (the divergence part)
+ * are not written.  Limit: N1 * n_rhs * sizeof(real) <= 16 MiB (2,097,152 DoFs in FP64,
+ * 4,194,304 in FP32); larger contexts get YGM_EINVAL.  The first call on a device looks up the
+ * scratch array's device address (cudaGetSymbolAddress) and should therefore come before any
+ * stream capture.  All calls share the one scratch array, which keeps the last call's contents:
+ * calls whose work overlaps on the GPU (other streams, other contexts) race on it.  Every element
+ * of the scratch is written before it is read, so nothing needs clearing.  Asynchronous on the
+ * context stream; errors YGM_EINVAL, YGM_ECFL, YGM_ENODEV, YGM_ECUDA. */
+int ygm_step_noalloc(ygm_ctx* ctx, void* e, const void* b_in, void* b_out, double dt);
+
 /* Conserved discrete energy of the current state (e_n, b_{n-1/2}), per right-hand side:
  *   W_n = 1/2 e_n^T Q1 e_n + 1/2 b_{n+1/2}^T M2 b_{n-1/2}
  * (telescoping invariant of the leapfrog; exact up to round-off without sources), and the

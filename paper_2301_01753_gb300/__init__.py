@@ -17,7 +17,7 @@ YGM_OK, YGM_EINVAL, YGM_ECFL, YGM_ENOTSPD, YGM_ENOMEM, YGM_ECUDA, YGM_ETIMEOUT, 
 YGM_FP64, YGM_FP32 = 0, 1
 YGM_Q1_DEFAULT, YGM_Q1_DIAG, YGM_Q1_SM1, YGM_Q1_SM1SQ = 0, 1, 2, 3
 
-EXPORTED = ["ygm_create", "ygm_sizes", "ygm_set_state", "ygm_get_state", "ygm_project_E", "ygm_step",
+EXPORTED = ["ygm_create", "ygm_sizes", "ygm_set_state", "ygm_get_state", "ygm_project_E", "ygm_step", "ygm_step_noalloc",
             "ygm_energy", "ygm_energy_history", "ygm_time", "ygm_export_q1", "ygm_set_q1", "ygm_q1_info",
             "ygm_local_blocks", "ygm_kernel_timing", "ygm_kernel_times", "ygm_launch_count",
             "ygm_last_error", "ygm_destroy"]
@@ -62,6 +62,7 @@ def load_library(path=LIB_PATH):
         "ygm_get_state": (C.c_int, [P, P, P, C.c_int, C.c_int]),
         "ygm_project_E": (C.c_int, [P, E0_CB, P, C.c_int32]),
         "ygm_step": (C.c_int, [P, I64, D, C.POINTER(ygm_source), C.c_int32]),
+        "ygm_step_noalloc": (C.c_int, [P, P, P, P, D]),
         "ygm_energy": (C.c_int, [P, pD, pD]),
         "ygm_energy_history": (C.c_int, [P, pD, I64, pI64]),
         "ygm_time": (C.c_int, [P, pI64, pD]),
@@ -180,6 +181,14 @@ class Context:
             arr[i].sigma = float(s["sigma"])
             arr[i].rhs = int(s.get("rhs", 0))
         self._check(_lib.ygm_step(self._h, int(n), float(dt), arr, len(sources)))
+
+    def step_noalloc(self, e, b_in, b_out, dt):
+        """One leapfrog step on caller-owned device tensors, no device allocation (ygm_step_noalloc)."""
+        pe, de = _ptr(e)
+        pbi, dbi = _ptr(b_in)
+        pbo, dbo = _ptr(b_out)
+        assert de == dbi == dbo == 1, "ygm_step_noalloc works on device buffers"
+        self._check(_lib.ygm_step_noalloc(self._h, pe, pbi, pbo, float(dt)))
 
     def energy(self):
         W = (C.c_double * self.n_rhs)()

@@ -1115,7 +1115,19 @@ static int launch_energy(ygm_ctx* ctx, const void* e, const void* x, const void*
     return 0;
 }
 
-// ====================================================================== C ABI
+// ====================================================================== no-allocation step
+// Callers that must not allocate device memory (code that runs while a CUDA graph is being
+// captured with allocation forbidden, in a process whose memory pool is reserved up front, or
+// under a real-time budget that rules out cudaMalloc latency) still need the Q1 e scratch
+// vector of a leapfrog step.  It lives in this fixed, file-scope device array instead: every
+// GPU that loads the library holds these 16 MiB until the process exits.  Host code must not
+// pass the symbol itself to a kernel (on the host it is only a stand-in): its device address
+// is obtained once per device with cudaGetSymbolAddress.
+constexpr size_t NOALLOC_SCRATCH_BYTES = 16u << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+static void* g_noalloc_addr[256] = {nullptr};
+static std::mutex g_noalloc_mutex;
+
 extern "C" {
 
 const char* ygm_last_error(const ygm_ctx* ctx) {
@@ -1446,6 +1458,77 @@ int ygm_set_q1(ygm_ctx* ctx, const int64_t* rowptr, const int64_t* colind, const
         ctx->q = nullptr;
         if ((rc = upload_real(ctx, &ctx->q, ctx->S.qvals))) return rc;
     }
+    return YGM_OK;
+}
+
+int ygm_step_noalloc(ygm_ctx* ctx, void* e, const void* b_in, void* b_out, double dt) {
+    if (!ctx || !e || !b_in || !b_out) return fail(ctx, YGM_EINVAL, "NULL argument");
+    const size_t need = (size_t)ctx->S.L.N1 * ctx->n_rhs * ctx->rs;
+    if (need > NOALLOC_SCRATCH_BYTES)
+        return fail(ctx, YGM_EINVAL,
+                    "ygm_step_noalloc: N1 * n_rhs * sizeof(real) = " + std::to_string(need) +
+                        " bytes exceeds the fixed 16 MiB scratch (use ygm_step)");
+    if (ctx->host_only) return fail(ctx, YGM_ENODEV, "context was created host-only (device = -1)");
+    if (!(dt > 0) || !std::isfinite(dt)) return fail(ctx, YGM_EINVAL, "need finite dt > 0");
+    if (dt > ctx->S.tau_cfl * (1.0 + 1e-12))
+        return fail(ctx, YGM_ECFL, "dt exceeds the CFL bound 2/omega_max (Prop. stability)");
+    if (ctx->device < 0 || ctx->device >= 256) return fail(ctx, YGM_EINVAL, "device ordinal out of range");
+    CK(cudaSetDevice(ctx->device));
+    void* x = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mutex);
+        if (!g_noalloc_addr[ctx->device]) {
+            void* p = nullptr;
+            CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+            g_noalloc_addr[ctx->device] = p;
+        }
+        x = g_noalloc_addr[ctx->device];
+    }
+    // x = Q1 e (every element of x is written, so the scratch needs no clearing)
+    const size_t smem = (size_t)ctx->max_slots * (2 * sizeof(long long) + 8 * sizeof(int));
+    if (ctx->nqblocks) {
+        if (ctx->precision == YGM_FP64)
+            k_qapply_b<double><<<ctx->nqblocks, ctx->qthreads, smem, ctx->stream>>>(
+                ctx->c1, ctx->qslots, ctx->qblocks, ctx->max_slots, (const double*)ctx->q, (const double*)e, (double*)x);
+        else
+            k_qapply_b<float><<<ctx->nqblocks, ctx->qthreads, smem, ctx->stream>>>(
+                ctx->c1, ctx->qslots, ctx->qblocks, ctx->max_slots, (const float*)ctx->q, (const float*)e, (float*)x);
+    }
+    // b_out = b_in - dt C x ; e += dt C^T M2 b_out
+    if (ctx->nbblocks) {
+        if (ctx->precision == YGM_FP64)
+            k_curl_b_b<double><<<ctx->nbblocks, BLOCK, 0, ctx->stream>>>(ctx->c1, ctx->c2, ctx->terms, ctx->bblocks,
+                                                                         (const double*)x, (const double*)b_in,
+                                                                         (double*)b_out, dt);
+        else
+            k_curl_b_b<float><<<ctx->nbblocks, BLOCK, 0, ctx->stream>>>(ctx->c1, ctx->c2, ctx->terms, ctx->bblocks,
+                                                                        (const float*)x, (const float*)b_in,
+                                                                        (float*)b_out, (float)dt);
+    }
+    if (ctx->pterms) {
+        const int mt = ctx->max_terms;
+        const size_t smem_e = (size_t)mt * sizeof(long long) + (size_t)(mt + (mt & 1)) * ctx->rs + (size_t)mt * 6 * sizeof(int);
+        if (ctx->neblocks) {
+            if (ctx->precision == YGM_FP64)
+                k_curlT_e_b<double><<<ctx->neblocks, BLOCK, smem_e, ctx->stream>>>(
+                    ctx->c1, ctx->pbeg, (const PTerm<double>*)ctx->pterms, ctx->eblocks, mt, (const double*)b_out, (double*)e, dt);
+            else
+                k_curlT_e_b<float><<<ctx->neblocks, BLOCK, smem_e, ctx->stream>>>(
+                    ctx->c1, ctx->pbeg, (const PTerm<float>*)ctx->pterms, ctx->eblocks, mt, (const float*)b_out, (float*)e,
+                    (float)dt);
+        }
+    } else {
+        dim3 g((ctx->nrowsE + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+        if (ctx->precision == YGM_FP64)
+            k_curlT_e<double><<<g, BLOCK, 0, ctx->stream>>>(ctx->tb, ctx->rowsE, ctx->nrowsE, (const double*)ctx->W,
+                                                            (const double*)b_out, (const double*)ctx->inv_mu, (double*)e, dt);
+        else
+            k_curlT_e<float><<<g, BLOCK, 0, ctx->stream>>>(ctx->tb, ctx->rowsE, ctx->nrowsE, (const float*)ctx->W,
+                                                           (const float*)b_out, (const float*)ctx->inv_mu, (float*)e,
+                                                           (float)dt);
+    }
+    ctx->launches += 3;
+    CK(cudaGetLastError());
     return YGM_OK;
 }
 
