@@ -7,7 +7,11 @@ k = 2, per-tet permittivity i.i.d. U[1,4) (seed 2000), mu = 1, one Gaussian-modu
 2000 leapfrog steps per run, FP32 fields.  One benchmark step is one whole 2000-step run from the
 zero state; value = (N1 + N2) * 2000 / run time, summed over ranks (independent replicas).
 
-Run:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Batched mode (--rhs R, R a power of two): R independent excitations as R right-hand-side columns
+of one context, one Gaussian-pulse dipole per column at U[0.2,0.8)^3 points (seed 3001) with
+normalised-Gaussian orientations (seed 3002); value = (N1 + N2) * R * steps / run time.
+
+Run:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--rhs R]
 """
 import argparse
 import json
@@ -28,15 +32,23 @@ METRIC = "field DoF-updates/s on 1 GB300 (FP32/batched vs FP64) at stated L2 err
 UNIT = "DoF-updates/s"
 
 
-def workload(n=32, k=2, leapfrog_steps=2000):
-    x0 = synth.source_positions(2001, 1)[0]
-    return dict(n=n, k=k, eps=synth.tet_eps(2000, n, 1.0, 4.0), x0=x0, d=np.array([0.0, 0.0, 1.0]),
+def workload(n=32, k=2, leapfrog_steps=2000, rhs=1):
+    if rhs == 1:
+        x0 = synth.source_positions(2001, 1)
+        d = np.array([[0.0, 0.0, 1.0]])
+    else:
+        x0 = synth.source_positions(3001, rhs)
+        d = synth.unit_vectors(3002, rhs)
+    return dict(n=n, k=k, eps=synth.tet_eps(2000, n, 1.0, 4.0), x0=x0[0], xs=x0, d=d[0], ds=d, rhs=rhs,
                 omega=np.pi * np.sqrt(5.0), width=20.0, steps=leapfrog_steps)
 
 
-def source_for(W, dt):
+def source_for(W, dt, column=None):
+    """The workload's dipoles (one per column); column = r gives column r's dipole alone, on column 0."""
     sigma = W["width"] * dt
-    return [dict(x=W["x0"], d=W["d"], amp=1.0, omega=W["omega"], t0=4 * sigma, sigma=sigma, rhs=0)]
+    cols = range(W["rhs"]) if column is None else [column]
+    return [dict(x=W["xs"][r], d=W["ds"][r], amp=1.0, omega=W["omega"], t0=4 * sigma, sigma=sigma,
+                 rhs=r if column is None else 0) for r in cols]
 
 
 # ------------------------------------------------------------------ clocks
@@ -174,20 +186,21 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    W = workload(n=args.n, k=args.order, leapfrog_steps=args.leapfrog_steps)
+    W = workload(n=args.n, k=args.order, leapfrog_steps=args.leapfrog_steps, rhs=args.rhs)
+    R = args.rhs
     stream = torch.cuda.current_stream()
     prec = Y.YGM_FP32 if args.precision == "fp32" else Y.YGM_FP64
     tb = time.perf_counter()
     # the timed context also records the conserved energy every 100 steps (row A-5)
     ctx = Y.Context(W["n"], W["k"], eps=W["eps"], precision=prec, device=local_rank, stream=stream.cuda_stream,
-                    energy_every=args.energy_every)
+                    energy_every=args.energy_every, n_rhs=R)
     setup_s = time.perf_counter() - tb
     dt = 0.5 * ctx.tau_cfl
     src = source_for(W, dt)
     tdt = torch.float32 if prec == Y.YGM_FP32 else torch.float64
-    ze = torch.zeros(ctx.N1, dtype=tdt, device="cuda")
-    zb = torch.zeros(ctx.N2, dtype=tdt, device="cuda")
-    units = (ctx.N1 + ctx.N2) * W["steps"]
+    ze = torch.zeros(ctx.N1 * R, dtype=tdt, device="cuda")
+    zb = torch.zeros(ctx.N2 * R, dtype=tdt, device="cuda")
+    units = (ctx.N1 + ctx.N2) * R * W["steps"]
 
     def one_run():
         ctx.set_state(ze, zb)
@@ -219,10 +232,10 @@ def run_ours(args, rank, world, local_rank):
     value, t_job = aggregate(units * args.steps, ms_total * 1e-3, dist, device="cuda")
 
     # end to end through the public API with host buffers (pinned): H2D state in, D2H state out
-    he = torch.zeros(ctx.N1, dtype=tdt).pin_memory().numpy()
-    hb = torch.zeros(ctx.N2, dtype=tdt).pin_memory().numpy()
-    oe = torch.empty(ctx.N1, dtype=tdt).pin_memory().numpy()
-    ob = torch.empty(ctx.N2, dtype=tdt).pin_memory().numpy()
+    he = torch.zeros(ctx.N1 * R, dtype=tdt).pin_memory().numpy()
+    hb = torch.zeros(ctx.N2 * R, dtype=tdt).pin_memory().numpy()
+    oe = torch.empty(ctx.N1 * R, dtype=tdt).pin_memory().numpy()
+    ob = torch.empty(ctx.N2 * R, dtype=tdt).pin_memory().numpy()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
@@ -233,40 +246,58 @@ def run_ours(args, rank, world, local_rank):
     e2e_val, _ = aggregate(units, e2e_s, dist, device="cuda")
     rs = 4 if prec == Y.YGM_FP32 else 8
 
-    # roofline of the dominant kernel (Q1 apply): algorithmic bytes = unique symmetric Q1 values
-    # + e read + x write
+    # roofline of the dominant kernel (Q1 apply).  Algorithmic bytes of one launch = the distinct
+    # Q1 values its rows use (a symmetric pair once) + e read + x written.  Steps with an energy
+    # read-out compute every row; the others only the curl-carrying rows (C x reads nothing else).
     qms, qn = kt["k_qapply"]
-    q_unique = (ctx.q1_nnz + ctx.N1) // 2
-    alg_bytes = rs * (q_unique + 2 * ctx.N1)
+    n_all = kt["k_energy"][1]                  # one all-rows Q1 apply per energy read-out
+    n_act = qn - n_all
+    ra, ua, sa = ctx.qapply_counts(False)
+    rf, uf, sf = ctx.qapply_counts(True)
+    alg_total = rs * (n_act * (ua + R * (ctx.N1 + ra)) + n_all * (uf + R * (ctx.N1 + rf)))
+    streamed_total = rs * (n_act * (sa + R * (ctx.N1 + ra)) + n_all * (sf + R * (ctx.N1 + rf)))
+    alg_bytes = alg_total / max(qn, 1)
     q_avg_s = (qms / max(qn, 1)) * 1e-3
     peak, peak_kind = peaks()
     achieved = alg_bytes / q_avg_s / 1e9
+    streamed_gbs = streamed_total / max(qn, 1) / q_avg_s / 1e9
+    q_unique = uf
     step_kernels = {k: dict(ms_per_launch=(v[0] / v[1] if v[1] else None), launches=v[1]) for k, v in kt.items()}
 
     # accuracy at the stated configuration: FP32 vs the FP64 GPU path (same operators, one run),
     # and the discrete energy drift after the pulse has passed
     acc = None
     if rank == 0 and not args.no_accuracy:
+        # FP64 single-column reference run(s): column 0 (and the last column when batched)
         ref = Y.Context(W["n"], W["k"], eps=W["eps"], precision=Y.YGM_FP64, device=local_rank,
                         energy_every=100, stream=stream.cuda_stream)
-        ref.set_state(np.zeros(ref.N1), np.zeros(ref.N2))
-        torch.cuda.synchronize()
-        t64 = time.perf_counter()
-        ref.step(W["steps"], dt, src)
-        e64, b64 = ref.get_state(synced=True)
-        t64 = time.perf_counter() - t64
-        Wh = ref.energy_history()
         ctx.set_state(ze, zb)
         ctx.step(W["steps"], dt, src)
-        W32 = ctx.energy_history()
+        W32 = ctx.energy_history().reshape(-1, R)
         e32, b32 = ctx.get_state(synced=True)
-        drift32 = float(np.max(np.abs(W32[3:] - W32[3])) / W32[3]) if len(W32) > 4 else None
-        acc = dict(rel_l2_e_vs_fp64_gpu=float(np.linalg.norm(e32 - e64) / np.linalg.norm(e64)),
-                   rel_l2_b_vs_fp64_gpu=float(np.linalg.norm(b32 - b64) / np.linalg.norm(b64)),
-                   energy_drift_fp64_after_pulse=float(np.max(np.abs(Wh[3:] - Wh[3])) / Wh[3]),
-                   energy_every=100, note="drift = max |W_n - W_300| / W_300 over n >= 300 (pulse over)",
-                   energy_drift_fp32_after_pulse=drift32,
-                   fp64_gpu_value=units / t64, fp64_gpu_ms_per_run=t64 * 1e3)
+        e32, b32 = e32.reshape(ctx.N1, R), b32.reshape(ctx.N2, R)
+        cols = [0] if R == 1 else [0, R - 1]
+        errs_e, errs_b, drift64, drift32, t64 = [], [], [], [], None
+        for r in cols:
+            ref.set_state(np.zeros(ref.N1), np.zeros(ref.N2))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ref.step(W["steps"], dt, source_for(W, dt, column=r))
+            e64, b64 = ref.get_state(synced=True)
+            if t64 is None:
+                t64 = time.perf_counter() - t0
+            Wh = ref.energy_history()
+            errs_e.append(float(np.linalg.norm(e32[:, r] - e64) / np.linalg.norm(e64)))
+            errs_b.append(float(np.linalg.norm(b32[:, r] - b64) / np.linalg.norm(b64)))
+            drift64.append(float(np.max(np.abs(Wh[3:] - Wh[3])) / Wh[3]))
+            w = W32[:, r]
+            drift32.append(float(np.max(np.abs(w[3:] - w[3])) / w[3]) if len(w) > 4 else None)
+        acc = dict(columns_checked=cols, rel_l2_e_vs_fp64_gpu=max(errs_e), rel_l2_b_vs_fp64_gpu=max(errs_b),
+                   energy_drift_fp64_after_pulse=max(drift64), energy_every=100,
+                   note="drift = max |W_n - W_300| / W_300 over n >= 300 (pulse over); FP64 reference = "
+                        "single-column FP64 GPU run of the same column's source",
+                   energy_drift_fp32_after_pulse=max(d for d in drift32 if d is not None) if drift32 else None,
+                   fp64_gpu_value=(ref.N1 + ref.N2) * W["steps"] / t64, fp64_gpu_ms_per_run=t64 * 1e3)
         ref.close()
 
     cpu = None
@@ -279,18 +310,27 @@ def run_ours(args, rank, world, local_rank):
         line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                     ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None,
                     dtype="f32" if prec == Y.YGM_FP32 else "f64", data="synthetic",
-                    config=dict(workload=f"PEC cube N={W['n']} (6N^3={6 * W['n'] ** 3} Kuhn tets), k={W['k']}, "
-                                         f"eps~U[1,4) seed 2000, z-dipole seed 2001, dt=0.5 tau_CFL, "
-                                         f"{W['steps']} leapfrog steps per step",
+                    config=dict(workload=(f"PEC cube N={W['n']} (6N^3={6 * W['n'] ** 3} Kuhn tets), k={W['k']}, "
+                                          f"eps~U[1,4) seed 2000, z-dipole seed 2001, dt=0.5 tau_CFL, "
+                                          f"{W['steps']} leapfrog steps per step") if R == 1 else
+                                         (f"batched: PEC cube N={W['n']} (6N^3={6 * W['n'] ** 3} Kuhn tets), "
+                                          f"k={W['k']}, eps~U[1,4) seed 2000, {R} RHS columns, one dipole each "
+                                          f"(positions seed 3001, orientations seed 3002), dt=0.5 tau_CFL, "
+                                          f"{W['steps']} leapfrog steps per step"),
+                                n_rhs=R,
                                 N1=ctx.N1, N2=ctx.N2, dofs=ctx.N1 + ctx.N2, leapfrog_steps=W["steps"],
                                 q1_nnz=ctx.q1_nnz, q1=ctx.q1_info(), dt=dt, setup_s=setup_s,
                                 parallelism=f"replicas{world}" if world > 1 else "single",
                                 l2_policy="inputs larger than L2 (Q1 %.0f MB > 129 MB L2)" % (rs * q_unique / 1e6)),
-                    e2e=dict(value=e2e_val, unit=UNIT, h2d_bytes_per_step=rs * (ctx.N1 + ctx.N2),
-                             d2h_bytes_per_step=rs * (ctx.N1 + ctx.N2)),
+                    e2e=dict(value=e2e_val, unit=UNIT, h2d_bytes_per_step=rs * (ctx.N1 + ctx.N2) * R,
+                             d2h_bytes_per_step=rs * (ctx.N1 + ctx.N2) * R),
                     gpu_launches=launches,
                     roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
-                                  traffic=None, kernel="k_qapply", bytes_per_launch=alg_bytes,
+                                  traffic=None, kernel="k_qapply_p", bytes_per_launch=alg_bytes,
+                                  launches=dict(curl_rows_only=n_act, all_rows=n_all),
+                                  streamed_gbs=streamed_gbs,
+                                  note="bytes: distinct Q1 values (symmetric pair once) + e + x; streamed_gbs "
+                                       "counts the full-row Q1 entries the kernel actually reads",
                                   peak_source=f"{peak_kind} hbm_gbs"),
                     kernels=step_kernels, clocks=clk.summary(), accuracy=acc, cpu_baseline=cpu)
         print(json.dumps(line), flush=True)
@@ -311,6 +351,7 @@ def main():
     ap.add_argument("--leapfrog-steps", type=int, default=2000)
     ap.add_argument("--cpu-steps", type=int, default=2000)
     ap.add_argument("--energy-every", type=int, default=100)
+    ap.add_argument("--rhs", type=int, default=1, help="right-hand-side columns (batched excitations)")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

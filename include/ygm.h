@@ -191,6 +191,17 @@ int ygm_kernel_times(ygm_ctx* ctx, double* ms, int64_t* count);
 /* Launch statistics: kernels launched by this context so far (all kernels of the library). */
 int ygm_launch_count(const ygm_ctx* ctx, int64_t* count);
 
+/* Sizes of one Q1 apply x = Q1 e, for roofline accounting (no compute, no device access).
+ * all_rows = 1 describes the launch that computes every row (steps with an energy read-out and
+ * ygm_energy); all_rows = 0 the launch of every other step, which computes only the rows of the
+ * curl-carrying 1-forms: C has zero columns at the gradient 1-forms (Sec. 2, C G = 0), so C x
+ * never reads the other rows.  rows: rows computed; unique_values: distinct Q1 values those rows
+ * use, a symmetric pair counted once; stored_values: Q1 entries the kernel streams (full rows,
+ * zeros at neighbours outside the mesh, plane padding).  NULL outputs are skipped.
+ * Returns YGM_EINVAL for a NULL context, YGM_ENODEV for a host-only one. */
+int ygm_qapply_counts(const ygm_ctx* ctx, int all_rows, int64_t* rows, int64_t* unique_values,
+                      int64_t* stored_values);
+
 /* Message of the last failure on this context (or of the last failed ygm_create when ctx is
  * NULL).  Valid until the next call on the same context. */
 const char* ygm_last_error(const ygm_ctx* ctx);

@@ -20,7 +20,7 @@ YGM_Q1_DEFAULT, YGM_Q1_DIAG, YGM_Q1_SM1, YGM_Q1_SM1SQ = 0, 1, 2, 3
 EXPORTED = ["ygm_create", "ygm_sizes", "ygm_set_state", "ygm_get_state", "ygm_project_E", "ygm_step", "ygm_step_noalloc",
             "ygm_energy", "ygm_energy_history", "ygm_time", "ygm_export_q1", "ygm_set_q1", "ygm_q1_info",
             "ygm_local_blocks", "ygm_kernel_timing", "ygm_kernel_times", "ygm_launch_count",
-            "ygm_last_error", "ygm_destroy"]
+            "ygm_qapply_counts", "ygm_last_error", "ygm_destroy"]
 KERNEL_KINDS = ["k_qapply", "k_curl_b", "k_curlT_e", "k_source", "k_energy"]
 
 
@@ -73,6 +73,7 @@ def load_library(path=LIB_PATH):
         "ygm_kernel_timing": (C.c_int, [P, C.c_int]),
         "ygm_kernel_times": (C.c_int, [P, pD, pI64]),
         "ygm_launch_count": (C.c_int, [P, pI64]),
+        "ygm_qapply_counts": (C.c_int, [P, C.c_int, pI64, pI64, pI64]),
         "ygm_last_error": (C.c_char_p, [P]),
         "ygm_destroy": (None, [P]),
     }
@@ -263,6 +264,12 @@ class Context:
         c = C.c_int64()
         self._check(_lib.ygm_launch_count(self._h, C.byref(c)))
         return c.value
+
+    def qapply_counts(self, all_rows):
+        """(rows, unique Q1 values, streamed Q1 entries) of one Q1 apply launch (roofline accounting)."""
+        r, u, st = C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(_lib.ygm_qapply_counts(self._h, 1 if all_rows else 0, C.byref(r), C.byref(u), C.byref(st)))
+        return r.value, u.value, st.value
 
 
 def pulse_source(x, d, omega, dt, width_steps=20.0, amp=1.0, t0_sigmas=4.0, rhs=0):

@@ -1252,6 +1252,7 @@ int build_setup(Setup& S, int n, double side, int k, const double* eps, const do
         S.tau_cfl = 2.0 / std::sqrt(S.omega_max_sq);
         stage("CFL (Lanczos)");
         B.stencils(pat);
+        pack_full(S, threads);
         stage("stencils + packing");
     } catch (const std::exception& ex) {
         S.err = ex.what();
@@ -1289,6 +1290,39 @@ int refresh_spectrum(Setup& S, int threads_in) {
         return -3;
     }
     return 0;
+}
+
+// ============================================================== full row storage of Q1
+void pack_full(Setup& S, int threads_in) {
+    const int threads = default_threads(threads_in);
+    const Lattice& L = S.L;
+    const size_t nc = L.c1.size();
+    S.qf_off.assign(nc + 1, 0);
+    S.qf_plane.assign(nc, 0);
+    for (size_t c = 0; c < nc; ++c) {
+        const Box& b = L.c1[c].box;
+        const int64_t plane = ((int64_t)b.num[0] * b.num[1] + 3) / 4 * 4;
+        S.qf_plane[c] = plane;
+        S.qf_off[c + 1] = S.qf_off[c] + (int64_t)(S.st_begin[c + 1] - S.st_begin[c]) * plane * b.num[2];
+    }
+    S.qfull.assign(S.qf_off[nc], 0.0);
+    for (size_t c = 0; c < nc; ++c) {
+        const Box& b = L.c1[c].box;
+        const int64_t plane = S.qf_plane[c], ns = S.st_begin[c + 1] - S.st_begin[c];
+        parallel_for(b.size, threads, [&](int64_t lo, int64_t hi, int) {
+            for (int64_t r = lo; r < hi; ++r) {
+                const int rx = (int)(r % b.num[0]), ry = (int)((r / b.num[0]) % b.num[1]);
+                const int rz = (int)(r / ((int64_t)b.num[0] * b.num[1]));
+                const int v0 = rx + b.lo[0], v1 = ry + b.lo[1], v2 = rz + b.lo[2];
+                for (int64_t s = 0; s < ns; ++s) {
+                    const auto& st = S.st_slots[S.st_begin[c] + s];
+                    const int64_t gj = L.index1(st.cls, v0 + st.d[0], v1 + st.d[1], v2 + st.d[2]);
+                    S.qfull[S.qf_off[c] + (s * b.num[2] + rz) * plane + (int64_t)ry * b.num[0] + rx] =
+                        gj >= 0 ? S.Q1.get(b.offset + r, gj) : 0.0;
+                }
+            }
+        });
+    }
 }
 
 // ============================================================== user-supplied Q1
@@ -1361,6 +1395,7 @@ int install_q1(Setup& S, const int64_t* rowptr, const int64_t* colind, const dou
             }
         });
     }
+    pack_full(S, threads);
     return refresh_spectrum(S, threads);
 }
 

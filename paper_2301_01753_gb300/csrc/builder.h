@@ -116,7 +116,15 @@ struct Setup {
     std::vector<int32_t> n_upper;                // per class
     std::vector<int64_t> qoff;                   // per class: offset of its (slot-major) value block
     std::vector<double> qvals;                   // packed upper values, [class][slot][box index]
+    // full row storage for the streamed Q1 apply: every slot of the class stencil (upper and
+    // lower) for every row, [class][slot][z-plane padded to 4 entries][y][x]
+    std::vector<int64_t> qf_off;                 // per class: first entry
+    std::vector<int64_t> qf_plane;               // per class: padded plane length (multiple of 4)
+    std::vector<double> qfull;
 };
+
+// Fill qfull from Q1 and the stencil tables (called by build_setup and install_q1).
+void pack_full(Setup& S, int threads);
 
 int build_setup(Setup& S, int n, double side, int k, const double* eps, const double* mu,
                 int q1_pattern, int threads);

@@ -38,7 +38,18 @@ struct DCls {            // a DoF class box (1-form or 2-form)
     long long qoff;      // 1-forms: first packed Q1 value of the class
     int st_begin, st_end;    // 1-forms: stencil slots; 2-forms: curl terms
     int inc_begin, inc_end;  // 1-forms: incident tets
+    int pbase;               // 1-forms: first element of the class region in the padded copy of e
+    int pad_;
 };
+// Padded copy of e: every 1-form class owns a cube of NP^3 entries indexed by lattice anchor + H
+// (anchors -H .. n+H), zero outside the class box, so any Q1 neighbour (|d| <= H per axis) of
+// any row is addressed without range checks.
+struct PadGeo {
+    int H, NP;
+};
+__device__ __forceinline__ int pad_index(const DCls& C, PadGeo g, int vx, int vy, int vz) {
+    return C.pbase + ((vz + g.H) * g.NP + (vy + g.H)) * g.NP + vx + g.H;
+}
 struct DSlot {           // Q1 stencil slot
     int cls;
     int slot;
@@ -80,44 +91,75 @@ __device__ __forceinline__ bool in_box(const DCls& D, int u0, int u1, int u2) {
     return u0 >= 0 && u1 >= 0 && u2 >= 0 && u0 < D.num[0] && u1 < D.num[1] && u2 < D.num[2];
 }
 
-// ------------------------------------------------------------------ x = Q1 e
-// Q1 is symmetric; each row stores its upper slots (neighbours at or after itself in
-// (dz, dy, dx, class) order) as slot-major arrays over the class box.  A lower entry of row
-// i is the upper entry of the neighbour row j for (class_i, -d): it is read there.
+// ------------------------------------------------------------------ x = Q1 e, padded e, full rows
+// One thread per row.  Q1 is stored by full rows, slot-major per class and z-plane
+// (qf[class][slot][z][y][x], zero where the neighbour lies outside its box), and e is read from
+// its padded copy, so slot s of every row of a class is the constant offset soff[s] from the
+// row's own padded index: the loop body is two loads and one FMA, with no range checks.
+constexpr int PBLOCK = 256;
+struct PBlk {            // up to PBLOCK consecutive rows of one (class, z-plane)
+    int i0;              // first in-plane row index (y * num0 + x) of the block
+    int cnt;             // rows in the block
+    int num0;            // x extent of the class box
+    int pz0;             // padded index of the plane's first anchor (lo_x, lo_y, vz)
+    int s_begin, ns;     // slot offsets of the class
+    long long q0;        // qf index of the block's first row, slot 0
+    long long sstr;      // qf distance between consecutive slots of a row
+    long long x0;        // x index of the block's first row
+};
+// With R = 2^rshift right-hand sides ([N][R] layout) a row owns R consecutive threads, one per
+// column; soff is then pre-scaled by R and each Q1 value is shared by the row's R threads.
 template <typename real>
-__global__ void __launch_bounds__(BLOCK) k_qapply(Tables tb, const DRow* __restrict__ rows, int nrows,
-                                                  const real* __restrict__ q, const real* __restrict__ e,
-                                                  real* __restrict__ x) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = blockIdx.x * WARPS_PER_BLOCK + warp;
-    if (row >= nrows) return;
-    const DRow R = rows[row];
-    const DCls C = tb.c1[R.cls];
-    for (int x0 = 0; x0 < C.num[0]; x0 += 32) {
-        const int ix = x0 + lane;                 // x index inside the box
-        const bool act = ix < C.num[0];
-        const int vx = C.lo[0] + ix;
-        real acc = real(0);
-        for (int s = C.st_begin; s < C.st_end; ++s) {
-            const DSlot S = tb.slots[s];
-            const DCls D = tb.c1[S.cls];
-            const int uy = R.vy + S.d[1] - D.lo[1], uz = R.vz + S.d[2] - D.lo[2];
-            if (uy < 0 || uz < 0 || uy >= D.num[1] || uz >= D.num[2]) continue;   // warp-uniform
-            const int ux = vx + S.d[0] - D.lo[0];
-            if (!act || ux < 0 || ux >= D.num[0]) continue;
-            const long long nb = ((long long)uz * D.num[1] + uy) * D.num[0] + ux;
-            const real qv = S.upper ? __ldg(q + C.qoff + (long long)S.slot * C.size + R.rbase + ix)
-                                    : __ldg(q + D.qoff + (long long)S.slot * D.size + nb);
-            acc = fma(qv, __ldg(e + D.off + nb), acc);
-        }
-        if (act) x[C.off + R.rbase + ix] = acc;
+__global__ void __launch_bounds__(PBLOCK) k_qapply_p(const PBlk* __restrict__ blks, const int* __restrict__ soff,
+                                                     int np, int rshift, const real* __restrict__ qf,
+                                                     const real* __restrict__ ep, real* __restrict__ x) {
+    extern __shared__ __align__(16) int s_off[];
+    const PBlk B = blks[blockIdx.x];
+    for (int s = threadIdx.x; s < B.ns; s += blockDim.x) s_off[s] = soff[B.s_begin + s];
+    __syncthreads();
+    const int row = (int)threadIdx.x >> rshift, col = (int)threadIdx.x & ((1 << rshift) - 1);
+    if (row >= B.cnt) return;
+    const int i = B.i0 + row;
+    const int ry = i / B.num0, rx = i - ry * B.num0;
+    const real* __restrict__ e0 = ep + (((long long)(B.pz0 + ry * np + rx) << rshift) + col);
+    const real* __restrict__ q = qf + B.q0 + row;
+    const long long st = B.sstr;
+    real acc = real(0);
+    int s = 0;
+    for (; s + 4 <= B.ns; s += 4) {
+        const int4 o = *reinterpret_cast<const int4*>(&s_off[s]);
+        const real q0 = __ldg(q), q1 = __ldg(q + st), q2 = __ldg(q + 2 * st), q3 = __ldg(q + 3 * st);
+        const real v0 = __ldg(e0 + o.x), v1 = __ldg(e0 + o.y), v2 = __ldg(e0 + o.z), v3 = __ldg(e0 + o.w);
+        acc = fma(q0, v0, acc);
+        acc = fma(q1, v1, acc);
+        acc = fma(q2, v2, acc);
+        acc = fma(q3, v3, acc);
+        q += 4 * st;
+    }
+    for (; s < B.ns; ++s) {
+        acc = fma(__ldg(q), __ldg(e0 + s_off[s]), acc);
+        q += st;
+    }
+    x[((B.x0 + row) << rshift) + col] = acc;
+}
+
+// ep (padded) <- e (compact), one block per (class, z-plane)
+template <typename real>
+__global__ void k_pad_e(const DCls* __restrict__ c1, const int2* __restrict__ planes, PadGeo g, int rshift,
+                        const real* __restrict__ e, real* __restrict__ ep) {
+    const int2 P = planes[blockIdx.x];     // (class, vz)
+    const DCls C = c1[P.x];
+    const int plane = C.num[0] * C.num[1];
+    const long long base = C.off + (long long)(P.y - C.lo[2]) * plane;
+    const int R = 1 << rshift;
+    for (int t = threadIdx.x; t < plane * R; t += blockDim.x) {
+        const int i = t >> rshift, col = t & (R - 1);
+        const int ry = i / C.num[0], rx = i - ry * C.num[0];
+        ep[((long long)pad_index(C, g, C.lo[0] + rx, C.lo[1] + ry, P.y) << rshift) + col] = e[((base + i) << rshift) + col];
     }
 }
 
-// ------------------------------------------------------------------ x = Q1 e, tiled version
-// A warp owns a tile of TY consecutive y-rows (same class, same z) x 32 lanes along x.  Slot
-// descriptors carry everything warp-uniform (neighbour box, base offsets), so the per-lane
-// work per slot is one range check, two coalesced loads and one FMA per row of the tile.
+// ------------------------------------------------------------------ x = Q1 e, symmetric storage
 constexpr int TY = 4;
 struct QSlot {
     int ux0, uy0, uz0;   // slot offset minus the neighbour box origin
@@ -127,60 +169,6 @@ struct QSlot {
     int upper;
     int pad;
 };
-struct QTile {
-    int cls;
-    int vy0, vz;         // first row of the tile (lattice coordinates)
-    int nrows;           // rows in the tile (<= TY)
-};
-template <typename real>
-__global__ void __launch_bounds__(BLOCK) k_qapply_t(const DCls* __restrict__ c1, const QSlot* __restrict__ slots,
-                                                    const QTile* __restrict__ tiles, int ntiles,
-                                                    const real* __restrict__ q, const real* __restrict__ e,
-                                                    real* __restrict__ x) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile = blockIdx.x * WARPS_PER_BLOCK + warp;
-    if (tile >= ntiles) return;
-    const QTile Tl = tiles[tile];
-    const DCls C = c1[Tl.cls];
-    const int ry0 = Tl.vy0 - C.lo[1], rz = Tl.vz - C.lo[2];
-    for (int x0 = 0; x0 < C.num[0]; x0 += 32) {
-        const int ix = x0 + lane;
-        const bool act = ix < C.num[0];
-        const int vx = C.lo[0] + ix;
-        long long rb[TY];
-#pragma unroll
-        for (int t = 0; t < TY; ++t) rb[t] = ((long long)rz * C.num[1] + ry0 + t) * C.num[0] + ix;
-        real acc[TY];
-#pragma unroll
-        for (int t = 0; t < TY; ++t) acc[t] = real(0);
-        for (int s = C.st_begin; s < C.st_end; ++s) {
-            const QSlot S = slots[s];
-            const int uz = Tl.vz + S.uz0;
-            if (uz < 0 || uz >= S.nz) continue;                       // warp-uniform
-            const int ux = vx + S.ux0;
-            const bool xok = act && (unsigned)ux < (unsigned)S.nx;
-            real qv[TY], ev[TY];
-#pragma unroll
-            for (int t = 0; t < TY; ++t) {
-                const int uy = Tl.vy0 + t + S.uy0;
-                const bool ok = xok && t < Tl.nrows && (unsigned)uy < (unsigned)S.ny;
-                const long long nb = ((long long)uz * S.ny + uy) * S.nx + ux;
-                const long long qi = S.upper ? S.qbase + rb[t] : S.qbase + nb;
-                const long long ei = S.ebase + nb;
-                qv[t] = ok ? __ldg(q + qi) : real(0);
-                ev[t] = ok ? __ldg(e + ei) : real(0);
-            }
-#pragma unroll
-            for (int t = 0; t < TY; ++t) acc[t] = fma(qv[t], ev[t], acc[t]);
-        }
-        if (act) {
-#pragma unroll
-            for (int t = 0; t < TY; ++t)
-                if (t < Tl.nrows) x[C.off + rb[t]] = acc[t];
-        }
-    }
-}
-
 // ------------------------------------------------------------------ x = Q1 e, block per (z, class)
 // A block owns one z-plane of one class; its warps take y-tiles of TY rows (32 lanes along x).
 // The class's slot descriptors are staged in shared memory once; the slot loop is straight
@@ -272,86 +260,14 @@ struct PTerm {
     long long bbase;
     real w;
 };
-template <typename real>
-__global__ void __launch_bounds__(BLOCK) k_curlT_e_t(const DCls* __restrict__ c1, const int* __restrict__ pbeg,
-                                                     const PTerm<real>* __restrict__ terms, const QTile* __restrict__ tiles,
-                                                     int ntiles, const real* __restrict__ b, real* e, real ctau) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile = blockIdx.x * WARPS_PER_BLOCK + warp;
-    if (tile >= ntiles) return;
-    const QTile Tl = tiles[tile];
-    const DCls C = c1[Tl.cls];
-    const int ry0 = Tl.vy0 - C.lo[1], rz = Tl.vz - C.lo[2];
-    const int tb = pbeg[Tl.cls], te = pbeg[Tl.cls + 1];
-    for (int x0 = 0; x0 < C.num[0]; x0 += 32) {
-        const int ix = x0 + lane;
-        const bool act = ix < C.num[0];
-        const int vx = C.lo[0] + ix;
-        real acc[TY];
-#pragma unroll
-        for (int t = 0; t < TY; ++t) acc[t] = real(0);
-        for (int s = tb; s < te; ++s) {
-            const PTerm<real> P = terms[s];
-            const int uz = Tl.vz + P.uz0;
-            if (uz < 0 || uz >= P.nz) continue;
-            const int ux = vx + P.ux0;
-            const bool xok = act && (unsigned)ux < (unsigned)P.nx;
-            real bv[TY];
-#pragma unroll
-            for (int t = 0; t < TY; ++t) {
-                const int uy = Tl.vy0 + t + P.uy0;
-                const bool ok = xok && t < Tl.nrows && (unsigned)uy < (unsigned)P.ny;
-                bv[t] = ok ? __ldg(b + P.bbase + ((long long)uz * P.ny + uy) * P.nx + ux) : real(0);
-            }
-#pragma unroll
-            for (int t = 0; t < TY; ++t) acc[t] = fma(P.w, bv[t], acc[t]);
-        }
-        if (act) {
-#pragma unroll
-            for (int t = 0; t < TY; ++t)
-                if (t < Tl.nrows) {
-                    const long long g = C.off + ((long long)rz * C.num[1] + ry0 + t) * C.num[0] + ix;
-                    e[g] = e[g] + ctau * acc[t];
-                }
-        }
-    }
-}
-
-// ------------------------------------------------------------------ b_out = b_in - ctau C x
-template <typename real>
-__global__ void __launch_bounds__(BLOCK) k_curl_b(Tables tb, const DRow* __restrict__ rows, int nrows,
-                                                  const real* __restrict__ x, const real* b_in, real* b_out,
-                                                  real ctau) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = blockIdx.x * WARPS_PER_BLOCK + warp;
-    if (row >= nrows) return;
-    const DRow R = rows[row];
-    const DCls C = tb.c2[R.cls];
-    for (int x0 = 0; x0 < C.num[0]; x0 += 32) {
-        const int ix = x0 + lane;
-        if (ix >= C.num[0]) break;
-        const int vx = C.lo[0] + ix;
-        real acc = real(0);
-        for (int s = C.st_begin; s < C.st_end; ++s) {
-            const DTerm Tm = tb.terms[s];
-            const DCls D = tb.c1[Tm.cls];
-            const int ux = vx + Tm.d[0] - D.lo[0], uy = R.vy + Tm.d[1] - D.lo[1], uz = R.vz + Tm.d[2] - D.lo[2];
-            if (!in_box(D, ux, uy, uz)) continue;        // PEC: boundary edges carry no DoF
-            const real xv = x[D.off + ((long long)uz * D.num[1] + uy) * D.num[0] + ux];
-            acc += Tm.sign > 0 ? xv : -xv;
-        }
-        const long long g = C.off + R.rbase + ix;
-        b_out[g] = b_in[g] - ctau * acc;
-    }
-}
-
 // ------------------------------------------------------------------ e += ctau C^T M2 b
 // Per tet T containing the entity: (1/mu_T) sum_r W[loc][r] b_T[r], W = C_loc^T M2_loc on the
 // curl-carrying local 2-forms (the divergence part of b never changes: C has no row there).
 template <typename real>
 __global__ void __launch_bounds__(BLOCK) k_curlT_e(Tables tb, const DRow* __restrict__ rows, int nrows,
                                                    const real* __restrict__ W, const real* __restrict__ b,
-                                                   const real* __restrict__ inv_mu, real* e, real ctau) {
+                                                   const real* __restrict__ inv_mu, real* e, real ctau, real* ep,
+                                                   PadGeo g) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = blockIdx.x * WARPS_PER_BLOCK + warp;
     if (row >= nrows) return;
@@ -379,8 +295,10 @@ __global__ void __launch_bounds__(BLOCK) k_curlT_e(Tables tb, const DRow* __rest
             if (inv_mu) t *= __ldg(inv_mu + 6 * ((long long)cx + (long long)n * (cy + (long long)n * cz)) + I.shape);
             acc += t;
         }
-        const long long g = C.off + R.rbase + ix;
-        e[g] = e[g] + ctau * acc;
+        const long long gi = C.off + R.rbase + ix;
+        const real v = e[gi] + ctau * acc;
+        e[gi] = v;
+        if (ep) ep[pad_index(C, g, vx, R.vy, R.vz)] = v;
     }
 }
 
@@ -388,7 +306,8 @@ __global__ void __launch_bounds__(BLOCK) k_curlT_e(Tables tb, const DRow* __rest
 template <typename real>
 __global__ void __launch_bounds__(BLOCK) k_curlT_e_b(const DCls* __restrict__ c1, const int* __restrict__ pbeg,
                                                      const PTerm<real>* __restrict__ terms, const QBlock* __restrict__ blocks,
-                                                     int max_terms, const real* __restrict__ b, real* e, real ctau) {
+                                                     int max_terms, const real* __restrict__ b, real* e, real ctau,
+                                                     real* ep, PadGeo g) {
     extern __shared__ long long smem_p[];
     long long* s_b = smem_p;                                               // bbase
     real* s_w = reinterpret_cast<real*>(smem_p + max_terms);                // weight
@@ -441,8 +360,10 @@ __global__ void __launch_bounds__(BLOCK) k_curlT_e_b(const DCls* __restrict__ c1
 #pragma unroll
                 for (int t = 0; t < TY; ++t)
                     if (t < nrows) {
-                        const long long g = g0 + (long long)t * C.num[0];
-                        e[g] = e[g] + ctau * acc[t];
+                        const long long gi = g0 + (long long)t * C.num[0];
+                        const real v = e[gi] + ctau * acc[t];
+                        e[gi] = v;
+                        if (ep) ep[pad_index(C, g, vx, vy0 + t, Bk.vz)] = v;
                     }
             }
         }
@@ -509,12 +430,146 @@ struct DSrc {
 };
 template <typename real>
 __global__ void k_source(const DSrc* __restrict__ src, int nsrc, const long long* __restrict__ dofs,
-                         const real* __restrict__ w, const double* __restrict__ amp, real* e) {
+                         const int* __restrict__ pdofs, const real* __restrict__ w, const double* __restrict__ amp,
+                         real* e, real* ep) {
     for (int s = 0; s < nsrc; ++s) {
         const DSrc S = src[s];
         const real a = (real)amp[s];
-        for (int i = S.begin + threadIdx.x; i < S.end; i += blockDim.x) e[dofs[i]] = e[dofs[i]] - a * w[i];
+        for (int i = S.begin + threadIdx.x; i < S.end; i += blockDim.x) {
+            const real v = e[dofs[i]] - a * w[i];
+            e[dofs[i]] = v;
+            ep[pdofs[i]] = v;
+        }
         __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ R > 1 right-hand sides
+// State vectors are [N][R] (R = 2^rshift contiguous columns).  These kernels give every
+// (DoF, column) pair its own thread inside a block that owns one (class, z-plane): consecutive
+// threads run over the R columns of one DoF, so every gather of a neighbour reads R contiguous
+// values.  The operator tables are the ones of the single-column kernels.
+
+// b_out = b_in - ctau C x
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_curl_b_r(const DCls* __restrict__ c1, const DCls* __restrict__ c2,
+                                                    const DTerm* __restrict__ terms, const QBlock* __restrict__ blocks,
+                                                    int rshift, const real* __restrict__ x, const real* b_in,
+                                                    real* b_out, real ctau) {
+    const QBlock Bk = blocks[blockIdx.x];
+    const DCls C = c2[Bk.cls];
+    const int nt = C.st_end - C.st_begin;
+    int t_ux0[3], t_uy0[3], t_uz0[3], t_nx[3], t_ny[3], t_nz[3], t_sg[3];
+    long long t_off[3];
+    for (int s = 0; s < 3; ++s) {
+        if (s < nt) {
+            const DTerm Tm = terms[C.st_begin + s];
+            const DCls D = c1[Tm.cls];
+            t_ux0[s] = Tm.d[0] - D.lo[0];
+            t_uy0[s] = Tm.d[1] - D.lo[1];
+            t_uz0[s] = Tm.d[2] - D.lo[2];
+            t_nx[s] = D.num[0];
+            t_ny[s] = D.num[1];
+            t_nz[s] = D.num[2];
+            t_off[s] = D.off;
+            t_sg[s] = Tm.sign;
+        } else {
+            t_ux0[s] = t_uy0[s] = t_uz0[s] = 0;
+            t_nx[s] = t_ny[s] = t_nz[s] = 0;      // never valid
+            t_off[s] = 0;
+            t_sg[s] = 0;
+        }
+    }
+    const int plane = C.num[0] * C.num[1], R = 1 << rshift;
+    const long long base = C.off + (long long)(Bk.vz - C.lo[2]) * plane;
+    for (int t = threadIdx.x; t < plane * R; t += blockDim.x) {
+        const int i = t >> rshift, col = t & (R - 1);
+        const int ry = i / C.num[0], rx = i - ry * C.num[0];
+        const int vx = C.lo[0] + rx, vy = C.lo[1] + ry;
+        real acc = real(0);
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            const int ux = vx + t_ux0[s], uy = vy + t_uy0[s], uz = Bk.vz + t_uz0[s];
+            const bool ok = (unsigned)ux < (unsigned)t_nx[s] && (unsigned)uy < (unsigned)t_ny[s] &&
+                            (unsigned)uz < (unsigned)t_nz[s];
+            const real xv =
+                ok ? __ldg(x + ((t_off[s] + ((long long)uz * t_ny[s] + uy) * t_nx[s] + ux) << rshift) + col) : real(0);
+            acc += t_sg[s] > 0 ? xv : -xv;
+        }
+        const long long g = ((base + i) << rshift) + col;
+        b_out[g] = b_in[g] - ctau * acc;
+    }
+}
+
+// e += ctau C^T M2 b with the merged constant stencil (uniform mu); writes the padded copy too
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_curlT_e_r(const DCls* __restrict__ c1, const int* __restrict__ pbeg,
+                                                     const PTerm<real>* __restrict__ terms, const QBlock* __restrict__ blocks,
+                                                     int rshift, const real* __restrict__ b, real* e, real ctau, real* ep,
+                                                     PadGeo g) {
+    extern __shared__ long long smem_r[];
+    const QBlock Bk = blocks[blockIdx.x];
+    const DCls C = c1[Bk.cls];
+    const int tb = pbeg[Bk.cls], nt = pbeg[Bk.cls + 1] - tb;
+    PTerm<real>* s_t = reinterpret_cast<PTerm<real>*>(smem_r);
+    for (int s = threadIdx.x; s < nt; s += blockDim.x) s_t[s] = terms[tb + s];
+    __syncthreads();
+    const int plane = C.num[0] * C.num[1], R = 1 << rshift;
+    const long long base = C.off + (long long)(Bk.vz - C.lo[2]) * plane;
+    for (int t = threadIdx.x; t < plane * R; t += blockDim.x) {
+        const int i = t >> rshift, col = t & (R - 1);
+        const int ry = i / C.num[0], rx = i - ry * C.num[0];
+        const int vx = C.lo[0] + rx, vy = C.lo[1] + ry;
+        real acc = real(0);
+        for (int s = 0; s < nt; ++s) {
+            const PTerm<real> P = s_t[s];
+            const int ux = vx + P.ux0, uy = vy + P.uy0, uz = Bk.vz + P.uz0;
+            if ((unsigned)ux < (unsigned)P.nx && (unsigned)uy < (unsigned)P.ny && (unsigned)uz < (unsigned)P.nz)
+                acc = fma(P.w, __ldg(b + ((P.bbase + ((long long)uz * P.ny + uy) * P.nx + ux) << rshift) + col), acc);
+        }
+        const long long gi = ((base + i) << rshift) + col;
+        const real v = e[gi] + ctau * acc;
+        e[gi] = v;
+        if (ep) ep[((long long)pad_index(C, g, vx, vy, Bk.vz) << rshift) + col] = v;
+    }
+}
+
+// e += ctau C^T M2 b tet by tet (per-tet 1/mu); writes the padded copy too
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_curlT_e_rt(Tables tb, const QBlock* __restrict__ blocks, int rshift,
+                                                      const real* __restrict__ W, const real* __restrict__ b,
+                                                      const real* __restrict__ inv_mu, real* e, real ctau, real* ep,
+                                                      PadGeo g) {
+    const QBlock Bk = blocks[blockIdx.x];
+    const DCls C = tb.c1[Bk.cls];
+    const int n = tb.n, n2a = tb.n2a;
+    const int plane = C.num[0] * C.num[1], R = 1 << rshift;
+    const long long base = C.off + (long long)(Bk.vz - C.lo[2]) * plane;
+    for (int t = threadIdx.x; t < plane * R; t += blockDim.x) {
+        const int i = t >> rshift, col = t & (R - 1);
+        const int ry = i / C.num[0], rx = i - ry * C.num[0];
+        const int vx = C.lo[0] + rx, vy = C.lo[1] + ry;
+        real acc = real(0);
+        for (int ic = C.inc_begin; ic < C.inc_end; ++ic) {
+            const DInc I = tb.inc[ic];
+            const int cx = vx + I.dcube[0], cy = vy + I.dcube[1], cz = Bk.vz + I.dcube[2];
+            const real* Wr = W + (long long)I.loc * n2a;
+            const DLoc2* L2 = tb.loc2 + I.shape * n2a;
+            real tq = real(0);
+            for (int r = 0; r < n2a; ++r) {
+                const DLoc2 Lr = L2[r];
+                const DCls D = tb.c2[Lr.cls];
+                const int ux = cx + Lr.off[0] - D.lo[0], uy = cy + Lr.off[1] - D.lo[1], uz = cz + Lr.off[2] - D.lo[2];
+                if (!in_box(D, ux, uy, uz)) continue;    // PEC: boundary faces carry no DoF
+                tq = fma(__ldg(Wr + r), __ldg(b + ((D.off + ((long long)uz * D.num[1] + uy) * D.num[0] + ux) << rshift) + col), tq);
+            }
+            if (inv_mu) tq *= __ldg(inv_mu + 6 * ((long long)cx + (long long)n * (cy + (long long)n * cz)) + I.shape);
+            acc += tq;
+        }
+        const long long gi = ((base + i) << rshift) + col;
+        const real v = e[gi] + ctau * acc;
+        e[gi] = v;
+        if (ep) ep[((long long)pad_index(C, g, vx, vy, Bk.vz) << rshift) + col] = v;
     }
 }
 
@@ -621,10 +676,80 @@ __global__ void k_finish(const double2* __restrict__ p1, int n1, const double2* 
     if (threadIdx.x == 0) *out = 0.5 * (a.s + a.c) + 0.5 * (b.s + b.c);
 }
 
-template <typename T>
-__global__ void k_convert(const double* __restrict__ in, T* __restrict__ out, long long n) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        out[i] = (T)in[i];
+// ---- energies per right-hand side (R > 1): part[block][col], fixed-order merges
+// the block's threads with equal column merge their partial sums in thread order
+__device__ Neu block_reduce_col(Neu v, int rshift, Neu* sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    const int R = 1 << rshift;
+    Neu r{0.0, 0.0};
+    if ((int)threadIdx.x < R)
+        for (int j = threadIdx.x; j < (int)blockDim.x; j += R) r = neu_merge(r, sh[j]);
+    __syncthreads();
+    return r;
+}
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_dot_r(const real* __restrict__ a, const real* __restrict__ b, long long n,
+                                                 int rshift, double2* part) {
+    __shared__ Neu sh[BLOCK];
+    const int R = 1 << rshift, col = threadIdx.x & (R - 1);
+    const long long per = blockDim.x >> rshift;
+    Neu v{0.0, 0.0};
+    for (long long i = (long long)blockIdx.x * per + (threadIdx.x >> rshift); i < n; i += (long long)gridDim.x * per)
+        v = neu_add(v, (double)a[(i << rshift) + col] * (double)b[(i << rshift) + col]);
+    v = block_reduce_col(v, rshift, sh);
+    if ((int)threadIdx.x < R) part[(long long)blockIdx.x * R + threadIdx.x] = make_double2(v.s, v.c);
+}
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_tet_quad_r(Tables tb, const double* __restrict__ M2a, const real* __restrict__ bn,
+                                                      const real* __restrict__ bo, const real* __restrict__ inv_mu, int rshift,
+                                                      double2* part) {
+    __shared__ Neu sh[BLOCK];
+    const int n = tb.n, n2a = tb.n2a;
+    const long long T = 6LL * n * n * n;
+    const int R = 1 << rshift, col = threadIdx.x & (R - 1);
+    const long long per = blockDim.x >> rshift;
+    Neu v{0.0, 0.0};
+    double vn[27], vo[27];
+    for (long long t = (long long)blockIdx.x * per + (threadIdx.x >> rshift); t < T; t += (long long)gridDim.x * per) {
+        const int s = (int)(t % 6);
+        const long long cube = t / 6;
+        const int cx = (int)(cube % n), cy = (int)((cube / n) % n), cz = (int)(cube / ((long long)n * n));
+        for (int r = 0; r < n2a; ++r) {
+            const DLoc2 Lr = tb.loc2[s * n2a + r];
+            const DCls D = tb.c2[Lr.cls];
+            const int ux = cx + Lr.off[0] - D.lo[0], uy = cy + Lr.off[1] - D.lo[1], uz = cz + Lr.off[2] - D.lo[2];
+            if (in_box(D, ux, uy, uz)) {
+                const long long gi = ((D.off + ((long long)uz * D.num[1] + uy) * D.num[0] + ux) << rshift) + col;
+                vn[r] = (double)bn[gi];
+                vo[r] = (double)bo[gi];
+            } else {
+                vn[r] = 0.0;
+                vo[r] = 0.0;
+            }
+        }
+        double q = 0.0;
+        for (int r = 0; r < n2a; ++r) {
+            double u = 0.0;
+            for (int c = 0; c < n2a; ++c) u += M2a[r * n2a + c] * vo[c];
+            q += vn[r] * u;
+        }
+        if (inv_mu) q *= (double)inv_mu[t];
+        v = neu_add(v, q);
+    }
+    v = block_reduce_col(v, rshift, sh);
+    if ((int)threadIdx.x < R) part[(long long)blockIdx.x * R + threadIdx.x] = make_double2(v.s, v.c);
+}
+// out[col] = 0.5 sum_blocks p1[block][col] + 0.5 sum_blocks p2[block][col], one thread per column
+__global__ void k_finish_r(const double2* __restrict__ p1, const double2* __restrict__ p2, int nblk, int R, double* out) {
+    for (int col = threadIdx.x; col < R; col += blockDim.x) {
+        Neu a{0.0, 0.0}, b{0.0, 0.0};
+        for (int i = 0; i < nblk; ++i) {
+            a = neu_merge(a, Neu{p1[(long long)i * R + col].x, p1[(long long)i * R + col].y});
+            b = neu_merge(b, Neu{p2[(long long)i * R + col].x, p2[(long long)i * R + col].y});
+        }
+        out[col] = 0.5 * (a.s + a.c) + 0.5 * (b.s + b.c);
+    }
 }
 
 }  // namespace
@@ -632,7 +757,7 @@ __global__ void k_convert(const double* __restrict__ in, T* __restrict__ out, lo
 // ====================================================================== context
 struct ygm_ctx {
     ygm::Setup S;
-    int precision = YGM_FP64, n_rhs = 1, energy_every = 0, device = 0;
+    int precision = YGM_FP64, n_rhs = 1, rshift = 0, energy_every = 0, device = 0;   // n_rhs = 2^rshift
     size_t rs = 8;                          // sizeof(real)
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -645,8 +770,8 @@ struct ygm_ctx {
     DTerm* terms = nullptr;
     DInc* inc = nullptr;
     DLoc2* loc2 = nullptr;
-    DRow *rowsA = nullptr, *rowsB = nullptr, *rowsE = nullptr;
-    int nrowsA = 0, nrowsB = 0, nrowsE = 0;
+    DRow* rowsE = nullptr;
+    int nrowsE = 0;
     double2* part = nullptr;
     int npart = 0;
     double* hist = nullptr;
@@ -666,8 +791,17 @@ struct ygm_ctx {
     int nqblocks = 0, max_slots = 0, qthreads = BLOCK;
     QBlock *eblocks = nullptr, *bblocks = nullptr;
     int neblocks = 0, nbblocks = 0, max_terms = 0;
-    QTile *tilesA = nullptr, *tilesE = nullptr;
-    int ntilesA = 0, ntilesE = 0;
+    // padded copy of e and full-row Q1 (k_qapply_p)
+    void *ep = nullptr, *qf = nullptr;
+    PBlk* pblks = nullptr;                   // every row of every class (first npblks_act: curl-carrying rows)
+    int npblks = 0, npblks_act = 0, max_ns = 0;
+    int* soff = nullptr;
+    int2* planes = nullptr;                  // (class, vz) of every non-empty 1-form plane
+    int nplanes = 0;
+    PadGeo pg{0, 0};
+    long long n1pad = 0;
+    int* spdofs = nullptr;                   // padded indices of the source DoFs
+    int64_t qc_rows[2] = {0, 0}, qc_unique[2] = {0, 0}, qc_stored[2] = {0, 0};   // [active only, all rows]
     void* pterms = nullptr;                  // PTerm<real> merged C^T M2 stencil (uniform mu)
     int* pbeg = nullptr;
     // time state
@@ -778,6 +912,16 @@ static int setup_device(ygm_ctx* ctx) {
     ygm::Setup& S = ctx->S;
     ygm::Lattice& L = S.L;
     const int k = L.k;
+    // padded copy of e: halo H = the widest Q1 stencil offset
+    int H = 0;
+    for (const auto& st : S.st_slots)
+        for (int a = 0; a < 3; ++a) H = std::max(H, std::abs((int)st.d[a]));
+    const int NP = L.n + 2 * H + 1;
+    const long long np3 = (long long)NP * NP * NP;
+    if (np3 * (long long)L.c1.size() * ctx->n_rhs > (long long)INT32_MAX)
+        return fail(ctx, YGM_EINVAL, "mesh x n_rhs too large for 32-bit indices of the padded e copy");
+    ctx->pg = PadGeo{H, NP};
+    ctx->n1pad = np3 * (long long)L.c1.size();
     // classes
     std::vector<DCls> c1(L.c1.size()), c2(L.c2.size());
     std::vector<DInc> inc;
@@ -795,6 +939,8 @@ static int setup_device(ygm_ctx* ctx) {
         D.inc_begin = (int)inc.size();
         for (auto& I : L.inc1[c]) inc.push_back(DInc{{I.dcube[0], I.dcube[1], I.dcube[2]}, I.shape, I.loc});
         D.inc_end = (int)inc.size();
+        D.pbase = (int)(c * np3);
+        D.pad_ = 0;
     }
     std::vector<DSlot> slots(S.st_slots.size());
     for (size_t s = 0; s < slots.size(); ++s)
@@ -814,6 +960,7 @@ static int setup_device(ygm_ctx* ctx) {
         D.size = L.c2[c].box.size;
         D.qoff = 0;
         D.inc_begin = D.inc_end = 0;
+        D.pbase = D.pad_ = 0;
         D.st_begin = (int)terms.size();
         if (L.c2[c].active) {
             // find a tet shape and local index carrying this class
@@ -845,12 +992,9 @@ static int setup_device(ygm_ctx* ctx) {
         (rc = upload(ctx, &ctx->terms, terms)) || (rc = upload(ctx, &ctx->inc, inc)) || (rc = upload(ctx, &ctx->loc2, loc2)))
         return rc;
     // rows
-    std::vector<DRow> rA = make_rows(L.c1, L.n, false), rE = make_rows(L.c1, L.n, true), rB = make_rows(L.c2, L.n, true);
-    ctx->nrowsA = (int)rA.size();
+    std::vector<DRow> rE = make_rows(L.c1, L.n, true);
     ctx->nrowsE = (int)rE.size();
-    ctx->nrowsB = (int)rB.size();
-    if ((rc = upload(ctx, &ctx->rowsA, rA)) || (rc = upload(ctx, &ctx->rowsE, rE)) || (rc = upload(ctx, &ctx->rowsB, rB)))
-        return rc;
+    if ((rc = upload(ctx, &ctx->rowsE, rE))) return rc;
     // operators
     if ((rc = upload_real(ctx, &ctx->q, S.qvals)) || (rc = upload_real(ctx, &ctx->W, S.Wloc))) return rc;
     std::vector<double> M2a(S.M2aloc);
@@ -875,9 +1019,9 @@ static int setup_device(ygm_ctx* ctx) {
     CK(cudaMemsetAsync(ctx->b[1], 0, L.N2 * R * ctx->rs, ctx->stream));
     CK(cudaMemsetAsync(ctx->bscr, 0, L.N2 * R * ctx->rs, ctx->stream));
     ctx->npart = 4 * 152;
-    CK(cudaMalloc((void**)&ctx->part, 2 * ctx->npart * sizeof(double2)));
-    ctx->hist_cap = 1 << 16;
-    CK(cudaMalloc((void**)&ctx->hist, ctx->hist_cap * sizeof(double)));
+    CK(cudaMalloc((void**)&ctx->part, 2 * (size_t)ctx->npart * ctx->n_rhs * sizeof(double2)));
+    ctx->hist_cap = 1 << 16;   // records of R values
+    CK(cudaMalloc((void**)&ctx->hist, (size_t)ctx->hist_cap * ctx->n_rhs * sizeof(double)));
     ctx->tb = Tables{ctx->c1, ctx->c2, ctx->slots, ctx->terms, ctx->inc, ctx->loc2, L.n, L.n1, L.n2a};
     (void)k;
     // flattened Q1 slot descriptors
@@ -899,20 +1043,6 @@ static int setup_device(ygm_ctx* ctx) {
             Q.pad = 0;
         }
     if ((rc = upload(ctx, &ctx->qslots, qs))) return rc;
-    auto make_tiles = [&](bool active_only) {
-        std::vector<QTile> t;
-        for (int vz = 0; vz < L.n; ++vz)
-            for (int j = 0; j * TY < L.n; ++j)
-                for (int c = 0; c < (int)L.c1.size(); ++c) {
-                    const auto& b = L.c1[c].box;
-                    if (active_only && !L.c1[c].active) continue;
-                    if (vz < b.lo[2] || vz >= b.lo[2] + b.num[2] || b.num[0] == 0) continue;
-                    int vy0 = b.lo[1] + j * TY;
-                    if (vy0 >= b.lo[1] + b.num[1]) continue;
-                    t.push_back(QTile{c, vy0, vz, std::min(TY, b.lo[1] + b.num[1] - vy0)});
-                }
-        return t;
-    };
     std::vector<QBlock> qb;
     for (int vz = 0; vz < L.n; ++vz)
         for (int c = 0; c < (int)L.c1.size(); ++c) {
@@ -921,6 +1051,70 @@ static int setup_device(ygm_ctx* ctx) {
             qb.push_back(QBlock{c, vz});
         }
     ctx->nqblocks = (int)qb.size();
+    // k_qapply_p: slot offsets in the padded layout, row blocks, full-row Q1, padded e
+    {
+        std::vector<int> so(S.st_slots.size());
+        for (size_t c = 0; c < L.c1.size(); ++c)
+            for (int sidx = S.st_begin[c]; sidx < S.st_begin[c + 1]; ++sidx) {
+                const auto& st = S.st_slots[sidx];
+                so[sidx] = (int)((((long long)st.cls - (long long)c) * np3 + ((long long)st.d[2] * NP + st.d[1]) * NP + st.d[0])
+                                 << ctx->rshift);
+            }
+        // rows of the curl-carrying classes first: x of a gradient 1-form (a zero column of C) is
+        // needed only by the energy, so the steps without an energy read-out skip those rows
+        std::vector<PBlk> pb;
+        std::vector<int2> planes;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int vz = 0; vz < L.n; ++vz)
+            for (int c = 0; c < (int)L.c1.size(); ++c) {
+                const auto& b = L.c1[c].box;
+                if (L.c1[c].active != (pass == 0)) continue;
+                if (vz < b.lo[2] || vz >= b.lo[2] + b.num[2] || b.num[0] == 0 || b.num[1] == 0) continue;
+                planes.push_back(make_int2(c, vz));
+                const int plane = b.num[0] * b.num[1], rz = vz - b.lo[2];
+                const long long qplane = S.qf_plane[c];
+                const int pz0 = (int)(c * np3) + ((vz + H) * NP + b.lo[1] + H) * NP + b.lo[0] + H;
+                const int rows_per = PBLOCK >> ctx->rshift;   // a row owns R threads
+                for (int i0 = 0; i0 < plane; i0 += rows_per)
+                    pb.push_back(PBlk{i0, std::min(rows_per, plane - i0), b.num[0], pz0, S.st_begin[c],
+                                      S.st_begin[c + 1] - S.st_begin[c], (long long)S.qf_off[c] + rz * qplane + i0,
+                                      (long long)b.num[2] * qplane, (long long)b.offset + (long long)rz * plane + i0});
+            }
+            if (pass == 0) ctx->npblks_act = (int)pb.size();
+        }
+        ctx->npblks = (int)pb.size();
+        ctx->nplanes = (int)planes.size();
+        if ((rc = upload(ctx, &ctx->soff, so)) || (rc = upload(ctx, &ctx->pblks, pb)) ||
+            (rc = upload(ctx, &ctx->planes, planes)) || (rc = upload_real(ctx, &ctx->qf, S.qfull)))
+            return rc;
+        for (size_t c = 0; c < L.c1.size(); ++c) ctx->max_ns = std::max(ctx->max_ns, S.st_begin[c + 1] - S.st_begin[c]);
+        // roofline counts of the two launch kinds
+        std::vector<char> act(L.N1, 0);
+        for (size_t c = 0; c < L.c1.size(); ++c) {
+            const auto& b = L.c1[c].box;
+            const int64_t stored = (int64_t)(S.st_begin[c + 1] - S.st_begin[c]) * S.qf_plane[c] * b.num[2];
+            for (int a = 0; a < 2; ++a)
+                if (a == 1 || L.c1[c].active) {
+                    ctx->qc_rows[a] += b.size;
+                    ctx->qc_stored[a] += stored;
+                }
+            if (L.c1[c].active) std::fill(act.begin() + b.offset, act.begin() + b.offset + b.size, 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            int64_t ent = 0, both = 0;   // entries of the computed rows; off-diagonal ones between two such rows
+            for (int64_t i = 0; i < L.N1; ++i) {
+                if (a == 0 && !act[i]) continue;
+                for (int64_t p = S.Q1.ptr[i]; p < S.Q1.ptr[i + 1]; ++p) {
+                    ++ent;
+                    const int64_t j = S.Q1.col[p];
+                    if (j != i && (a == 1 || act[j])) ++both;
+                }
+            }
+            ctx->qc_unique[a] = ent - both / 2;
+        }
+        CK(cudaMalloc(&ctx->ep, (size_t)ctx->n1pad * ctx->n_rhs * ctx->rs));
+        CK(cudaMemsetAsync(ctx->ep, 0, (size_t)ctx->n1pad * ctx->n_rhs * ctx->rs, ctx->stream));
+    }
     // k_qapply_b: one warp per TY y-rows of the class box, at most 8 warps per block
     ctx->qthreads = 32 * std::max(1, std::min(WARPS_PER_BLOCK, (L.n + TY - 1) / TY));
     if ((rc = upload(ctx, &ctx->qblocks, qb))) return rc;
@@ -941,10 +1135,6 @@ static int setup_device(ygm_ctx* ctx) {
     ctx->neblocks = (int)eb.size();
     ctx->nbblocks = (int)bb.size();
     if ((rc = upload(ctx, &ctx->eblocks, eb)) || (rc = upload(ctx, &ctx->bblocks, bb))) return rc;
-    std::vector<QTile> tA = make_tiles(false), tE = make_tiles(true);
-    ctx->ntilesA = (int)tA.size();
-    ctx->ntilesE = (int)tE.size();
-    if ((rc = upload(ctx, &ctx->tilesA, tA)) || (rc = upload(ctx, &ctx->tilesE, tE))) return rc;
     // merged C^T M2 stencil when mu is uniform
     double mu0 = S.mu.empty() ? 1.0 : S.mu[0];
     bool mu_uniform = true;
@@ -997,7 +1187,8 @@ static int setup_device(ygm_ctx* ctx) {
     const size_t smem_q = (size_t)ctx->max_slots * (2 * sizeof(long long) + 8 * sizeof(int));
     const size_t smem_e = (size_t)ctx->max_terms * sizeof(long long) + (size_t)(ctx->max_terms + 1) * ctx->rs +
                           (size_t)ctx->max_terms * 6 * sizeof(int);
-    if (smem_q > 227 * 1024 || smem_e > 227 * 1024) return fail(ctx, YGM_EINVAL, "stencil too wide for shared memory");
+    if (smem_q > 227 * 1024 || smem_e > 227 * 1024 || (size_t)ctx->max_ns * sizeof(int) > 48 * 1024)
+        return fail(ctx, YGM_EINVAL, "stencil too wide for shared memory");
     // raise-only: the limit is process-wide per kernel, shared by every context (a smaller value
     // set by one context would make another context's launches invalid)
     {
@@ -1026,16 +1217,19 @@ static int setup_device(ygm_ctx* ctx) {
 }
 
 // ------------------------------------------------------------------ launch helpers
-static int launch_qapply(ygm_ctx* ctx, const void* e, void* x) {
-    if (!ctx->nqblocks) return 0;
+// x = Q1 e of the context state, read from the padded copy of e; all_rows = false computes only
+// the rows of the curl-carrying 1-forms (all that C x needs)
+static int launch_qapply(ygm_ctx* ctx, void* x, bool all_rows) {
+    const int nb = all_rows ? ctx->npblks : ctx->npblks_act;
+    if (!nb) return 0;
     time_begin(ctx, KQ);
-    const size_t smem = (size_t)ctx->max_slots * (2 * sizeof(long long) + 8 * sizeof(int));
+    const size_t smem = (size_t)ctx->max_ns * sizeof(int);
     if (ctx->precision == YGM_FP64)
-        k_qapply_b<double><<<ctx->nqblocks, ctx->qthreads, smem, ctx->stream>>>(ctx->c1, ctx->qslots, ctx->qblocks, ctx->max_slots,
-                                                                        (const double*)ctx->q, (const double*)e, (double*)x);
+        k_qapply_p<double><<<nb, PBLOCK, smem, ctx->stream>>>(ctx->pblks, ctx->soff, ctx->pg.NP, ctx->rshift, (const double*)ctx->qf,
+                                                                       (const double*)ctx->ep, (double*)x);
     else
-        k_qapply_b<float><<<ctx->nqblocks, ctx->qthreads, smem, ctx->stream>>>(ctx->c1, ctx->qslots, ctx->qblocks, ctx->max_slots,
-                                                                       (const float*)ctx->q, (const float*)e, (float*)x);
+        k_qapply_p<float><<<nb, PBLOCK, smem, ctx->stream>>>(ctx->pblks, ctx->soff, ctx->pg.NP, ctx->rshift, (const float*)ctx->qf,
+                                                                      (const float*)ctx->ep, (float*)x);
     time_end(ctx);
     ctx->launches++;
     return 0;
@@ -1043,7 +1237,15 @@ static int launch_qapply(ygm_ctx* ctx, const void* e, void* x) {
 static int launch_curl_b(ygm_ctx* ctx, const void* x, const void* bin, void* bout, double ctau) {
     if (!ctx->nbblocks) return 0;
     time_begin(ctx, KB);
-    if (ctx->precision == YGM_FP64)
+    if (ctx->rshift) {
+        if (ctx->precision == YGM_FP64)
+            k_curl_b_r<double><<<ctx->nbblocks, BLOCK, 0, ctx->stream>>>(ctx->c1, ctx->c2, ctx->terms, ctx->bblocks, ctx->rshift,
+                                                                         (const double*)x, (const double*)bin, (double*)bout, ctau);
+        else
+            k_curl_b_r<float><<<ctx->nbblocks, BLOCK, 0, ctx->stream>>>(ctx->c1, ctx->c2, ctx->terms, ctx->bblocks, ctx->rshift,
+                                                                        (const float*)x, (const float*)bin, (float*)bout,
+                                                                        (float)ctau);
+    } else if (ctx->precision == YGM_FP64)
         k_curl_b_b<double><<<ctx->nbblocks, BLOCK, 0, ctx->stream>>>(ctx->c1, ctx->c2, ctx->terms, ctx->bblocks,
                                                                      (const double*)x, (const double*)bin, (double*)bout, ctau);
     else
@@ -1056,27 +1258,51 @@ static int launch_curl_b(ygm_ctx* ctx, const void* x, const void* bin, void* bou
 }
 static int launch_curlT_e(ygm_ctx* ctx, const void* b, void* e, double ctau) {
     time_begin(ctx, KE);
-    if (ctx->pterms) {
+    if (ctx->rshift) {
+        if (!ctx->neblocks) {
+        } else if (ctx->pterms) {
+            const size_t smem = (size_t)ctx->max_terms * (ctx->precision == YGM_FP64 ? sizeof(PTerm<double>) : sizeof(PTerm<float>));
+            if (ctx->precision == YGM_FP64)
+                k_curlT_e_r<double><<<ctx->neblocks, BLOCK, smem, ctx->stream>>>(
+                    ctx->c1, ctx->pbeg, (const PTerm<double>*)ctx->pterms, ctx->eblocks, ctx->rshift, (const double*)b,
+                    (double*)e, ctau, (double*)ctx->ep, ctx->pg);
+            else
+                k_curlT_e_r<float><<<ctx->neblocks, BLOCK, smem, ctx->stream>>>(
+                    ctx->c1, ctx->pbeg, (const PTerm<float>*)ctx->pterms, ctx->eblocks, ctx->rshift, (const float*)b,
+                    (float*)e, (float)ctau, (float*)ctx->ep, ctx->pg);
+        } else {
+            if (ctx->precision == YGM_FP64)
+                k_curlT_e_rt<double><<<ctx->neblocks, BLOCK, 0, ctx->stream>>>(
+                    ctx->tb, ctx->eblocks, ctx->rshift, (const double*)ctx->W, (const double*)b, (const double*)ctx->inv_mu,
+                    (double*)e, ctau, (double*)ctx->ep, ctx->pg);
+            else
+                k_curlT_e_rt<float><<<ctx->neblocks, BLOCK, 0, ctx->stream>>>(
+                    ctx->tb, ctx->eblocks, ctx->rshift, (const float*)ctx->W, (const float*)b, (const float*)ctx->inv_mu,
+                    (float*)e, (float)ctau, (float*)ctx->ep, ctx->pg);
+        }
+    } else if (ctx->pterms) {
         const int mt = ctx->max_terms;
         const size_t smem = (size_t)mt * sizeof(long long) + (size_t)(mt + (mt & 1)) * ctx->rs + (size_t)mt * 6 * sizeof(int);
         if (ctx->neblocks) {
             if (ctx->precision == YGM_FP64)
                 k_curlT_e_b<double><<<ctx->neblocks, BLOCK, smem, ctx->stream>>>(
-                    ctx->c1, ctx->pbeg, (const PTerm<double>*)ctx->pterms, ctx->eblocks, mt, (const double*)b, (double*)e, ctau);
+                    ctx->c1, ctx->pbeg, (const PTerm<double>*)ctx->pterms, ctx->eblocks, mt, (const double*)b, (double*)e, ctau,
+                    (double*)ctx->ep, ctx->pg);
             else
                 k_curlT_e_b<float><<<ctx->neblocks, BLOCK, smem, ctx->stream>>>(
                     ctx->c1, ctx->pbeg, (const PTerm<float>*)ctx->pterms, ctx->eblocks, mt, (const float*)b, (float*)e,
-                    (float)ctau);
+                    (float)ctau, (float*)ctx->ep, ctx->pg);
         }
     } else {
         dim3 g((ctx->nrowsE + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
         if (ctx->precision == YGM_FP64)
             k_curlT_e<double><<<g, BLOCK, 0, ctx->stream>>>(ctx->tb, ctx->rowsE, ctx->nrowsE, (const double*)ctx->W,
-                                                            (const double*)b, (const double*)ctx->inv_mu, (double*)e, ctau);
+                                                            (const double*)b, (const double*)ctx->inv_mu, (double*)e, ctau,
+                                                            (double*)ctx->ep, ctx->pg);
         else
             k_curlT_e<float><<<g, BLOCK, 0, ctx->stream>>>(ctx->tb, ctx->rowsE, ctx->nrowsE, (const float*)ctx->W,
                                                            (const float*)b, (const float*)ctx->inv_mu, (float*)e,
-                                                           (float)ctau);
+                                                           (float)ctau, (float*)ctx->ep, ctx->pg);
     }
     time_end(ctx);
     ctx->launches++;
@@ -1086,12 +1312,24 @@ static int launch_source(ygm_ctx* ctx, const double* amp_dev) {
     if (!ctx->nsrc) return 0;
     time_begin(ctx, KS);
     if (ctx->precision == YGM_FP64)
-        k_source<double><<<1, 256, 0, ctx->stream>>>(ctx->dsrc, ctx->nsrc, ctx->sdofs, (const double*)ctx->sw, amp_dev,
-                                                     (double*)ctx->e);
+        k_source<double><<<1, 256, 0, ctx->stream>>>(ctx->dsrc, ctx->nsrc, ctx->sdofs, ctx->spdofs, (const double*)ctx->sw,
+                                                     amp_dev, (double*)ctx->e, (double*)ctx->ep);
     else
-        k_source<float><<<1, 256, 0, ctx->stream>>>(ctx->dsrc, ctx->nsrc, ctx->sdofs, (const float*)ctx->sw, amp_dev,
-                                                    (float*)ctx->e);
+        k_source<float><<<1, 256, 0, ctx->stream>>>(ctx->dsrc, ctx->nsrc, ctx->sdofs, ctx->spdofs, (const float*)ctx->sw,
+                                                    amp_dev, (float*)ctx->e, (float*)ctx->ep);
     time_end(ctx);
+    ctx->launches++;
+    return 0;
+}
+// refresh the padded copy of e after the compact state was overwritten
+static int launch_pad_e(ygm_ctx* ctx) {
+    if (!ctx->nplanes) return 0;
+    if (ctx->precision == YGM_FP64)
+        k_pad_e<double><<<ctx->nplanes, BLOCK, 0, ctx->stream>>>(ctx->c1, ctx->planes, ctx->pg, ctx->rshift, (const double*)ctx->e,
+                                                                 (double*)ctx->ep);
+    else
+        k_pad_e<float><<<ctx->nplanes, BLOCK, 0, ctx->stream>>>(ctx->c1, ctx->planes, ctx->pg, ctx->rshift, (const float*)ctx->e,
+                                                                (float*)ctx->ep);
     ctx->launches++;
     return 0;
 }
@@ -1100,6 +1338,23 @@ static int launch_energy(ygm_ctx* ctx, const void* e, const void* x, const void*
     const int np = ctx->npart;
     const long long N1 = ctx->S.L.N1;
     time_begin(ctx, KW);
+    if (ctx->rshift) {   // out[R]
+        const int R = ctx->n_rhs;
+        double2* p2 = ctx->part + (size_t)np * R;
+        if (ctx->precision == YGM_FP64) {
+            k_dot_r<double><<<np, BLOCK, 0, ctx->stream>>>((const double*)e, (const double*)x, N1, ctx->rshift, ctx->part);
+            k_tet_quad_r<double><<<np, BLOCK, 0, ctx->stream>>>(ctx->tb, ctx->M2a, (const double*)bn, (const double*)bo,
+                                                                (const double*)ctx->inv_mu, ctx->rshift, p2);
+        } else {
+            k_dot_r<float><<<np, BLOCK, 0, ctx->stream>>>((const float*)e, (const float*)x, N1, ctx->rshift, ctx->part);
+            k_tet_quad_r<float><<<np, BLOCK, 0, ctx->stream>>>(ctx->tb, ctx->M2a, (const float*)bn, (const float*)bo,
+                                                               (const float*)ctx->inv_mu, ctx->rshift, p2);
+        }
+        k_finish_r<<<1, 256, 0, ctx->stream>>>(ctx->part, p2, np, R, out);
+        time_end(ctx);
+        ctx->launches += 3;
+        return 0;
+    }
     if (ctx->precision == YGM_FP64) {
         k_dot<double><<<np, BLOCK, 0, ctx->stream>>>((const double*)e, (const double*)x, N1, ctx->part);
         k_tet_quad<double><<<np, BLOCK, 0, ctx->stream>>>(ctx->tb, ctx->M2a, (const double*)bn, (const double*)bo,
@@ -1153,7 +1408,8 @@ int ygm_create(const ygm_mesh* mesh, int order, const double* eps, const double*
     o.n_rhs = 1;
     if (opts) o = *opts;
     if (o.precision != YGM_FP64 && o.precision != YGM_FP32) return cerr(YGM_EINVAL, "precision must be YGM_FP64 or YGM_FP32");
-    if (o.n_rhs != 1) return cerr(YGM_EINVAL, "n_rhs > 1 is not supported by this build");
+    if (o.n_rhs < 1 || o.n_rhs > 256 || (o.n_rhs & (o.n_rhs - 1)))
+        return cerr(YGM_EINVAL, "n_rhs must be a power of two in [1, 256]");
     if (o.energy_every < 0) return cerr(YGM_EINVAL, "energy_every must be >= 0");
     if (o.q1_pattern < 0 || o.q1_pattern > 3) return cerr(YGM_EINVAL, "unknown q1_pattern");
     const bool host_only = o.device == -1;
@@ -1167,6 +1423,7 @@ int ygm_create(const ygm_mesh* mesh, int order, const double* eps, const double*
     ctx->precision = o.precision;
     ctx->rs = o.precision == YGM_FP64 ? 8 : 4;
     ctx->n_rhs = o.n_rhs;
+    while ((1 << ctx->rshift) < o.n_rhs) ++ctx->rshift;
     ctx->energy_every = o.energy_every;
     ctx->device = o.device;
     ctx->host_only = host_only;
@@ -1226,6 +1483,8 @@ int ygm_set_state(ygm_ctx* ctx, const void* e, const void* b, int on_device) {
     CK(cudaMemcpyAsync(ctx->e, e, ne, kind, ctx->stream));
     CK(cudaMemcpyAsync(ctx->b[0], b, nb, kind, ctx->stream));
     CK(cudaMemcpyAsync(ctx->b[1], b, nb, kind, ctx->stream));
+    launch_pad_e(ctx);
+    CK(cudaGetLastError());
     if (!on_device) CK(cudaStreamSynchronize(ctx->stream));
     ctx->cur = 0;
     ctx->staggered = false;
@@ -1245,7 +1504,7 @@ int ygm_get_state(ygm_ctx* ctx, void* e, void* b, int on_device, int synced) {
         const void* src = ctx->b[ctx->cur];
         if (synced && ctx->staggered) {
             CK(cudaMemcpyAsync(ctx->bscr, ctx->b[ctx->cur], nb, cudaMemcpyDeviceToDevice, ctx->stream));
-            launch_qapply(ctx, ctx->e, ctx->x);
+            launch_qapply(ctx, ctx->x, false);
             launch_curl_b(ctx, ctx->x, ctx->b[ctx->cur], ctx->bscr, 0.5 * ctx->dt_prev);
             src = ctx->bscr;
         }
@@ -1266,9 +1525,13 @@ int ygm_project_E(ygm_ctx* ctx, void (*E0)(const double x[3], double out[3], voi
     int rc;
     void* de = nullptr;
     if ((rc = upload_real(ctx, &de, e0))) return rc;
-    CK(cudaMemcpyAsync(ctx->e, de, e0.size() * ctx->rs, cudaMemcpyDeviceToDevice, ctx->stream));
-    CK(cudaMemsetAsync(ctx->b[0], 0, bz.size() * ctx->rs, ctx->stream));
-    CK(cudaMemsetAsync(ctx->b[1], 0, bz.size() * ctx->rs, ctx->stream));
+    // column rhs of the [N1][R] state (a strided copy for R > 1); the other columns keep their e
+    CK(cudaMemcpy2DAsync((char*)ctx->e + (size_t)rhs * ctx->rs, (size_t)ctx->n_rhs * ctx->rs, de, ctx->rs, ctx->rs,
+                         e0.size(), cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemsetAsync(ctx->b[0], 0, bz.size() * ctx->n_rhs * ctx->rs, ctx->stream));
+    CK(cudaMemsetAsync(ctx->b[1], 0, bz.size() * ctx->n_rhs * ctx->rs, ctx->stream));
+    launch_pad_e(ctx);
+    CK(cudaGetLastError());
     CK(cudaStreamSynchronize(ctx->stream));
     cudaFree(de);
     ctx->cur = 0;
@@ -1285,6 +1548,7 @@ static int set_sources(ygm_ctx* ctx, const ygm_source* src, int32_t n_src) {
     if (same) return 0;
     std::vector<DSrc> hs;
     std::vector<long long> dofs;
+    std::vector<int> pdofs;
     std::vector<double> w;
     for (int i = 0; i < n_src; ++i) {
         const ygm_source& s = src[i];
@@ -1301,6 +1565,11 @@ static int set_sources(ygm_ctx* ctx, const ygm_source* src, int32_t n_src) {
         for (size_t j = 0; j < d.size(); ++j) {
             dofs.push_back(d[j] * ctx->n_rhs + s.rhs);
             w.push_back(ww[j]);
+            int cls, v[3];
+            ctx->S.L.decode1(d[j], &cls, v);
+            const int H = ctx->pg.H, NP = ctx->pg.NP;
+            pdofs.push_back((int)((((long long)cls * NP * NP * NP + ((long long)(v[2] + H) * NP + v[1] + H) * NP + v[0] + H)
+                                   << ctx->rshift) + s.rhs));
         }
         ds.end = (int)dofs.size();
         hs.push_back(ds);
@@ -1308,11 +1577,14 @@ static int set_sources(ygm_ctx* ctx, const ygm_source* src, int32_t n_src) {
     cudaFree(ctx->dsrc);
     cudaFree(ctx->sdofs);
     cudaFree(ctx->sw);
+    cudaFree(ctx->spdofs);
+    ctx->spdofs = nullptr;
     ctx->dsrc = nullptr;
     ctx->sdofs = nullptr;
     ctx->sw = nullptr;
     int rc;
-    if ((rc = upload(ctx, &ctx->dsrc, hs)) || (rc = upload(ctx, &ctx->sdofs, dofs)) || (rc = upload_real(ctx, &ctx->sw, w)))
+    if ((rc = upload(ctx, &ctx->dsrc, hs)) || (rc = upload(ctx, &ctx->sdofs, dofs)) || (rc = upload(ctx, &ctx->spdofs, pdofs)) ||
+        (rc = upload_real(ctx, &ctx->sw, w)))
         return rc;
     ctx->nsrc = n_src;
     ctx->src_cache.assign(src, src + n_src);
@@ -1332,14 +1604,14 @@ int ygm_step(ygm_ctx* ctx, int64_t n, double dt, const ygm_source* src, int32_t 
     void* b0 = ctx->b[ctx->cur];
     if (!ctx->staggered) {
         // initial half step Phi^e_{dt/2} (Eq. YeeLeapfrog): b_{-1/2} = b_0 + dt/2 C Q1 e_0
-        launch_qapply(ctx, ctx->e, ctx->x);
+        launch_qapply(ctx, ctx->x, false);
         launch_curl_b(ctx, ctx->x, b0, b0, -0.5 * dt);
         ctx->staggered = true;
         ctx->step_base = ctx->step;
         ctx->t_base = 0.0;
     } else if (dt != ctx->dt_prev) {
         // close the old staggering and reopen it with the new step (exact Strang composition)
-        launch_qapply(ctx, ctx->e, ctx->x);
+        launch_qapply(ctx, ctx->x, false);
         launch_curl_b(ctx, ctx->x, b0, b0, 0.5 * ctx->dt_prev - 0.5 * dt);
         ctx->t_base += (double)(ctx->step - ctx->step_base) * ctx->dt_prev;
         ctx->step_base = ctx->step;
@@ -1382,10 +1654,10 @@ int ygm_step(ygm_ctx* ctx, int64_t n, double dt, const ygm_source* src, int32_t 
     for (int64_t i = 0; i < n; ++i) {
         void* bo = ctx->b[ctx->cur];
         void* bn = ctx->b[ctx->cur ^ 1];
-        launch_qapply(ctx, ctx->e, ctx->x);
+        const bool want_w = ctx->energy_every && ctx->step % ctx->energy_every == 0 && ctx->hist_n < ctx->hist_cap - 2;
+        launch_qapply(ctx, ctx->x, want_w);     // W_n needs e^T Q1 e over every row
         launch_curl_b(ctx, ctx->x, bo, bn, dt);
-        if (ctx->energy_every && ctx->step % ctx->energy_every == 0 && ctx->hist_n < ctx->hist_cap - 2)
-            launch_energy(ctx, ctx->e, ctx->x, bn, bo, ctx->hist + ctx->hist_n++);
+        if (want_w) launch_energy(ctx, ctx->e, ctx->x, bn, bo, ctx->hist + (size_t)ctx->n_rhs * ctx->hist_n++);
         launch_curlT_e(ctx, bn, ctx->e, dt);
         if (amp_dev && src_on[i]) launch_source(ctx, amp_dev + (size_t)i * ctx->nsrc);
         ctx->cur ^= 1;
@@ -1400,25 +1672,26 @@ int ygm_energy(ygm_ctx* ctx, double* W, double* Htilde) {
     if (ctx && ctx->host_only) return fail(ctx, YGM_ENODEV, "context was created host-only (device = -1)");
     if (!ctx || !W) return fail(ctx, YGM_EINVAL, "NULL argument");
     const size_t nb = ctx->S.L.N2 * ctx->n_rhs * ctx->rs;
-    double* dout = ctx->hist + ctx->hist_cap - 2;   // two scratch slots at the end of the history
+    const int R = ctx->n_rhs;
+    double* dout = ctx->hist + (size_t)(ctx->hist_cap - 2) * R;   // two scratch records at the end of the history
     void* bo = ctx->b[ctx->cur];
-    launch_qapply(ctx, ctx->e, ctx->x);
+    launch_qapply(ctx, ctx->x, true);
     if (ctx->staggered) {
         CK(cudaMemcpyAsync(ctx->bscr, bo, nb, cudaMemcpyDeviceToDevice, ctx->stream));
         launch_curl_b(ctx, ctx->x, bo, ctx->bscr, ctx->dt_prev);
         launch_energy(ctx, ctx->e, ctx->x, ctx->bscr, bo, dout);
         launch_curl_b(ctx, ctx->x, bo, ctx->bscr, 0.5 * ctx->dt_prev);
-        launch_energy(ctx, ctx->e, ctx->x, ctx->bscr, ctx->bscr, dout + 1);
+        launch_energy(ctx, ctx->e, ctx->x, ctx->bscr, ctx->bscr, dout + R);
     } else {
         // not yet staggered: b is synchronised, W is reported as H~
         launch_energy(ctx, ctx->e, ctx->x, bo, bo, dout);
-        launch_energy(ctx, ctx->e, ctx->x, bo, bo, dout + 1);
+        launch_energy(ctx, ctx->e, ctx->x, bo, bo, dout + R);
     }
-    double h[2];
-    CK(cudaMemcpyAsync(h, dout, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<double> h(2 * (size_t)R);
+    CK(cudaMemcpyAsync(h.data(), dout, 2 * (size_t)R * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    *W = h[0];
-    if (Htilde) *Htilde = h[1];
+    std::copy(h.begin(), h.begin() + R, W);
+    if (Htilde) std::copy(h.begin() + R, h.end(), Htilde);
     return YGM_OK;
 }
 
@@ -1426,7 +1699,8 @@ int ygm_energy_history(ygm_ctx* ctx, double* out, int64_t max_count, int64_t* co
     if (ctx && ctx->host_only) return fail(ctx, YGM_ENODEV, "context was created host-only (device = -1)");
     if (!ctx || !count) return fail(ctx, YGM_EINVAL, "NULL argument");
     int64_t c = std::min<int64_t>(std::min<int64_t>(ctx->hist_n, ctx->hist_cap - 2), max_count);
-    if (c > 0 && out) CK(cudaMemcpyAsync(out, ctx->hist, c * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (c > 0 && out)
+        CK(cudaMemcpyAsync(out, ctx->hist, (size_t)c * ctx->n_rhs * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     *count = c;
     return YGM_OK;
@@ -1455,8 +1729,9 @@ int ygm_set_q1(ygm_ctx* ctx, const int64_t* rowptr, const int64_t* colind, const
     if (!ctx->host_only) {
         CK(cudaStreamSynchronize(ctx->stream));
         cudaFree(ctx->q);
-        ctx->q = nullptr;
-        if ((rc = upload_real(ctx, &ctx->q, ctx->S.qvals))) return rc;
+        cudaFree(ctx->qf);
+        ctx->q = ctx->qf = nullptr;
+        if ((rc = upload_real(ctx, &ctx->q, ctx->S.qvals)) || (rc = upload_real(ctx, &ctx->qf, ctx->S.qfull))) return rc;
     }
     return YGM_OK;
 }
@@ -1469,6 +1744,7 @@ int ygm_step_noalloc(ygm_ctx* ctx, void* e, const void* b_in, void* b_out, doubl
                     "ygm_step_noalloc: N1 * n_rhs * sizeof(real) = " + std::to_string(need) +
                         " bytes exceeds the fixed 16 MiB scratch (use ygm_step)");
     if (ctx->host_only) return fail(ctx, YGM_ENODEV, "context was created host-only (device = -1)");
+    if (ctx->n_rhs != 1) return fail(ctx, YGM_EINVAL, "ygm_step_noalloc: contexts with n_rhs > 1 are not supported");
     if (!(dt > 0) || !std::isfinite(dt)) return fail(ctx, YGM_EINVAL, "need finite dt > 0");
     if (dt > ctx->S.tau_cfl * (1.0 + 1e-12))
         return fail(ctx, YGM_ECFL, "dt exceeds the CFL bound 2/omega_max (Prop. stability)");
@@ -1511,24 +1787,37 @@ int ygm_step_noalloc(ygm_ctx* ctx, void* e, const void* b_in, void* b_out, doubl
         if (ctx->neblocks) {
             if (ctx->precision == YGM_FP64)
                 k_curlT_e_b<double><<<ctx->neblocks, BLOCK, smem_e, ctx->stream>>>(
-                    ctx->c1, ctx->pbeg, (const PTerm<double>*)ctx->pterms, ctx->eblocks, mt, (const double*)b_out, (double*)e, dt);
+                    ctx->c1, ctx->pbeg, (const PTerm<double>*)ctx->pterms, ctx->eblocks, mt, (const double*)b_out, (double*)e, dt,
+                    nullptr, ctx->pg);
             else
                 k_curlT_e_b<float><<<ctx->neblocks, BLOCK, smem_e, ctx->stream>>>(
                     ctx->c1, ctx->pbeg, (const PTerm<float>*)ctx->pterms, ctx->eblocks, mt, (const float*)b_out, (float*)e,
-                    (float)dt);
+                    (float)dt, nullptr, ctx->pg);
         }
     } else {
         dim3 g((ctx->nrowsE + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
         if (ctx->precision == YGM_FP64)
             k_curlT_e<double><<<g, BLOCK, 0, ctx->stream>>>(ctx->tb, ctx->rowsE, ctx->nrowsE, (const double*)ctx->W,
-                                                            (const double*)b_out, (const double*)ctx->inv_mu, (double*)e, dt);
+                                                            (const double*)b_out, (const double*)ctx->inv_mu, (double*)e, dt,
+                                                            nullptr, ctx->pg);
         else
             k_curlT_e<float><<<g, BLOCK, 0, ctx->stream>>>(ctx->tb, ctx->rowsE, ctx->nrowsE, (const float*)ctx->W,
                                                            (const float*)b_out, (const float*)ctx->inv_mu, (float*)e,
-                                                           (float)dt);
+                                                           (float)dt, nullptr, ctx->pg);
     }
     ctx->launches += 3;
     CK(cudaGetLastError());
+    return YGM_OK;
+}
+
+int ygm_qapply_counts(const ygm_ctx* ctx, int all_rows, int64_t* rows, int64_t* unique_values,
+                      int64_t* stored_values) {
+    if (!ctx) return YGM_EINVAL;
+    if (ctx->host_only) return YGM_ENODEV;
+    const int a = all_rows ? 1 : 0;
+    if (rows) *rows = ctx->qc_rows[a];
+    if (unique_values) *unique_values = ctx->qc_unique[a];
+    if (stored_values) *stored_values = ctx->qc_stored[a];
     return YGM_OK;
 }
 
@@ -1594,7 +1883,8 @@ void ygm_destroy(ygm_ctx* ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     void* ptrs[] = {ctx->e,     ctx->b[0],  ctx->b[1], ctx->x,     ctx->bscr,  ctx->q,     ctx->W,     ctx->inv_mu,
                     ctx->sw,    ctx->M2a,   ctx->c1,   ctx->c2,    ctx->slots, ctx->terms, ctx->inc,   ctx->loc2,
-                    ctx->rowsA, ctx->rowsB, ctx->rowsE, ctx->part, ctx->hist,  ctx->dsrc,  ctx->sdofs};
+                    ctx->rowsE, ctx->part, ctx->hist,  ctx->dsrc,  ctx->sdofs, ctx->ep,   ctx->qf,    ctx->pblks,
+                    ctx->soff,  ctx->planes, ctx->spdofs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
@@ -1603,7 +1893,7 @@ void ygm_destroy(ygm_ctx* ctx) {
         if (ctx->damp[i]) cudaFree(ctx->damp[i]);
         if (ctx->hamp[i]) cudaFreeHost(ctx->hamp[i]);
     }
-    void* more[] = {ctx->qslots, ctx->qblocks, ctx->eblocks, ctx->bblocks, ctx->tilesA, ctx->tilesE, ctx->pterms, ctx->pbeg};
+    void* more[] = {ctx->qslots, ctx->qblocks, ctx->eblocks, ctx->bblocks, ctx->pterms, ctx->pbeg};
     for (void* p : more)
         if (p) cudaFree(p);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);

@@ -1,0 +1,146 @@
+"""GPU parity of the batched mode: R right-hand sides (independent excitations) in one context,
+state vectors [N][R] with R contiguous.
+
+Every column of a batched run must follow the FP64 oracle trajectory of that column's own
+initial state and source (same tolerance as the single-column path, 1e-12 relative in FP64),
+and must agree with a single-column GPU run of the same inputs."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+import synth
+from oracle_runs import oracle_model, run_oracle, rel_l2
+
+Y = pytest.importorskip("paper_2301_01753_gb300")
+
+FP64_TOL = 1e-12
+
+
+def _sources(R, tau, seed):
+    """One z-or-seeded-direction dipole per column at seeded interior points."""
+    pos = 0.2 + 0.6 * synth.uniform(seed, 3 * R).reshape(R, 3)
+    dirs = synth.unit_vectors(seed + 1, R)
+    out = []
+    for r in range(R):
+        sigma = 5.0 * tau
+        out.append(dict(x=pos[r], d=dirs[r], amp=1.0, omega=np.pi * np.sqrt(5.0), t0=4 * sigma, sigma=sigma,
+                        rhs=r))
+    return out
+
+
+def _columns(a, N, R):
+    return np.asarray(a).reshape(N, R)
+
+
+@pytest.mark.parametrize("n,k,R", [(3, 1, 4), (3, 2, 2), (2, 3, 2)])
+def test_batched_columns_follow_oracle(n, k, R):
+    f, g, eps, _ = oracle_model(n, k, eps_seed=3000)
+    tau = 0.5 * g.tau_cfl()
+    N1, N2 = f.mesh.N1, f.mesh.N2
+    rng = np.random.default_rng(7)
+    E0 = rng.standard_normal((N1, R))
+    B0 = np.zeros((N2, R))
+    srcs = _sources(R, tau, 3001)
+    steps = 40
+    c = Y.Context(n, k, eps=eps, precision=Y.YGM_FP64, n_rhs=R, energy_every=10)
+    c.set_state(np.ascontiguousarray(E0.ravel()), np.ascontiguousarray(B0.ravel()))
+    c.step(steps, tau, srcs)
+    e, b = c.get_state(synced=True)
+    W = c.energy_history().reshape(-1, R)
+    e, b = _columns(e, N1, R), _columns(b, N2, R)
+    for r in range(R):
+        s = {kk: v for kk, v in srcs[r].items() if kk != "rhs"}
+        s["width_steps"] = 5.0
+        e_or, _, bs_or, W_or = run_oracle(f, g, E0[:, r].copy(), B0[:, r].copy(), tau, steps, sources=[s],
+                                          energy_every=10)
+        assert rel_l2(e[:, r], e_or) < FP64_TOL, r
+        assert rel_l2(b[:, r], bs_or) < FP64_TOL, r
+        assert np.max(np.abs(W[:, r] - W_or)) <= 1e-12 * np.max(np.abs(W_or)), r
+    c.close()
+
+
+def test_batched_equals_single_column_runs_fp32():
+    """R = 32 columns of FP32 state, checked column by column against R = 1 runs."""
+    n, k, R = 5, 2, 32
+    eps = synth.tet_eps(3000, n, 1.0, 4.0)
+    cb = Y.Context(n, k, eps=eps, precision=Y.YGM_FP32, n_rhs=R, energy_every=5)
+    tau = 0.5 * cb.tau_cfl
+    srcs = _sources(R, tau, 3001)
+    N1, N2 = cb.N1, cb.N2
+    cb.set_state(np.zeros(N1 * R, np.float32), np.zeros(N2 * R, np.float32))
+    cb.step(60, tau, srcs)
+    e, b = cb.get_state(synced=True)
+    Wb, Hb = cb.energy()
+    Wh = cb.energy_history().reshape(-1, R)
+    e, b = _columns(e, N1, R), _columns(b, N2, R)
+    c1 = Y.Context(n, k, eps=eps, precision=Y.YGM_FP32, energy_every=5)
+    for r in (0, 1, 17, 31):
+        s = dict(srcs[r])
+        s["rhs"] = 0
+        c1.set_state(np.zeros(N1, np.float32), np.zeros(N2, np.float32))
+        c1.step(60, tau, [s])
+        e1, b1 = c1.get_state(synced=True)
+        W1, H1 = c1.energy()
+        assert rel_l2(e[:, r], e1) < 1e-6, r
+        assert rel_l2(b[:, r], b1) < 1e-6, r
+        assert abs(Wb[r] - W1[0]) <= 1e-6 * abs(W1[0]), r
+        assert abs(Hb[r] - H1[0]) <= 1e-6 * abs(H1[0]), r
+        assert np.max(np.abs(Wh[:, r] - c1.energy_history())) <= 1e-6 * np.max(np.abs(Wh[:, r])), r
+    c1.close()
+    cb.close()
+
+
+def test_batched_per_tet_mu_follows_oracle():
+    """Non-uniform permeability takes the tet-by-tet C^T M2 kernel; two columns."""
+    from oracle import spai as SP
+    from oracle.fem import FEM
+    from oracle.gym import GYM
+    from oracle.mesh import KuhnMesh
+    n, k, R = 3, 1, 2
+    eps = synth.tet_eps(3000, n, 1.0, 4.0)
+    mu = synth.tet_eps(3005, n, 1.0, 2.0)
+    f = FEM(KuhnMesh(n, k), eps=eps, mu=mu)
+    M1 = f.M1()
+    Q, _ = SP.gym_q1(f, M1)
+    g = GYM(f.C(), f.M2(), Q, M1)
+    tau = 0.5 * g.tau_cfl()
+    rng = np.random.default_rng(11)
+    E0 = rng.standard_normal((f.mesh.N1, R))
+    B0 = rng.standard_normal((f.mesh.N2, R))
+    c = Y.Context(n, k, eps=eps, mu=mu, precision=Y.YGM_FP64, n_rhs=R)
+    c.set_state(np.ascontiguousarray(E0.ravel()), np.ascontiguousarray(B0.ravel()))
+    c.step(25, tau)
+    e, b = c.get_state(synced=True)
+    e, b = _columns(e, f.mesh.N1, R), _columns(b, f.mesh.N2, R)
+    for r in range(R):
+        e_or, _, bs_or, _ = run_oracle(f, g, E0[:, r].copy(), B0[:, r].copy(), tau, 25)
+        assert rel_l2(e[:, r], e_or) < FP64_TOL
+        assert rel_l2(b[:, r], bs_or) < FP64_TOL
+    c.close()
+
+
+def test_batched_project_into_one_column():
+    n, k, R = 3, 1, 4
+    c = Y.Context(n, k, precision=Y.YGM_FP64, n_rhs=R)
+    f, _, _, _ = oracle_model(n, k)
+    from oracle_runs import te110
+    c.project_E(lambda x: te110(x)[0], rhs=2)
+    e, b = c.get_state(synced=False)
+    e = _columns(e, c.N1, R)
+    assert rel_l2(e[:, 2], f.M1() @ f.edge_interpolant(te110)) < 1e-13
+    assert not np.any(e[:, [0, 1, 3]])
+    assert not np.any(b)
+    c.close()
+
+
+def test_batched_invalid_rhs_counts():
+    for R in (3, 0, 512):
+        with pytest.raises(Y.YgmError) as ei:
+            Y.Context(2, 1, n_rhs=R)
+        assert ei.value.code == Y.YGM_EINVAL
+    c = Y.Context(2, 1, n_rhs=2)
+    with pytest.raises(Y.YgmError) as ei:
+        c.step(1, 0.5 * c.tau_cfl, [dict(x=[0.5, 0.5, 0.5], d=[0, 0, 1], omega=1.0, t0=0.0, sigma=1.0, rhs=2)])
+    assert ei.value.code == Y.YGM_EINVAL
+    c.close()
