@@ -55,6 +55,57 @@ class PeriodicCubes:
                     v += [1 / hz, -1 / hz, -1 / hx, 1 / hx]
         return sp.csr_matrix((v, (r, c)), shape=(self.N2, self.N1))
 
+    # ---- consistent (unlumped) masses of the cubical Whitney forms, by quadrature ----------
+    # In a cell with local coordinates (s, t, u) in [0,1]^3, the x-edge function of the local
+    # edge at (t, u) = (bt, bu) is hat_bt(t) hat_bu(u) e_x (hat_0 = 1 - s, hat_1 = s), and the
+    # face with normal x at s = bs is hat_bs(s) e_x: the average-normalised Whitney forms
+    # (Eq. WhitneyFormDefn).  Their L2 products, summed over cells, give M1 and M2.
+    def _mass(self, kind):
+        nx, ny, nz = self.n
+        g, w = np.polynomial.legendre.leggauss(3)
+        g, w = 0.5 * (g + 1.0), 0.5 * w                 # Gauss-Legendre on [0, 1], exact to degree 5
+        hat = lambda b, x: x if b else 1.0 - x
+        N = self.N1 if kind == 1 else self.N2
+        r, c, v = [], [], []
+        for k in range(nz):
+            for j in range(ny):
+                for i in range(nx):
+                    loc = []                            # (global index, axis, function of (x, y, z))
+                    for a in range(3):
+                        o1, o2 = (a + 1) % 3, (a + 2) % 3
+                        if kind == 1:
+                            for b1 in (0, 1):
+                                for b2 in (0, 1):
+                                    off = [0, 0, 0]
+                                    off[o1], off[o2] = b1, b2
+                                    loc.append((self.edge(a, i + off[0], j + off[1], k + off[2]), a,
+                                                (lambda p, b1=b1, b2=b2, o1=o1, o2=o2: hat(b1, p[o1]) * hat(b2, p[o2]))))
+                        else:
+                            for b0 in (0, 1):
+                                off = [0, 0, 0]
+                                off[a] = b0
+                                loc.append((self.face(a, i + off[0], j + off[1], k + off[2]), a,
+                                            (lambda p, b0=b0, a=a: hat(b0, p[a]))))
+                    for (gi, ai, fi) in loc:
+                        for (gj, aj, fj) in loc:
+                            if ai != aj:
+                                continue                # orthogonal directions
+                            val = 0.0
+                            for x, wx in zip(g, w):
+                                for y, wy in zip(g, w):
+                                    for z, wz in zip(g, w):
+                                        val += wx * wy * wz * fi((x, y, z)) * fj((x, y, z))
+                            r.append(gi)
+                            c.append(gj)
+                            v.append(val * self.dV)
+        return sp.csr_matrix((v, (r, c)), shape=(N, N))
+
+    def M1(self):
+        return self._mass(1)
+
+    def M2(self):
+        return self._mass(2)
+
 
 def yee_textbook(E, B, tau, h, nsteps):
     """Standard Yee update on a periodic grid (c = 1): B^{n+1/2} = B^{n-1/2} - tau curl E^n,

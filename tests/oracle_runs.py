@@ -37,3 +37,24 @@ def run_oracle(f, g, e0, b0, tau, nsteps, sources=(), energy_every=0):
 
 def rel_l2(a, b):
     return float(np.linalg.norm(np.asarray(a, float) - np.asarray(b, float)) / max(np.linalg.norm(b), 1e-300))
+
+
+def golden(name):
+    """Rows of a golden fixture under tests/golden/ (whitespace-separated, '#' comments)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    rows = []
+    with open(path) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                rows.append(line.split())
+    return rows
+
+
+def fraction(text):
+    """'4/9' -> 0.444..., '1' -> 1.0, '+0.145' -> 0.145."""
+    if "/" in text:
+        a, b = text.split("/")
+        return float(a) / float(b)
+    return float(text)

@@ -1,6 +1,8 @@
 """Pins of the oracle's SPAI (Sec. 5, Eq. NormalEqSolve) against brute force, closed forms and
 the frequencies printed in Table dispersionTable."""
 import numpy as np
+
+from oracle_runs import fraction, golden
 import pytest
 import scipy.sparse as sp
 
@@ -108,20 +110,29 @@ def _dispersion(kind):
     return omega_space, zero_crossing_frequency(np.array(proj), tau), t.hx
 
 
+# printed values of Table dispersionTable (tests/golden/dispersion_table.txt)
+_TABLE = {r[0]: (fraction(r[1]), fraction(r[2])) for r in golden("dispersion_table.txt")}
+
+
 def test_dispersion_exact_feec():
     w, wt, h = _dispersion("exact")
     assert np.isclose(w, np.sqrt(6 / h ** 2 * (1 - np.cos(h)) / (2 + np.cos(h))), rtol=1e-12)
-    assert abs(w / 1.0041 - 1) < 1e-4 and abs(wt / 1.0041 - 1) < 3e-4
+    w0 = _TABLE["exact_feec"][0]
+    assert abs(w / w0 - 1) < 1e-4 and abs(wt / w0 - 1) < 3e-4
 
 
 def test_dispersion_diagonal_spai_matches_yee_row():
     w, wt, h = _dispersion("diag")
     assert np.isclose(w, np.sqrt(4.0 / 3.0) * 2 / h * np.sin(h / 2), rtol=1e-12)
-    assert abs(w / 1.1499 - 1) < 1e-4 and abs(wt / 1.1499 - 1) < 3e-4
-    assert abs((w - 1.0041) / 1.0041 - 0.145) < 5e-4          # printed +14.5 %
+    w0 = _TABLE["exact_feec"][0]
+    wp, dev = _TABLE["diagonal_yee"]
+    assert abs(w / wp - 1) < 1e-4 and abs(wt / wp - 1) < 3e-4
+    assert abs((w - w0) / w0 - dev) < 5e-4
 
 
 def test_dispersion_spai_sm1_matches_printed_value():
     w, wt, h = _dispersion("sm1")
-    assert abs(wt / 0.9634 - 1) < 3e-4 and abs(w / 0.9634 - 1) < 3e-4
-    assert abs((wt - 1.0041) / 1.0041 + 0.041) < 5e-4         # printed -4.1 %
+    w0 = _TABLE["exact_feec"][0]
+    wp, dev = _TABLE["spai_sm1"]
+    assert abs(wt / wp - 1) < 3e-4 and abs(w / wp - 1) < 3e-4
+    assert abs((wt - w0) / w0 - dev) < 5e-4

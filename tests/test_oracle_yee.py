@@ -5,6 +5,7 @@ import scipy.sparse as sp
 
 from oracle.gym import GYM
 from oracle.yee3d import PeriodicCubes, yee_textbook
+from oracle_runs import fraction, golden
 
 
 def test_gym_with_lumped_cubical_whitney_is_yee():
@@ -49,3 +50,44 @@ def test_cubical_complex_identities():
                     v += [1.0 / g.h[a], -1.0 / g.h[a]]
     G = sp.csr_matrix((v, (r, c)), shape=(g.N1, g.nc))
     assert abs(C @ G).max() < 1e-12
+
+
+def test_whitney_cube_masses_match_printed_values():
+    """The oracle's consistent cubical Whitney masses, assembled by quadrature, reproduce the
+    entries printed in Sec. 4 (Eq. whitMassMatrices) and the unit row sums that motivate the
+    lumped Yee masses (tests/golden/whitney_cube_masses.txt)."""
+    ref = {(r[0], r[1]): fraction(r[2]) for r in golden("whitney_cube_masses.txt")}
+    g = PeriodicCubes()
+    nx, ny, nz = g.n
+    M1, M2 = g.M1().tocsr(), g.M2().tocsr()
+
+    def decode(idx):
+        a, cell = divmod(idx, g.nc)
+        return a, (cell % nx, (cell // nx) % ny, cell // (nx * ny))
+
+    def wrap(d, n):
+        d = d % n
+        return d - n if d > n // 2 else d
+
+    seen1, seen2 = set(), set()
+    for M, seen, kind in ((M1, seen1, "M1"), (M2, seen2, "M2")):
+        for i in range(M.shape[0]):
+            ai, pi = decode(i)
+            row = M.getrow(i)
+            assert abs(row.sum() / g.dV - ref[("rowsum", "every_row_of_M1_and_M2")]) < 1e-13
+            for j, v in zip(row.indices, row.data):
+                aj, pj = decode(j)
+                assert ai == aj                       # perpendicular functions are L2-orthogonal
+                d = [wrap(pj[t] - pi[t], g.n[t]) for t in range(3)]
+                perp = [abs(d[t]) for t in range(3) if t != ai]
+                if kind == "M1":
+                    assert d[ai] == 0
+                    rel = {0: "same_edge", 1: "parallel_edges_sharing_a_face",
+                           2: "parallel_edges_sharing_only_a_cell"}[sum(perp)]
+                    assert max(perp) <= 1
+                else:
+                    assert perp == [0, 0] and abs(d[ai]) <= 1
+                    rel = "same_face" if d[ai] == 0 else "parallel_faces_of_one_cell"
+                assert abs(v / g.dV - ref[(kind, rel)]) < 1e-13, (kind, rel, v / g.dV)
+                seen.add(rel)
+    assert len(seen1) == 3 and len(seen2) == 2
