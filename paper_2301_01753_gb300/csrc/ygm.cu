@@ -126,15 +126,24 @@ __global__ void __launch_bounds__(PBLOCK) k_qapply_p(const PBlk* __restrict__ bl
     const long long st = B.sstr;
     real acc = real(0);
     int s = 0;
-    for (; s + 4 <= B.ns; s += 4) {
-        const int4 o = *reinterpret_cast<const int4*>(&s_off[s]);
-        const real q0 = __ldg(q), q1 = __ldg(q + st), q2 = __ldg(q + 2 * st), q3 = __ldg(q + 3 * st);
-        const real v0 = __ldg(e0 + o.x), v1 = __ldg(e0 + o.y), v2 = __ldg(e0 + o.z), v3 = __ldg(e0 + o.w);
-        acc = fma(q0, v0, acc);
-        acc = fma(q1, v1, acc);
-        acc = fma(q2, v2, acc);
-        acc = fma(q3, v3, acc);
-        q += 4 * st;
+    // eight slots per round: all sixteen loads are issued before the first FMA needs one
+    for (; s + 8 <= B.ns; s += 8) {
+        const int4 oa = *reinterpret_cast<const int4*>(&s_off[s]);
+        const int4 ob = *reinterpret_cast<const int4*>(&s_off[s + 4]);
+        real qv[8], ev[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) qv[u] = __ldg(q + u * st);
+        ev[0] = __ldg(e0 + oa.x);
+        ev[1] = __ldg(e0 + oa.y);
+        ev[2] = __ldg(e0 + oa.z);
+        ev[3] = __ldg(e0 + oa.w);
+        ev[4] = __ldg(e0 + ob.x);
+        ev[5] = __ldg(e0 + ob.y);
+        ev[6] = __ldg(e0 + ob.z);
+        ev[7] = __ldg(e0 + ob.w);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc = fma(qv[u], ev[u], acc);
+        q += 8 * st;
     }
     for (; s < B.ns; ++s) {
         acc = fma(__ldg(q), __ldg(e0 + s_off[s]), acc);

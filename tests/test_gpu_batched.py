@@ -2,7 +2,8 @@
 state vectors [N][R] with R contiguous.
 
 Every column of a batched run must follow the FP64 oracle trajectory of that column's own
-initial state and source (same tolerance as the single-column path, 1e-12 relative in FP64),
+initial state and source (the single-column tolerances: 1e-12 relative in FP64, 5e-11 for the
+k = 3 pipeline),
 and must agree with a single-column GPU run of the same inputs."""
 import numpy as np
 import pytest
@@ -15,6 +16,10 @@ from oracle_runs import oracle_model, run_oracle, rel_l2
 Y = pytest.importorskip("paper_2301_01753_gb300")
 
 FP64_TOL = 1e-12
+# full pipeline (host set-up + kernels), as for a single column: the builder's FP64 SPAI agrees
+# with the oracle's to ~2e-12 at k = 3 (the normal equations square the column problem's
+# condition number), which the run carries into the trajectory
+PIPE_TOL = {1: FP64_TOL, 2: FP64_TOL, 3: 5e-11}
 
 
 def _sources(R, tau, seed):
@@ -54,9 +59,9 @@ def test_batched_columns_follow_oracle(n, k, R):
         s["width_steps"] = 5.0
         e_or, _, bs_or, W_or = run_oracle(f, g, E0[:, r].copy(), B0[:, r].copy(), tau, steps, sources=[s],
                                           energy_every=10)
-        assert rel_l2(e[:, r], e_or) < FP64_TOL, r
-        assert rel_l2(b[:, r], bs_or) < FP64_TOL, r
-        assert np.max(np.abs(W[:, r] - W_or)) <= 1e-12 * np.max(np.abs(W_or)), r
+        assert rel_l2(e[:, r], e_or) < PIPE_TOL[k], r
+        assert rel_l2(b[:, r], bs_or) < PIPE_TOL[k], r
+        assert np.max(np.abs(W[:, r] - W_or)) <= PIPE_TOL[k] * np.max(np.abs(W_or)), r
     c.close()
 
 
