@@ -14,6 +14,8 @@ The oracle is a plain, slow, obviously-correct restatement of the paper:
                canonical edge interpolation
   spai.py      column-wise SPAI on a sparsity pattern (Eq. NormalEqSolve)
                followed by symmetrisation (Sec. 5)
+  spai_op.py   operator-probed SPAI: the symmetric Sylvester system of
+               Eq. SPAIOPSylvester solved by diagonally preconditioned CG (Sec. 5.1)
   gym.py       shear maps / Strang splitting (Eqs. shearMaps, strangSplit),
                the (b, e) leapfrog (Eq. preYeeFEECEqns, Eq. YeeLeapfrog),
                energies, CFL bound (Prop. stability), dipole source

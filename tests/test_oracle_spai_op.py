@@ -1,0 +1,126 @@
+"""Pins of the SPAI-OP oracle (Sec. 5.1) against what the paper fixes.
+
+- lam = 0 is symmetry-constrained SPAI; on the structured periodic grid it coincides with the
+  post-symmetrised column-wise SPAI (Sec. 7.2), and PCG reaches machine precision in two
+  iterations there (Sec. 5.1).
+- The solution of the vectorised system is symmetric (the permutation argument of Sec. 5.1).
+- PCG agrees with a direct solve of the explicit coefficient matrix of Eq. SPAIOPcoefficient.
+- The solution is stationary for the objective of Eq. SPAIOPobjective over symmetric Q1 on S
+  (brute-force finite differences of the objective).
+- Table dispersionTable, SPAI-OP row: probing the propagated eigenmode with lam = 5e5 gives the
+  frequency 1.00412 from the zero-crossing fit, within 1e-4 of the exact FEEC run, with the
+  Frobenius fit within 8 % of SPAI (Sec. 7.6).
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import spai as SP
+from oracle import spai_op as OP
+from oracle.cubical2d import Torus2D, zero_crossing_frequency
+from oracle.fem import FEM
+from oracle.gym import GYM
+from oracle.mesh import KuhnMesh
+from oracle_runs import fraction, golden
+import synth
+
+
+def _torus(nx, ny):
+    t = Torus2D(nx, ny)
+    M1, C, M2 = t.M1(), t.C(), t.M2()
+    return t, M1, C, M2, (C.T @ M2 @ C).tocsr()
+
+
+def _mode_m1_normalised(t, M1):
+    """The lowest non-kernel eigenmode sin(y) dx of M1^-1 P2, scaled to v^T M1 v = 1 (the
+    normalisation a generalised symmetric eigensolver returns)."""
+    a = t.mode_sin_y()
+    return a / np.sqrt(a @ (M1 @ a))
+
+
+def test_lambda_zero_is_column_spai_in_two_pcg_iterations():
+    t, M1, C, M2, P2 = _torus(20, 20)
+    S = SP.pattern("sm1", M1)
+    Qc = SP.symmetrize(SP.spai_columns(M1, S))
+    Q0, info = OP.spai_op(M1, S)                 # from q = 0
+    assert info["iters"] <= 2
+    assert info["rel_residual"] < 1e-13
+    assert abs(Q0 - Qc).max() < 1e-12 * abs(Qc).max()
+
+
+def test_solution_is_symmetric_and_matches_the_explicit_system():
+    t, M1, C, M2, P2 = _torus(4, 5)
+    S = SP.pattern("sm1", M1)
+    v = _mode_m1_normalised(t, M1)
+    lam = 3e2
+    Q, info = OP.spai_op(M1, S, P2=P2, V=v, lam=lam, tol=1e-14)
+    assert abs(Q - Q.T).max() < 1e-12 * abs(Q).max()
+    # direct solve of A q = r with A built entry by entry from Eq. SPAIOPcoefficient
+    M = M1.toarray()
+    ir, ic = OP.pattern_pairs(S)
+    W = (P2 @ v).reshape(-1, 1)
+    T = np.eye(M.shape[0]) + lam * W @ W.T
+    A = OP.sylvester_matrix(ir, ic, M @ M, T)
+    r = (M @ T + T @ M)[ir, ic]
+    q = np.linalg.solve(A, r)
+    assert np.allclose(np.asarray(Q[ir, ic]).ravel(), q, rtol=1e-10, atol=1e-12 * abs(q).max())
+
+
+def _objective(M1, Q, W, lam):
+    D = M1 @ Q - np.eye(M1.shape[0])
+    return np.sum(D ** 2) + lam * np.sum((D @ W) ** 2)
+
+
+@pytest.mark.parametrize("lam", [0.0, 50.0])
+def test_stationary_over_symmetric_q_on_the_pattern(lam):
+    """Brute force on a tiny 3-D Kuhn mesh: the objective cannot be lowered by moving any
+    symmetric pair (i, j), (j, i) of S (finite differences of Eq. SPAIOPobjective)."""
+    f = FEM(KuhnMesh(2, 1), eps=synth.tet_eps(21, 2, 1, 4))
+    M1 = f.M1()
+    P2 = (f.C().T @ f.M2() @ f.C()).tocsr()
+    S = SP.pattern("sm1", M1, f.dof1)
+    rng = np.random.default_rng(3)
+    V = rng.standard_normal((M1.shape[0], 2))
+    Q, _ = OP.spai_op(M1, S, P2=P2, V=V, lam=lam, tol=1e-15)
+    M, Qd = M1.toarray(), Q.toarray()
+    W = P2 @ V if lam else np.zeros((M.shape[0], 1))
+    ir, ic = OP.pattern_pairs(S)
+    h = 1e-6 * abs(Qd).max()
+    f0 = _objective(M, Qd, W, lam)
+    for k in rng.choice(len(ir), 12, replace=False):
+        i, j = ir[k], ic[k]
+        E = np.zeros_like(Qd)
+        E[i, j] += 1.0
+        E[j, i] += 1.0 if i != j else 0.0
+        g = (_objective(M, Qd + h * E, W, lam) - _objective(M, Qd - h * E, W, lam)) / (2 * h)
+        assert abs(g) < 1e-6 * (1.0 + f0)
+
+
+def _zero_crossing(t, M1, C, M2, Q, omega):
+    g = GYM(C, M2, Q)
+    v = M1 @ t.mode_sin_y()
+    v /= np.linalg.norm(v)
+    tau = 0.3 * g.tau_cfl()
+    n = int(200 * 2 * np.pi / omega / tau)
+    e, b = v.copy(), g.half_init(v, np.zeros(t.N2), tau)
+    proj = [v @ v]
+    for _ in range(n):
+        e, b, _, _ = g.step(e, b, tau)
+        proj.append(e @ v)
+    return zero_crossing_frequency(np.array(proj), tau)
+
+
+def test_table_dispersion_spai_op_row():
+    t, M1, C, M2, P2 = _torus(20, 20)
+    S = SP.pattern("sm1", M1)
+    Qc = SP.symmetrize(SP.spai_columns(M1, S))
+    v = _mode_m1_normalised(t, M1)
+    Q, info = OP.spai_op(M1, S, P2=P2, V=v, lam=5e5, q0=Qc, tol=1e-12)
+    omega = np.sqrt(v @ (P2 @ v))               # v^T M1 v = 1
+    w_op = _zero_crossing(t, M1, C, M2, Q, omega)
+    w_ex = _zero_crossing(t, M1, C, M2, sp.csr_matrix(np.linalg.inv(M1.toarray())), omega)
+    printed = {r[0]: fraction(r[1]) for r in golden("dispersion_table.txt")}
+    assert abs(w_op - w_ex) / w_ex < 1e-4
+    assert round(w_op, 5) == printed["spai_op_sm1"]
+    assert OP.frobenius_error(M1, Q) < 1.08 * OP.frobenius_error(M1, Qc)
+    assert info["iters"] < 1000
