@@ -269,8 +269,8 @@ def run_ours(args, rank, world, local_rank):
     acc = None
     if rank == 0 and not args.no_accuracy:
         # FP64 single-column reference run(s): column 0 (and the last column when batched)
-        ref = Y.Context(W["n"], W["k"], eps=W["eps"], precision=Y.YGM_FP64, device=local_rank,
-                        energy_every=100, stream=stream.cuda_stream)
+        # same operators (copied host set-up, nothing recomputed), FP64 state and arithmetic
+        ref = ctx.like(precision=Y.YGM_FP64, n_rhs=1, energy_every=100, stream=stream.cuda_stream)
         ctx.set_state(ze, zb)
         ctx.step(W["steps"], dt, src)
         W32 = ctx.energy_history().reshape(-1, R)
@@ -328,7 +328,8 @@ def run_ours(args, rank, world, local_rank):
                              d2h_bytes_per_step=rs * (ctx.N1 + ctx.N2) * R),
                     gpu_launches=launches,
                     roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
-                                  traffic=None, kernel="k_qapply_p", bytes_per_launch=alg_bytes,
+                                  traffic=None, kernel="k_qapply_s" if R == 1 else "k_qapply_p",
+                                  bytes_per_launch=alg_bytes,
                                   launches=dict(curl_rows_only=n_act, all_rows=n_all),
                                   streamed_gbs=streamed_gbs,
                                   note="bytes: distinct Q1 values (symmetric pair once) + e + x; streamed_gbs "

@@ -98,6 +98,13 @@ typedef struct {
 int ygm_create(const ygm_mesh* mesh, int order, const double* eps, const double* mu,
                const ygm_opts* opts, ygm_ctx** out);
 
+/* A second context of the same discrete problem: the mesh, order, eps, mu and the current
+ * operators of src (its Q1 included, also one installed by ygm_set_q1 or ygm_spai_op) are
+ * copied from src's host set-up, so nothing of Sec. 5 is recomputed; precision, n_rhs,
+ * energy_every, device and stream come from opts (q1_pattern and threads are ignored).  src is
+ * only read and may be host-only.  The new state is e = 0, b = 0, t = 0.  Errors as ygm_create. */
+int ygm_create_like(const ygm_ctx* src, const ygm_opts* opts, ygm_ctx** out);
+
 /* Sizes: N1 (1-form DoFs), N2 (2-form DoFs), stored nonzeros of the symmetric Q1, and
  * tau_CFL.  Any pointer may be NULL. */
 int ygm_sizes(const ygm_ctx* ctx, int64_t* n1, int64_t* n2, int64_t* q1_nnz, double* dt_cfl);
@@ -170,6 +177,24 @@ int ygm_export_q1(const ygm_ctx* ctx, int64_t* rowptr, int64_t* colind, double* 
  * SPD check and tau_CFL are recomputed; the state is kept.  Errors: YGM_EINVAL (pattern,
  * symmetry, sizes), YGM_ENOTSPD.  Synchronises the context stream. */
 int ygm_set_q1(ygm_ctx* ctx, const int64_t* rowptr, const int64_t* colind, const double* val);
+
+/* Operator-probed SPAI, SPAI-OP (Sec. 5.1): replace Q1 by the symmetric matrix on the current
+ * Q1 pattern that minimises ||M1 Q1 - 1||_F^2 + lambda sum_k ||(M1 Q1 - 1) P2 v_k||^2
+ * (Eq. SPAIOPobjective), i.e. solves the Sylvester system of Eq. SPAIOPSylvester by preconditioned
+ * conjugate gradients with the diagonal preconditioner of Eq. diagonalPreconditioner, starting
+ * from the current Q1 (the column-wise SPAI after ygm_create).  lambda = 0 gives the
+ * symmetry-constrained SPAI.  Host FP64 set-up work; afterwards the SPD check and tau_CFL are
+ * recomputed and the device copies refreshed, the state is kept.
+ *   V        probe modes v_k (eigenmodes of M1^-1 P2 of interest), host, N1 x n_probe,
+ *            column-major (mode k at V + k * N1), copied; may be NULL when n_probe = 0
+ *   lambda   probing weight >= 0
+ *   max_iter / tol  PCG stops when ||r|| <= tol ||r_0|| (relative residual of the system)
+ *   iters, rel_residual  (may be NULL) PCG iterations run and the final relative residual
+ * Available for contexts whose Q1 is computed in the original basis (order 1; ygm_q1_info
+ * ortho = 0).  Errors: YGM_EINVAL (arguments, basis), YGM_ETIMEOUT (PCG did not converge within
+ * max_iter; Q1 unchanged), YGM_ENOTSPD.  Synchronises the context stream. */
+int ygm_spai_op(ygm_ctx* ctx, const double* V, int32_t n_probe, double lambda, int32_t max_iter, double tol,
+                int32_t* iters, double* rel_residual);
 
 /* SPD check of Q1 (Sec. 5.1, practical considerations): Lanczos estimates of the smallest and
  * largest eigenvalue before any shift, the diagonal shift applied (0 if none), lambda_max(Q1 P2),

@@ -17,8 +17,8 @@ YGM_OK, YGM_EINVAL, YGM_ECFL, YGM_ENOTSPD, YGM_ENOMEM, YGM_ECUDA, YGM_ETIMEOUT, 
 YGM_FP64, YGM_FP32 = 0, 1
 YGM_Q1_DEFAULT, YGM_Q1_DIAG, YGM_Q1_SM1, YGM_Q1_SM1SQ = 0, 1, 2, 3
 
-EXPORTED = ["ygm_create", "ygm_sizes", "ygm_set_state", "ygm_get_state", "ygm_project_E", "ygm_step", "ygm_step_noalloc",
-            "ygm_energy", "ygm_energy_history", "ygm_time", "ygm_export_q1", "ygm_set_q1", "ygm_q1_info",
+EXPORTED = ["ygm_create", "ygm_create_like", "ygm_sizes", "ygm_set_state", "ygm_get_state", "ygm_project_E", "ygm_step", "ygm_step_noalloc",
+            "ygm_energy", "ygm_energy_history", "ygm_time", "ygm_export_q1", "ygm_set_q1", "ygm_spai_op", "ygm_q1_info",
             "ygm_local_blocks", "ygm_kernel_timing", "ygm_kernel_times", "ygm_launch_count",
             "ygm_qapply_counts", "ygm_last_error", "ygm_destroy"]
 KERNEL_KINDS = ["k_qapply", "k_curl_b", "k_curlT_e", "k_source", "k_energy"]
@@ -57,6 +57,7 @@ def load_library(path=LIB_PATH):
     pI64, pD, pI32 = C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_int32)
     sig = {
         "ygm_create": (C.c_int, [C.POINTER(ygm_mesh), C.c_int, pD, pD, C.POINTER(ygm_opts), C.POINTER(P)]),
+        "ygm_create_like": (C.c_int, [P, C.POINTER(ygm_opts), C.POINTER(P)]),
         "ygm_sizes": (C.c_int, [P, pI64, pI64, pI64, pD]),
         "ygm_set_state": (C.c_int, [P, P, P, C.c_int]),
         "ygm_get_state": (C.c_int, [P, P, P, C.c_int, C.c_int]),
@@ -68,6 +69,7 @@ def load_library(path=LIB_PATH):
         "ygm_time": (C.c_int, [P, pI64, pD]),
         "ygm_export_q1": (C.c_int, [P, pI64, pI64, pD]),
         "ygm_set_q1": (C.c_int, [P, pI64, pI64, pD]),
+        "ygm_spai_op": (C.c_int, [P, pD, C.c_int32, D, C.c_int32, D, pI32, pD]),
         "ygm_q1_info": (C.c_int, [P, pD, pD, pD, pD, pI32, pI32]),
         "ygm_local_blocks": (C.c_int, [P, pI32, pI32, pD, pD]),
         "ygm_kernel_timing": (C.c_int, [P, C.c_int]),
@@ -116,9 +118,26 @@ class Context:
         rc = _lib.ygm_create(C.byref(mesh), int(order), pe, pm, C.byref(opts), C.byref(self._h))
         if rc:
             raise YgmError(rc, _lib.ygm_last_error(None).decode())
-        self.n, self.order, self.precision, self.n_rhs = n, order, precision, n_rhs
+        self.n, self.order, self.precision, self.n_rhs, self.device = n, order, precision, n_rhs, device
         self.dtype = np.float64 if precision == YGM_FP64 else np.float32
         self.N1, self.N2, self.q1_nnz, self.tau_cfl = self.sizes()
+
+    def like(self, precision=None, n_rhs=1, energy_every=0, device=None, stream=None):
+        """A second context of the same problem (ygm_create_like): same mesh, materials and
+        operators, its own precision / columns / device; no operator set-up is recomputed."""
+        new = Context.__new__(Context)
+        new._h = C.c_void_p()
+        precision = self.precision if precision is None else precision
+        dev = self.device if device is None else device
+        opts = ygm_opts(precision, 0, n_rhs, energy_every, 0, dev, C.c_void_p(stream) if stream else None)
+        rc = _lib.ygm_create_like(self._h, C.byref(opts), C.byref(new._h))
+        if rc:
+            raise YgmError(rc, _lib.ygm_last_error(None).decode())
+        new._eps, new._mu = self._eps, self._mu
+        new.n, new.order, new.precision, new.n_rhs, new.device = self.n, self.order, precision, n_rhs, dev
+        new.dtype = np.float64 if precision == YGM_FP64 else np.float32
+        new.N1, new.N2, new.q1_nnz, new.tau_cfl = new.sizes()
+        return new
 
     # ---------------------------------------------------------------- helpers
     def _check(self, rc):
@@ -231,6 +250,21 @@ class Context:
                                     ci.ctypes.data_as(C.POINTER(C.c_int64)),
                                     va.ctypes.data_as(C.POINTER(C.c_double))))
         self.N1, self.N2, self.q1_nnz, self.tau_cfl = self.sizes()
+
+    def spai_op(self, V=None, lam=0.0, max_iter=5000, tol=1e-12):
+        """Operator-probed SPAI (ygm_spai_op): V is N1 x n_probe (probe modes as columns).
+        Returns (PCG iterations, final relative residual)."""
+        if V is None:
+            Vc, npb = None, 0
+        else:
+            V = np.asarray(V, dtype=np.float64).reshape(self.N1, -1)
+            npb = V.shape[1]
+            Vc = np.ascontiguousarray(V.T)             # column-major: mode k contiguous
+        it, rr = C.c_int32(), C.c_double()
+        self._check(_lib.ygm_spai_op(self._h, None if Vc is None else Vc.ctypes.data_as(C.POINTER(C.c_double)),
+                                     npb, float(lam), int(max_iter), float(tol), C.byref(it), C.byref(rr)))
+        self.N1, self.N2, self.q1_nnz, self.tau_cfl = self.sizes()
+        return it.value, rr.value
 
     def q1_info(self):
         lmin, lmax, sh, w2 = C.c_double(), C.c_double(), C.c_double(), C.c_double()

@@ -1253,6 +1253,7 @@ int build_setup(Setup& S, int n, double side, int k, const double* eps, const do
         stage("CFL (Lanczos)");
         B.stencils(pat);
         pack_full(S, threads);
+        if (!pack_sym(S, threads)) throw std::runtime_error("internal: 1-form anchor outside the lattice");
         stage("stencils + packing");
     } catch (const std::exception& ex) {
         S.err = ex.what();
@@ -1325,6 +1326,45 @@ void pack_full(Setup& S, int threads_in) {
     }
 }
 
+// ============================================================== symmetric storage on the anchor lattice
+bool pack_sym(Setup& S, int threads_in) {
+    const int threads = default_threads(threads_in);
+    const Lattice& L = S.L;
+    const size_t nc = L.c1.size();
+    int H = 0;
+    for (const auto& st : S.st_slots)
+        for (int a = 0; a < 3; ++a) H = std::max(H, std::abs((int)st.d[a]));
+    S.qs_h = H;
+    S.qs_nx = (L.n + 7) / 8 * 8;   // rows start on 32-byte boundaries in FP32 and FP64
+    S.qs_ny = L.n;
+    S.qs_nz = L.n;
+    S.qs_vol = (int64_t)S.qs_nx * S.qs_ny * S.qs_nz;
+    S.qs_guard = (((int64_t)H * S.qs_ny + H) * S.qs_nx + H + 31) / 32 * 32;
+    for (size_t c = 0; c < nc; ++c) {
+        const Box& b = L.c1[c].box;
+        for (int a = 0; a < 3; ++a)
+            if (b.num[a] > 0 && (b.lo[a] < 0 || b.lo[a] + b.num[a] > L.n)) return false;
+    }
+    S.qs_base.assign(nc + 1, 0);
+    S.qs_base[0] = S.qs_guard;
+    for (size_t c = 0; c < nc; ++c) S.qs_base[c + 1] = S.qs_base[c] + (int64_t)S.n_upper[c] * S.qs_vol;
+    S.qsym.assign(S.qs_base[nc] + S.qs_guard, 0.0);
+    for (size_t c = 0; c < nc; ++c) {
+        const Box& b = L.c1[c].box;
+        const int nup = S.n_upper[c];
+        parallel_for(b.size, threads, [&](int64_t lo, int64_t hi, int) {
+            for (int64_t r = lo; r < hi; ++r) {
+                const int v0 = (int)(r % b.num[0]) + b.lo[0], v1 = (int)((r / b.num[0]) % b.num[1]) + b.lo[1];
+                const int v2 = (int)(r / ((int64_t)b.num[0] * b.num[1])) + b.lo[2];
+                const int64_t at = ((int64_t)v2 * S.qs_ny + v1) * S.qs_nx + v0;
+                for (int s = 0; s < nup; ++s)
+                    S.qsym[S.qs_base[c] + s * S.qs_vol + at] = S.qvals[S.qoff[c] + (int64_t)s * b.size + r];
+            }
+        });
+    }
+    return true;
+}
+
 // ============================================================== user-supplied Q1
 int install_q1(Setup& S, const int64_t* rowptr, const int64_t* colind, const double* val, int threads_in) {
     const int threads = default_threads(threads_in);
@@ -1378,7 +1418,13 @@ int install_q1(Setup& S, const int64_t* rowptr, const int64_t* colind, const dou
                 return -1;
             }
     S.Q1 = std::move(Q);
-    // repack the stencil values
+    return repack_q1(S, threads);
+}
+
+// Repack the device-facing value tables from S.Q1 and recompute the SPD check and CFL bound.
+int repack_q1(Setup& S, int threads_in) {
+    const int threads = default_threads(threads_in);
+    const Lattice& L = S.L;
     for (size_t c = 0; c < L.c1.size(); ++c) {
         const Box& b = L.c1[c].box;
         parallel_for(b.size, threads, [&](int64_t lo, int64_t hi, int) {
@@ -1396,7 +1442,159 @@ int install_q1(Setup& S, const int64_t* rowptr, const int64_t* colind, const dou
         });
     }
     pack_full(S, threads);
+    if (!pack_sym(S, threads)) {
+        S.err = "internal: 1-form anchor outside the lattice";
+        return -1;
+    }
     return refresh_spectrum(S, threads);
+}
+
+// ============================================================== SPAI-OP (Sec. 5.1)
+// Symmetric Q1 on the pattern of the current Q1 minimising Eq. SPAIOPobjective: the Sylvester
+// system (U Q1 T + T Q1 U)_ij = R_ij on the pattern (Eq. SPAIOPSylvester), U = M1^2,
+// T = 1 + lam W W^T, W = P2 V, R = M1 T + T M1 (Eq. ThatDefinition), by PCG with the diagonal
+// preconditioner of Eq. diagonalPreconditioner, warm-started from the current Q1.  Q1 and U are
+// symmetric, so on an entry (i, j):
+//   (U Q1 T + T Q1 U)_ij = G_ij + G_ji + lam sum_p (Y_ip W_jp + W_ip Y_jp),  G = U Q1, Y = U Q1 W,
+//   R_ij = 2 M1_ij + lam sum_p (Z_ip W_jp + W_ip Z_jp),                       Z = M1 W.
+int spai_op(Setup& S, const double* V, int np, double lam, int maxit, double tol, int threads_in, int* iters,
+            double* relres) {
+    const int threads = default_threads(threads_in);
+    const Lattice& L = S.L;
+    const int64_t N1 = L.N1;
+    if (S.ortho) {
+        S.err = "SPAI-OP is available for Q1 computed in the original basis (order 1)";
+        return -1;
+    }
+    if (np < 0 || (np > 0 && !V) || !(lam >= 0) || !std::isfinite(lam) || maxit < 0 || !(tol > 0)) {
+        S.err = "SPAI-OP: need n_probe >= 0 (probe modes when > 0), finite lambda >= 0, max_iter >= 0, tol > 0";
+        return -1;
+    }
+    for (int64_t i = 0; i < N1 * (int64_t)np; ++i)
+        if (!std::isfinite(V[i])) {
+            S.err = "SPAI-OP: probe modes must be finite";
+            return -1;
+        }
+    try {
+        Builder B(S, threads);
+        const Csr& P = S.Q1;
+        const int64_t nq = P.ptr[N1];
+        std::vector<double> W((size_t)N1 * np), Z((size_t)N1 * np);
+        if (np > 0) B.make_P2loc();
+        for (int p = 0; p < np; ++p) {
+            B.P2_matvec(V + (size_t)p * N1, &W[(size_t)p * N1]);
+            S.M1.matvec(&W[(size_t)p * N1], &Z[(size_t)p * N1], threads);
+        }
+        const Csr U = spgemm(S.M1, S.M1, threads);
+        std::vector<int64_t> rowof(nq), tpos(nq);
+        for (int64_t i = 0; i < N1; ++i)
+            for (int64_t k = P.ptr[i]; k < P.ptr[i + 1]; ++k) rowof[k] = i;
+        for (int64_t k = 0; k < nq; ++k) {
+            const int64_t i = rowof[k], j = P.col[k];
+            const auto b = P.col.begin() + P.ptr[j], e = P.col.begin() + P.ptr[j + 1];
+            const auto it = std::lower_bound(b, e, i);
+            if (it == e || *it != i) {
+                S.err = "SPAI-OP: the Q1 pattern is not symmetric";
+                return -1;
+            }
+            tpos[k] = it - P.col.begin();
+        }
+        std::vector<double> Ud(N1), Td(N1, 1.0);
+        for (int64_t i = 0; i < N1; ++i) {
+            Ud[i] = U.get(i, i);
+            for (int p = 0; p < np; ++p) Td[i] += lam * W[(size_t)p * N1 + i] * W[(size_t)p * N1 + i];
+        }
+        auto lowrank = [&](const std::vector<double>& Yv, int64_t i, int64_t j) {
+            double t = 0;
+            for (int p = 0; p < np; ++p)
+                t += Yv[(size_t)p * N1 + i] * W[(size_t)p * N1 + j] + W[(size_t)p * N1 + i] * Yv[(size_t)p * N1 + j];
+            return lam * t;
+        };
+        std::vector<double> r(nq), prec(nq);
+        for (int64_t k = 0; k < nq; ++k) {
+            const int64_t i = rowof[k], j = P.col[k];
+            r[k] = 2.0 * S.M1.get(i, j) + (np ? lowrank(Z, i, j) : 0.0);
+            prec[k] = Ud[i] * Td[j] + Td[i] * Ud[j];
+        }
+        // y = A x on the pattern (matrix-free)
+        std::vector<double> G(nq), QW((size_t)N1 * np), Y((size_t)N1 * np);
+        auto apply = [&](const std::vector<double>& x, std::vector<double>& y) {
+            // G = U Q (entries of the pattern only), row-parallel with a dense column -> slot map
+            parallel_for(N1, threads, [&](int64_t b, int64_t e, int) {
+                std::vector<int64_t> slot(N1, -1);
+                for (int64_t i = b; i < e; ++i) {
+                    for (int64_t k = P.ptr[i]; k < P.ptr[i + 1]; ++k) {
+                        slot[P.col[k]] = k;
+                        G[k] = 0.0;
+                    }
+                    for (int64_t a = U.ptr[i]; a < U.ptr[i + 1]; ++a) {
+                        const int64_t m = U.col[a];
+                        const double u = U.val[a];
+                        for (int64_t c = P.ptr[m]; c < P.ptr[m + 1]; ++c) {
+                            const int64_t sl = slot[P.col[c]];
+                            if (sl >= 0) G[sl] += u * x[c];
+                        }
+                    }
+                    for (int64_t k = P.ptr[i]; k < P.ptr[i + 1]; ++k) slot[P.col[k]] = -1;
+                }
+            });
+            if (np > 0) {
+                parallel_for(N1, threads, [&](int64_t b, int64_t e, int) {
+                    for (int64_t i = b; i < e; ++i)
+                        for (int p = 0; p < np; ++p) {
+                            double t = 0;
+                            for (int64_t k = P.ptr[i]; k < P.ptr[i + 1]; ++k) t += x[k] * W[(size_t)p * N1 + P.col[k]];
+                            QW[(size_t)p * N1 + i] = t;
+                        }
+                });
+                for (int p = 0; p < np; ++p) U.matvec(&QW[(size_t)p * N1], &Y[(size_t)p * N1], threads);
+            }
+            parallel_for(nq, threads, [&](int64_t b, int64_t e, int) {
+                for (int64_t k = b; k < e; ++k)
+                    y[k] = G[k] + G[tpos[k]] + (np ? lowrank(Y, rowof[k], P.col[k]) : 0.0);
+            });
+        };
+        auto dot = [&](const std::vector<double>& a, const std::vector<double>& b2) {
+            double t = 0;
+            for (int64_t k = 0; k < nq; ++k) t += a[k] * b2[k];
+            return t;
+        };
+        std::vector<double> q(P.val), res(nq), z(nq), pdir(nq), Ap(nq);
+        apply(q, Ap);
+        for (int64_t k = 0; k < nq; ++k) res[k] = r[k] - Ap[k];
+        const double r0 = std::sqrt(dot(r, r));
+        double rn = std::sqrt(dot(res, res));
+        for (int64_t k = 0; k < nq; ++k) z[k] = res[k] / prec[k];
+        pdir = z;
+        double rz = dot(res, z);
+        int it = 0;
+        while (it < maxit && rn > tol * r0) {
+            apply(pdir, Ap);
+            const double alpha = rz / dot(pdir, Ap);
+            for (int64_t k = 0; k < nq; ++k) {
+                q[k] += alpha * pdir[k];
+                res[k] -= alpha * Ap[k];
+            }
+            rn = std::sqrt(dot(res, res));
+            ++it;
+            for (int64_t k = 0; k < nq; ++k) z[k] = res[k] / prec[k];
+            const double rz2 = dot(res, z);
+            for (int64_t k = 0; k < nq; ++k) pdir[k] = z[k] + (rz2 / rz) * pdir[k];
+            rz = rz2;
+        }
+        if (iters) *iters = it;
+        if (relres) *relres = r0 > 0 ? rn / r0 : 0.0;
+        if (!(rn <= tol * r0)) {
+            S.err = "SPAI-OP: PCG did not reach the tolerance within max_iter (Q1 unchanged)";
+            return -2;
+        }
+        // the solution is symmetric up to the PCG's rounding (Sec. 5.1); store it exactly so
+        for (int64_t k = 0; k < nq; ++k) S.Q1.val[k] = 0.5 * (q[k] + q[tpos[k]]);
+    } catch (const std::exception& ex) {
+        S.err = ex.what();
+        return -3;
+    }
+    return repack_q1(S, threads);
 }
 
 // ============================================================== sources and projections

@@ -121,10 +121,20 @@ struct Setup {
     std::vector<int64_t> qf_off;                 // per class: first entry
     std::vector<int64_t> qf_plane;               // per class: padded plane length (multiple of 4)
     std::vector<double> qfull;
+    // upper-triangle storage on the common anchor lattice for the plane-sweep Q1 apply: every
+    // class and upper slot owns an NZ x NY x NX box indexed by the row's absolute anchor
+    // (qsym[qs_base[c] + s * qs_vol + (vz * NY + vy) * NX + vx]), zero where no row exists, with a
+    // zeroed guard of qs_guard entries at both ends so every stencil neighbour address is in range
+    int qs_nx = 0, qs_ny = 0, qs_nz = 0, qs_h = 0;
+    int64_t qs_vol = 0, qs_guard = 0;
+    std::vector<int64_t> qs_base;                // per class (size C1 + 1; the last is the end of the data)
+    std::vector<double> qsym;
 };
 
 // Fill qfull from Q1 and the stencil tables (called by build_setup and install_q1).
 void pack_full(Setup& S, int threads);
+// Fill qsym from qvals (called after pack_full).  Returns false if an anchor lies outside [0, n).
+bool pack_sym(Setup& S, int threads);
 
 int build_setup(Setup& S, int n, double side, int k, const double* eps, const double* mu,
                 int q1_pattern, int threads);
@@ -133,6 +143,13 @@ int build_setup(Setup& S, int n, double side, int k, const double* eps, const do
 // device-facing values and recompute the SPD check and the CFL bound.
 int install_q1(Setup& S, const int64_t* rowptr, const int64_t* colind, const double* val, int threads);
 int refresh_spectrum(Setup& S, int threads);
+// Repack qvals / qfull / qsym from S.Q1 and refresh the SPD check and CFL bound.
+int repack_q1(Setup& S, int threads);
+// Operator-probed SPAI (Sec. 5.1) on the pattern of the current Q1, warm-started from it.
+// V: N1 x np probe modes (column-major).  Returns 0, -1 (bad input), -2 (PCG not converged,
+// Q1 unchanged), -3 (not SPD after the update).
+int spai_op(Setup& S, const double* V, int np, double lam, int maxit, double tol, int threads, int* iters,
+            double* relres);
 
 // Source vector of one dipole: tet index and the n1 weights d . Lambda1_i(x0) (global DoFs).
 int dipole_weights(const Setup& S, const double x[3], const double d[3], std::vector<int64_t>& dofs,

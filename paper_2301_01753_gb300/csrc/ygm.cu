@@ -152,6 +152,160 @@ __global__ void __launch_bounds__(PBLOCK) k_qapply_p(const PBlk* __restrict__ bl
     x[((B.x0 + row) << rshift) + col] = acc;
 }
 
+// ------------------------------------------------------------------ x = Q1 e, upper triangle, plane sweep
+// Q1 stored once per symmetric pair: row (c, v) keeps its upper slots (neighbours at or after
+// itself in (dz, dy, dx, class) order) in qs[c][slot][vz][vy][vx] on the common anchor lattice;
+// its lower slots are the neighbours' upper slots, i.e. the same array at a constant offset
+// from the row.  Every slot is therefore one 32-bit element offset for Q1 and one for the padded
+// e, and the loop body is two loads and one FMA.  Lower slots point to rows at dz <= 0, and the
+// blocks are ordered by z-plane, so those values were streamed from HBM by the blocks of the
+// previous planes moments before and are read again from L2: each distinct value crosses the
+// HBM interface about once.  Lattice points outside the row's box (PEC-removed rows, and the
+// wrap-around of neighbour offsets) hold finite values that multiply a zero of the padded e.
+constexpr int SBLOCK = 256;
+struct SBlk {            // up to SBLOCK consecutive lattice points (vy * NX + vx) of one (class, z-plane)
+    long long q0;        // qs index of the plane's first lattice point (class base + vz * NY * NX)
+    int cls;
+    int vz;
+    int t0;              // first lattice point of the block inside the plane
+    int cnt;
+};
+struct SymGeo {
+    int NX;              // lattice row length (multiple of 8)
+    int H, NP;           // padded e geometry
+};
+template <typename real>
+__global__ void __launch_bounds__(SBLOCK) k_qapply_s(const SBlk* __restrict__ blks, const DCls* __restrict__ c1,
+                                                     const int2* __restrict__ soff2, SymGeo g,
+                                                     const real* __restrict__ qs, const real* __restrict__ ep,
+                                                     real* __restrict__ x, real* __restrict__ xp) {
+    extern __shared__ __align__(16) int2 s_o2[];
+    const SBlk B = blks[blockIdx.x];
+    const DCls C = c1[B.cls];
+    const int ns = C.st_end - C.st_begin;
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) s_o2[s] = soff2[C.st_begin + s];
+    __syncthreads();
+    if ((int)threadIdx.x >= B.cnt) return;
+    const int t = B.t0 + (int)threadIdx.x;
+    const int vy = t / g.NX, vx = t - vy * g.NX;
+    const int rx = vx - C.lo[0], ry = vy - C.lo[1];
+    if ((unsigned)rx >= (unsigned)C.num[0] || (unsigned)ry >= (unsigned)C.num[1]) return;
+    const real* __restrict__ q = qs + (B.q0 + t);
+    const int pe = C.pbase + ((B.vz + g.H) * g.NP + (vy + g.H)) * g.NP + vx + g.H;
+    const real* __restrict__ e0 = ep + pe;
+    real acc = real(0);
+    int s = 0;
+    for (; s + 8 <= ns; s += 8) {
+        const int4 o0 = *reinterpret_cast<const int4*>(&s_o2[s]);
+        const int4 o1 = *reinterpret_cast<const int4*>(&s_o2[s + 2]);
+        const int4 o2 = *reinterpret_cast<const int4*>(&s_o2[s + 4]);
+        const int4 o3 = *reinterpret_cast<const int4*>(&s_o2[s + 6]);
+        real qv[8], ev[8];
+        qv[0] = __ldg(q + o0.x);
+        qv[1] = __ldg(q + o0.z);
+        qv[2] = __ldg(q + o1.x);
+        qv[3] = __ldg(q + o1.z);
+        qv[4] = __ldg(q + o2.x);
+        qv[5] = __ldg(q + o2.z);
+        qv[6] = __ldg(q + o3.x);
+        qv[7] = __ldg(q + o3.z);
+        ev[0] = __ldg(e0 + o0.y);
+        ev[1] = __ldg(e0 + o0.w);
+        ev[2] = __ldg(e0 + o1.y);
+        ev[3] = __ldg(e0 + o1.w);
+        ev[4] = __ldg(e0 + o2.y);
+        ev[5] = __ldg(e0 + o2.w);
+        ev[6] = __ldg(e0 + o3.y);
+        ev[7] = __ldg(e0 + o3.w);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc = fma(qv[u], ev[u], acc);
+    }
+    for (; s < ns; ++s) {
+        const int2 o = s_o2[s];
+        acc = fma(__ldg(q + o.x), __ldg(e0 + o.y), acc);
+    }
+    x[C.off + ((long long)(B.vz - C.lo[2]) * C.num[1] + ry) * C.num[0] + rx] = acc;
+    xp[pe] = acc;
+}
+
+// ------------------------------------------------------------------ curls on the padded lattice, one column
+// Same blocks as k_qapply_s (SBLOCK lattice points of one class and z-plane).  x and b keep
+// zero-halo padded copies in the geometry of the padded e, so every curl term is a constant
+// 32-bit offset from the row's padded index and the loops carry no range checks.  The terms
+// are summed in the order of the range-checked kernels, so both give identical results.
+struct CTermL {          // one entry of an integer curl row: sign * xp[row + off]
+    int off;
+    int sign;
+};
+template <typename real>
+struct WTermL {          // one merged C^T M2 weight: w * bp[row + off]
+    int off;
+    real w;
+};
+__device__ __forceinline__ int pad_row(PadGeo g, int vx, int vy, int vz) {
+    return ((vz + g.H) * g.NP + (vy + g.H)) * g.NP + vx + g.H;
+}
+// b_out = b_in - ctau C x; also bp <- b_out
+template <typename real>
+__global__ void __launch_bounds__(SBLOCK) k_curl_b_s(const SBlk* __restrict__ blks, const DCls* __restrict__ c2,
+                                                     const CTermL* __restrict__ terms, PadGeo g, int NX,
+                                                     const real* __restrict__ xp, const real* b_in, real* b_out,
+                                                     real* __restrict__ bp, real ctau) {
+    const SBlk B = blks[blockIdx.x];
+    const DCls C = c2[B.cls];
+    if ((int)threadIdx.x >= B.cnt) return;
+    const int t = B.t0 + (int)threadIdx.x;
+    const int vy = t / NX, vx = t - vy * NX;
+    const int rx = vx - C.lo[0], ry = vy - C.lo[1];
+    if ((unsigned)rx >= (unsigned)C.num[0] || (unsigned)ry >= (unsigned)C.num[1]) return;
+    const int p = pad_row(g, vx, vy, B.vz);
+    real acc = real(0);
+    for (int s = C.st_begin; s < C.st_end; ++s) {
+        const CTermL T = terms[s];
+        const real xv = __ldg(xp + p + T.off);
+        acc += T.sign > 0 ? xv : -xv;
+    }
+    const long long gi = C.off + ((long long)(B.vz - C.lo[2]) * C.num[1] + ry) * C.num[0] + rx;
+    const real v = b_in[gi] - ctau * acc;
+    b_out[gi] = v;
+    bp[C.pbase + p] = v;
+}
+// e += ctau C^T M2 b (uniform mu), from the padded b; also ep <- e
+template <typename real>
+__global__ void __launch_bounds__(SBLOCK) k_curlT_e_s(const SBlk* __restrict__ blks, const DCls* __restrict__ c1,
+                                                      const int* __restrict__ pbeg, const WTermL<real>* __restrict__ terms,
+                                                      PadGeo g, int NX, const real* __restrict__ bp, real* __restrict__ e,
+                                                      real ctau, real* __restrict__ ep) {
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    WTermL<real>* s_t = reinterpret_cast<WTermL<real>*>(s_raw);
+    const SBlk B = blks[blockIdx.x];
+    const DCls C = c1[B.cls];
+    const int tb = pbeg[B.cls], nt = pbeg[B.cls + 1] - tb;
+    for (int s = threadIdx.x; s < nt; s += blockDim.x) s_t[s] = terms[tb + s];
+    __syncthreads();
+    if ((int)threadIdx.x >= B.cnt) return;
+    const int t = B.t0 + (int)threadIdx.x;
+    const int vy = t / NX, vx = t - vy * NX;
+    const int rx = vx - C.lo[0], ry = vy - C.lo[1];
+    if ((unsigned)rx >= (unsigned)C.num[0] || (unsigned)ry >= (unsigned)C.num[1]) return;
+    const int p = pad_row(g, vx, vy, B.vz);
+    const real* __restrict__ b0 = bp + p;
+    real acc = real(0);
+    int s = 0;
+    for (; s + 8 <= nt; s += 8) {
+        real bv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) bv[u] = __ldg(b0 + s_t[s + u].off);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc = fma(s_t[s + u].w, bv[u], acc);
+    }
+    for (; s < nt; ++s) acc = fma(s_t[s].w, __ldg(b0 + s_t[s].off), acc);
+    const long long gi = C.off + ((long long)(B.vz - C.lo[2]) * C.num[1] + ry) * C.num[0] + rx;
+    const real v = e[gi] + ctau * acc;
+    e[gi] = v;
+    ep[C.pbase + p] = v;
+}
+
 // ep (padded) <- e (compact), one block per (class, z-plane)
 template <typename real>
 __global__ void k_pad_e(const DCls* __restrict__ c1, const int2* __restrict__ planes, PadGeo g, int rshift,
@@ -810,6 +964,18 @@ struct ygm_ctx {
     PadGeo pg{0, 0};
     long long n1pad = 0;
     int* spdofs = nullptr;                   // padded indices of the source DoFs
+    // upper-triangle Q1 on the anchor lattice (k_qapply_s, one column)
+    bool use_sym = false;
+    void* qsd = nullptr;
+    int2* soff2 = nullptr;
+    SBlk* sblks = nullptr;                   // [curl-carrying classes, z-plane order][all classes, z-plane order]
+    int nsblks_act = 0, nsblks_all = 0;
+    SymGeo sg{0, 0, 0};
+    // padded x and b with the lattice curl kernels (one column, with k_qapply_s)
+    void *xp = nullptr, *bp = nullptr, *wterms = nullptr;
+    CTermL* cterms = nullptr;
+    SBlk *lblks_b = nullptr, *lblks_e = nullptr;
+    int nlb = 0, nle = 0;
     int64_t qc_rows[2] = {0, 0}, qc_unique[2] = {0, 0}, qc_stored[2] = {0, 0};   // [active only, all rows]
     void* pterms = nullptr;                  // PTerm<real> merged C^T M2 stencil (uniform mu)
     int* pbeg = nullptr;
@@ -917,18 +1083,61 @@ static std::vector<DRow> make_rows(const std::vector<ygm::DofClass>& cls, int n,
     return rows;
 }
 
+// k_qapply_s tables (one column only): (Q1, padded e) offsets per stencil slot and the z-plane
+// ordered block lists -- curl-carrying classes only, then every class.  Skipped (the full-row
+// kernel is used) when the lattice offsets do not fit 32 bits.
+static int setup_sym(ygm_ctx* ctx, const std::vector<int>& eoff) {
+    ygm::Setup& S = ctx->S;
+    ygm::Lattice& L = S.L;
+    ctx->use_sym = false;
+    if (ctx->n_rhs != 1 || S.qsym.empty() || (size_t)(ctx->max_ns + 8) * sizeof(int2) > 48 * 1024) return 0;
+    const int NX = S.qs_nx, NY = S.qs_ny;
+    std::vector<int2> o2(S.st_slots.size());
+    for (size_t c = 0; c < L.c1.size(); ++c)
+        for (int sidx = S.st_begin[c]; sidx < S.st_begin[c + 1]; ++sidx) {
+            const auto& st = S.st_slots[sidx];
+            long long qo = st.upper ? (long long)st.slot * S.qs_vol
+                                    : S.qs_base[st.cls] - S.qs_base[c] + (long long)st.slot * S.qs_vol +
+                                          ((long long)st.d[2] * NY + st.d[1]) * NX + st.d[0];
+            if (qo > INT32_MAX || qo < INT32_MIN) return 0;
+            o2[sidx] = make_int2((int)qo, eoff[sidx]);
+        }
+    std::vector<SBlk> sb;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int vz = 0; vz < L.n; ++vz)
+            for (int c = 0; c < (int)L.c1.size(); ++c) {
+                const auto& b = L.c1[c].box;
+                if (pass == 0 && !L.c1[c].active) continue;
+                if (vz < b.lo[2] || vz >= b.lo[2] + b.num[2] || b.num[0] == 0 || b.num[1] == 0) continue;
+                const long long q0 = S.qs_base[c] + (long long)vz * NY * NX;
+                const int t1 = (b.lo[1] + b.num[1]) * NX;
+                for (int t0 = b.lo[1] * NX; t0 < t1; t0 += SBLOCK)
+                    sb.push_back(SBlk{q0, c, vz, t0, std::min(SBLOCK, t1 - t0)});
+            }
+        if (pass == 0) ctx->nsblks_act = (int)sb.size();
+    }
+    ctx->nsblks_all = (int)sb.size() - ctx->nsblks_act;
+    int rc;
+    if ((rc = upload(ctx, &ctx->soff2, o2)) || (rc = upload(ctx, &ctx->sblks, sb)) || (rc = upload_real(ctx, &ctx->qsd, S.qsym)))
+        return rc;
+    ctx->sg = SymGeo{NX, ctx->pg.H, ctx->pg.NP};
+    ctx->use_sym = true;
+    return 0;
+}
+
 static int setup_device(ygm_ctx* ctx) {
     ygm::Setup& S = ctx->S;
     ygm::Lattice& L = S.L;
     const int k = L.k;
-    // padded copy of e: halo H = the widest Q1 stencil offset
-    int H = 0;
+    // padded copies of e (and, for one column, of x and b): halo H = the widest Q1 stencil
+    // offset, at least 1 so the curl stencils (offsets within +-1 per axis) fit as well
+    int H = 1;
     for (const auto& st : S.st_slots)
         for (int a = 0; a < 3; ++a) H = std::max(H, std::abs((int)st.d[a]));
     const int NP = L.n + 2 * H + 1;
     const long long np3 = (long long)NP * NP * NP;
-    if (np3 * (long long)L.c1.size() * ctx->n_rhs > (long long)INT32_MAX)
-        return fail(ctx, YGM_EINVAL, "mesh x n_rhs too large for 32-bit indices of the padded e copy");
+    if (np3 * (long long)std::max(L.c1.size(), L.c2.size()) * ctx->n_rhs > (long long)INT32_MAX)
+        return fail(ctx, YGM_EINVAL, "mesh x n_rhs too large for 32-bit indices of the padded state copies");
     ctx->pg = PadGeo{H, NP};
     ctx->n1pad = np3 * (long long)L.c1.size();
     // classes
@@ -969,7 +1178,8 @@ static int setup_device(ygm_ctx* ctx) {
         D.size = L.c2[c].box.size;
         D.qoff = 0;
         D.inc_begin = D.inc_end = 0;
-        D.pbase = D.pad_ = 0;
+        D.pbase = (int)(c * np3);
+        D.pad_ = 0;
         D.st_begin = (int)terms.size();
         if (L.c2[c].active) {
             // find a tet shape and local index carrying this class
@@ -1000,6 +1210,17 @@ static int setup_device(ygm_ctx* ctx) {
     if ((rc = upload(ctx, &ctx->c1, c1)) || (rc = upload(ctx, &ctx->c2, c2)) || (rc = upload(ctx, &ctx->slots, slots)) ||
         (rc = upload(ctx, &ctx->terms, terms)) || (rc = upload(ctx, &ctx->inc, inc)) || (rc = upload(ctx, &ctx->loc2, loc2)))
         return rc;
+    if (ctx->n_rhs == 1) {
+        // the same curl rows as offsets in the padded geometry (k_curl_b_s)
+        std::vector<CTermL> ct(terms.size());
+        for (size_t i = 0; i < terms.size(); ++i)
+            for (int a = 0; a < 3; ++a)
+                if (std::abs(terms[i].d[a]) > H) return fail(ctx, YGM_EINVAL, "internal: curl term beyond the padded halo");
+        for (size_t i = 0; i < terms.size(); ++i)
+            ct[i] = CTermL{(int)(terms[i].cls * np3 + ((long long)terms[i].d[2] * NP + terms[i].d[1]) * NP + terms[i].d[0]),
+                           terms[i].sign};
+        if ((rc = upload(ctx, &ctx->cterms, ct))) return rc;
+    }
     // rows
     std::vector<DRow> rE = make_rows(L.c1, L.n, true);
     ctx->nrowsE = (int)rE.size();
@@ -1097,6 +1318,7 @@ static int setup_device(ygm_ctx* ctx) {
             (rc = upload(ctx, &ctx->planes, planes)) || (rc = upload_real(ctx, &ctx->qf, S.qfull)))
             return rc;
         for (size_t c = 0; c < L.c1.size(); ++c) ctx->max_ns = std::max(ctx->max_ns, S.st_begin[c + 1] - S.st_begin[c]);
+        if ((rc = setup_sym(ctx, so))) return rc;
         // roofline counts of the two launch kinds
         std::vector<char> act(L.N1, 0);
         for (size_t c = 0; c < L.c1.size(); ++c) {
@@ -1189,6 +1411,50 @@ static int setup_device(ygm_ctx* ctx) {
         }
         if ((rc = upload(ctx, &ctx->pbeg, pbeg))) return rc;
         for (size_t c = 0; c < L.c1.size(); ++c) ctx->max_terms = std::max(ctx->max_terms, pbeg[c + 1] - pbeg[c]);
+        if (ctx->n_rhs == 1) {
+            // the same weights as offsets into the padded b (k_curlT_e_s)
+            auto wfill = [&](auto* dummy) {
+                using R = std::remove_pointer_t<decltype(dummy)>;
+                std::vector<WTermL<R>> wt(all.size());
+                for (size_t i = 0; i < all.size(); ++i) {
+                    const auto& nb = all[i].first;
+                    for (int a = 0; a < 3; ++a)
+                        if (std::abs(nb.d[a]) > H) return fail(ctx, YGM_EINVAL, "internal: C^T M2 term beyond the padded halo");
+                    wt[i] = WTermL<R>{(int)(nb.cls * np3 + ((long long)nb.d[2] * NP + nb.d[1]) * NP + nb.d[0]), (R)all[i].second};
+                }
+                WTermL<R>* d = nullptr;
+                int r2 = upload(ctx, &d, wt);
+                ctx->wterms = d;
+                return r2;
+            };
+            if ((rc = ctx->precision == YGM_FP64 ? wfill((double*)nullptr) : wfill((float*)nullptr))) return rc;
+        }
+    }
+    // lattice block lists of the padded curl kernels (one column, with k_qapply_s)
+    if (ctx->use_sym) {
+        const int NX = ctx->sg.NX;
+        auto blocks_of = [&](const std::vector<ygm::DofClass>& cls) {
+            std::vector<SBlk> out;
+            for (int vz = 0; vz < L.n; ++vz)
+                for (int c = 0; c < (int)cls.size(); ++c) {
+                    const auto& b = cls[c].box;
+                    if (!cls[c].active) continue;
+                    if (vz < b.lo[2] || vz >= b.lo[2] + b.num[2] || b.num[0] == 0 || b.num[1] == 0) continue;
+                    const int t1 = (b.lo[1] + b.num[1]) * NX;
+                    for (int t0 = b.lo[1] * NX; t0 < t1; t0 += SBLOCK)
+                        out.push_back(SBlk{0, c, vz, t0, std::min(SBLOCK, t1 - t0)});
+                }
+            return out;
+        };
+        std::vector<SBlk> lb = blocks_of(L.c2), le = blocks_of(L.c1);
+        ctx->nlb = (int)lb.size();
+        ctx->nle = (int)le.size();
+        if ((rc = upload(ctx, &ctx->lblks_b, lb)) || (rc = upload(ctx, &ctx->lblks_e, le))) return rc;
+        const size_t n2pad = (size_t)np3 * L.c2.size();
+        CK(cudaMalloc(&ctx->xp, (size_t)ctx->n1pad * ctx->rs));
+        CK(cudaMalloc(&ctx->bp, n2pad * ctx->rs));
+        CK(cudaMemsetAsync(ctx->xp, 0, (size_t)ctx->n1pad * ctx->rs, ctx->stream));
+        CK(cudaMemsetAsync(ctx->bp, 0, n2pad * ctx->rs, ctx->stream));
     }
     for (int i = 0; i < 2; ++i) CK(cudaEventCreateWithFlags(&ctx->damp_ev[i], cudaEventDisableTiming));
     // dynamic shared memory of the block kernels (slot / term tables of one class); above 48 KB
@@ -1229,6 +1495,22 @@ static int setup_device(ygm_ctx* ctx) {
 // x = Q1 e of the context state, read from the padded copy of e; all_rows = false computes only
 // the rows of the curl-carrying 1-forms (all that C x needs)
 static int launch_qapply(ygm_ctx* ctx, void* x, bool all_rows) {
+    if (ctx->use_sym) {
+        const int nb = all_rows ? ctx->nsblks_all : ctx->nsblks_act;
+        if (!nb) return 0;
+        const SBlk* blks = ctx->sblks + (all_rows ? ctx->nsblks_act : 0);
+        time_begin(ctx, KQ);
+        const size_t smem = (size_t)(ctx->max_ns + 8) * sizeof(int2);
+        if (ctx->precision == YGM_FP64)
+            k_qapply_s<double><<<nb, SBLOCK, smem, ctx->stream>>>(blks, ctx->c1, ctx->soff2, ctx->sg, (const double*)ctx->qsd,
+                                                                  (const double*)ctx->ep, (double*)x, (double*)ctx->xp);
+        else
+            k_qapply_s<float><<<nb, SBLOCK, smem, ctx->stream>>>(blks, ctx->c1, ctx->soff2, ctx->sg, (const float*)ctx->qsd,
+                                                                 (const float*)ctx->ep, (float*)x, (float*)ctx->xp);
+        time_end(ctx);
+        ctx->launches++;
+        return 0;
+    }
     const int nb = all_rows ? ctx->npblks : ctx->npblks_act;
     if (!nb) return 0;
     time_begin(ctx, KQ);
@@ -1246,7 +1528,16 @@ static int launch_qapply(ygm_ctx* ctx, void* x, bool all_rows) {
 static int launch_curl_b(ygm_ctx* ctx, const void* x, const void* bin, void* bout, double ctau) {
     if (!ctx->nbblocks) return 0;
     time_begin(ctx, KB);
-    if (ctx->rshift) {
+    if (ctx->use_sym && ctx->nlb) {      // x was written to its padded copy by k_qapply_s
+        if (ctx->precision == YGM_FP64)
+            k_curl_b_s<double><<<ctx->nlb, SBLOCK, 0, ctx->stream>>>(ctx->lblks_b, ctx->c2, ctx->cterms, ctx->pg, ctx->sg.NX,
+                                                                     (const double*)ctx->xp, (const double*)bin, (double*)bout,
+                                                                     (double*)ctx->bp, ctau);
+        else
+            k_curl_b_s<float><<<ctx->nlb, SBLOCK, 0, ctx->stream>>>(ctx->lblks_b, ctx->c2, ctx->cterms, ctx->pg, ctx->sg.NX,
+                                                                    (const float*)ctx->xp, (const float*)bin, (float*)bout,
+                                                                    (float*)ctx->bp, (float)ctau);
+    } else if (ctx->rshift) {
         if (ctx->precision == YGM_FP64)
             k_curl_b_r<double><<<ctx->nbblocks, BLOCK, 0, ctx->stream>>>(ctx->c1, ctx->c2, ctx->terms, ctx->bblocks, ctx->rshift,
                                                                          (const double*)x, (const double*)bin, (double*)bout, ctau);
@@ -1267,7 +1558,17 @@ static int launch_curl_b(ygm_ctx* ctx, const void* x, const void* bin, void* bou
 }
 static int launch_curlT_e(ygm_ctx* ctx, const void* b, void* e, double ctau) {
     time_begin(ctx, KE);
-    if (ctx->rshift) {
+    if (ctx->use_sym && ctx->nlb && ctx->wterms && ctx->nle) {   // b was written to its padded copy by k_curl_b_s
+        const size_t smem = (size_t)ctx->max_terms * (ctx->precision == YGM_FP64 ? sizeof(WTermL<double>) : sizeof(WTermL<float>));
+        if (ctx->precision == YGM_FP64)
+            k_curlT_e_s<double><<<ctx->nle, SBLOCK, smem, ctx->stream>>>(ctx->lblks_e, ctx->c1, ctx->pbeg,
+                                                                        (const WTermL<double>*)ctx->wterms, ctx->pg, ctx->sg.NX,
+                                                                        (const double*)ctx->bp, (double*)e, ctau, (double*)ctx->ep);
+        else
+            k_curlT_e_s<float><<<ctx->nle, SBLOCK, smem, ctx->stream>>>(ctx->lblks_e, ctx->c1, ctx->pbeg,
+                                                                       (const WTermL<float>*)ctx->wterms, ctx->pg, ctx->sg.NX,
+                                                                       (const float*)ctx->bp, (float*)e, (float)ctau, (float*)ctx->ep);
+    } else if (ctx->rshift) {
         if (!ctx->neblocks) {
         } else if (ctx->pterms) {
             const size_t smem = (size_t)ctx->max_terms * (ctx->precision == YGM_FP64 ? sizeof(PTerm<double>) : sizeof(PTerm<float>));
@@ -1400,6 +1701,8 @@ const char* ygm_last_error(const ygm_ctx* ctx) {
     return g_create_err.c_str();
 }
 
+static int finish_create(ygm_ctx* ctx, const ygm_opts& o, ygm_ctx** out);
+
 int ygm_create(const ygm_mesh* mesh, int order, const double* eps, const double* mu, const ygm_opts* opts,
                ygm_ctx** out) {
     auto cerr = [](int code, const std::string& m) {
@@ -1429,23 +1732,35 @@ int ygm_create(const ygm_mesh* mesh, int order, const double* eps, const double*
     }
     ygm_ctx* ctx = new (std::nothrow) ygm_ctx();
     if (!ctx) return cerr(YGM_ENOMEM, "host allocation failed");
+    int rc = ygm::build_setup(ctx->S, mesh->n, mesh->side, order, eps, mu, o.q1_pattern, o.threads);
+    if (rc) {
+        std::string m = ctx->S.err;
+        delete ctx;
+        return cerr(rc == -1 ? YGM_EINVAL : YGM_ENOTSPD, m);
+    }
+    return finish_create(ctx, o, out);
+}
+
+// Second half of context creation: the options, the stream and the device copies of an
+// already built host set-up (ctx->S).  Takes ownership of ctx.
+static int finish_create(ygm_ctx* ctx, const ygm_opts& o, ygm_ctx** out) {
     ctx->precision = o.precision;
     ctx->rs = o.precision == YGM_FP64 ? 8 : 4;
     ctx->n_rhs = o.n_rhs;
+    ctx->rshift = 0;
     while ((1 << ctx->rshift) < o.n_rhs) ++ctx->rshift;
     ctx->energy_every = o.energy_every;
     ctx->device = o.device;
-    ctx->host_only = host_only;
-    if (host_only) {
-        int rc = ygm::build_setup(ctx->S, mesh->n, mesh->side, order, eps, mu, o.q1_pattern, o.threads);
-        if (rc) {
-            std::string m = ctx->S.err;
-            delete ctx;
-            return cerr(rc == -1 ? YGM_EINVAL : YGM_ENOTSPD, m);
-        }
+    ctx->host_only = o.device == -1;
+    if (ctx->host_only) {
         *out = ctx;
         return YGM_OK;
     }
+    auto cerr = [&](int code, const std::string& m) {
+        std::lock_guard<std::mutex> lk(g_err_mutex);
+        g_create_err = m;
+        return code;
+    };
     if (cudaSetDevice(o.device) != cudaSuccess) {
         delete ctx;
         return cerr(YGM_ECUDA, "cudaSetDevice failed");
@@ -1459,13 +1774,7 @@ int ygm_create(const ygm_mesh* mesh, int order, const double* eps, const double*
         }
         ctx->own_stream = true;
     }
-    int rc = ygm::build_setup(ctx->S, mesh->n, mesh->side, order, eps, mu, o.q1_pattern, o.threads);
-    if (rc) {
-        std::string m = ctx->S.err;
-        ygm_destroy(ctx);
-        return cerr(rc == -1 ? YGM_EINVAL : YGM_ENOTSPD, m);
-    }
-    rc = setup_device(ctx);
+    int rc = setup_device(ctx);
     if (rc) {
         std::string m = ctx->err;
         ygm_destroy(ctx);
@@ -1473,6 +1782,39 @@ int ygm_create(const ygm_mesh* mesh, int order, const double* eps, const double*
     }
     *out = ctx;
     return YGM_OK;
+}
+
+int ygm_create_like(const ygm_ctx* src, const ygm_opts* opts, ygm_ctx** out) {
+    auto cerr = [](int code, const std::string& m) {
+        std::lock_guard<std::mutex> lk(g_err_mutex);
+        g_create_err = m;
+        return code;
+    };
+    if (!out) return cerr(YGM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!src) return cerr(YGM_EINVAL, "src is NULL");
+    ygm_opts o{};
+    o.precision = YGM_FP64;
+    o.n_rhs = 1;
+    if (opts) o = *opts;
+    if (o.precision != YGM_FP64 && o.precision != YGM_FP32) return cerr(YGM_EINVAL, "precision must be YGM_FP64 or YGM_FP32");
+    if (o.n_rhs < 1 || o.n_rhs > 256 || (o.n_rhs & (o.n_rhs - 1)))
+        return cerr(YGM_EINVAL, "n_rhs must be a power of two in [1, 256]");
+    if (o.energy_every < 0) return cerr(YGM_EINVAL, "energy_every must be >= 0");
+    if (o.device != -1) {
+        int ndev = 0;
+        if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return cerr(YGM_ENODEV, "no CUDA device");
+        if (o.device < 0 || o.device >= ndev) return cerr(YGM_EINVAL, "device ordinal out of range");
+    }
+    ygm_ctx* ctx = new (std::nothrow) ygm_ctx();
+    if (!ctx) return cerr(YGM_ENOMEM, "host allocation failed");
+    try {
+        ctx->S = src->S;
+    } catch (const std::exception& ex) {
+        delete ctx;
+        return cerr(YGM_ENOMEM, std::string("copying the host set-up failed: ") + ex.what());
+    }
+    return finish_create(ctx, o, out);
 }
 
 int ygm_sizes(const ygm_ctx* ctx, int64_t* n1, int64_t* n2, int64_t* q1_nnz, double* dt_cfl) {
@@ -1739,8 +2081,32 @@ int ygm_set_q1(ygm_ctx* ctx, const int64_t* rowptr, const int64_t* colind, const
         CK(cudaStreamSynchronize(ctx->stream));
         cudaFree(ctx->q);
         cudaFree(ctx->qf);
-        ctx->q = ctx->qf = nullptr;
+        cudaFree(ctx->qsd);
+        ctx->q = ctx->qf = ctx->qsd = nullptr;
         if ((rc = upload_real(ctx, &ctx->q, ctx->S.qvals)) || (rc = upload_real(ctx, &ctx->qf, ctx->S.qfull))) return rc;
+        if (ctx->use_sym && (rc = upload_real(ctx, &ctx->qsd, ctx->S.qsym))) return rc;
+    }
+    return YGM_OK;
+}
+
+int ygm_spai_op(ygm_ctx* ctx, const double* V, int32_t n_probe, double lambda, int32_t max_iter, double tol,
+                int32_t* iters, double* rel_residual) {
+    if (!ctx) return YGM_EINVAL;
+    int it = 0;
+    double rr = 0.0;
+    int rc = ygm::spai_op(ctx->S, V, n_probe, lambda, max_iter, tol, 0, &it, &rr);
+    if (iters) *iters = it;
+    if (rel_residual) *rel_residual = rr;
+    if (rc) return fail(ctx, rc == -1 ? YGM_EINVAL : rc == -2 ? YGM_ETIMEOUT : YGM_ENOTSPD, ctx->S.err);
+    if (!ctx->host_only) {
+        CK(cudaSetDevice(ctx->device));
+        CK(cudaStreamSynchronize(ctx->stream));
+        cudaFree(ctx->q);
+        cudaFree(ctx->qf);
+        cudaFree(ctx->qsd);
+        ctx->q = ctx->qf = ctx->qsd = nullptr;
+        if ((rc = upload_real(ctx, &ctx->q, ctx->S.qvals)) || (rc = upload_real(ctx, &ctx->qf, ctx->S.qfull))) return rc;
+        if (ctx->use_sym && (rc = upload_real(ctx, &ctx->qsd, ctx->S.qsym))) return rc;
     }
     return YGM_OK;
 }
@@ -1902,7 +2268,9 @@ void ygm_destroy(ygm_ctx* ctx) {
         if (ctx->damp[i]) cudaFree(ctx->damp[i]);
         if (ctx->hamp[i]) cudaFreeHost(ctx->hamp[i]);
     }
-    void* more[] = {ctx->qslots, ctx->qblocks, ctx->eblocks, ctx->bblocks, ctx->pterms, ctx->pbeg};
+    void* more[] = {ctx->qslots, ctx->qblocks, ctx->eblocks, ctx->bblocks, ctx->pterms, ctx->pbeg,
+                    ctx->qsd,    ctx->soff2,   ctx->sblks,   ctx->xp,      ctx->bp,     ctx->wterms,
+                    ctx->cterms, ctx->lblks_b, ctx->lblks_e};
     for (void* p : more)
         if (p) cudaFree(p);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);

@@ -70,3 +70,70 @@ def test_set_q1_checks_pattern_symmetry_and_definiteness():
         c.set_q1(Q.tocsr())
     with pytest.raises(Y.YgmError):
         c.set_q1(-g.Q1)                                # negative definite
+
+
+def _probe_modes(f, M1, count):
+    """The lowest non-kernel eigenmodes of M1^-1 P2 (dense generalised eigensolver, test side),
+    normalised to v^T M1 v = 1."""
+    import scipy.linalg as sl
+    P2 = (f.C().T @ f.M2() @ f.C()).tocsr()
+    w, V = sl.eigh(P2.toarray(), M1.toarray())
+    nz = np.where(w > 1e-8 * w[-1])[0][:count]
+    return P2, w[nz], V[:, nz]
+
+
+@pytest.mark.parametrize("lam", [0.0, 1e3])
+def test_host_spai_op_matches_oracle(lam):
+    """ygm_spai_op (Sec. 5.1) against the oracle's Sylvester PCG, same pattern, probes, warm start."""
+    from oracle import spai as SP
+    from oracle import spai_op as OP
+    f, g, eps, _ = oracle_model(3, 1, eps_seed=5)
+    M1 = f.M1()
+    P2, w, V = _probe_modes(f, M1, 3)
+    c = Y.Context(3, 1, eps=eps, device=-1)
+    it, rr = c.spai_op(V, lam, tol=1e-13)
+    assert rr <= 1e-13 and it > 0
+    rp, ci, va = c.export_q1()
+    Qb = sp.csr_matrix((va, ci, rp), shape=(c.N1, c.N1))
+    Qo, _ = OP.spai_op(M1, SP.pattern("sm1", M1, f.dof1), P2=P2, V=V, lam=lam, q0=g.Q1, tol=1e-13)
+    assert Qb.nnz == Qo.nnz
+    assert abs(Qb - Qo).max() <= 1e-9 * abs(Qo).max()
+    assert abs(Qb - Qb.T).max() == 0.0
+    if lam > 0:    # the probed modes' residuals fall well below the column SPAI's
+        for j in range(V.shape[1]):
+            assert OP.eig_residual(Qb, P2, V[:, j], w[j]) < 0.05 * OP.eig_residual(g.Q1, P2, V[:, j], w[j])
+    info = c.q1_info()
+    assert info["lmin"] > 0 and abs(c.tau_cfl - 2 / np.sqrt(info["omega_max_sq"])) < 1e-12 * c.tau_cfl
+
+
+def test_host_spai_op_rejects_bad_input():
+    c = Y.Context(2, 1, device=-1)
+    with pytest.raises(Y.YgmError) as ei:
+        c.spai_op(np.full((c.N1, 1), np.nan), 1.0)
+    assert ei.value.code == Y.YGM_EINVAL
+    with pytest.raises(Y.YgmError) as ei:
+        c.spai_op(np.ones((c.N1, 1)), -1.0)
+    assert ei.value.code == Y.YGM_EINVAL
+    with pytest.raises(Y.YgmError) as ei:
+        c.spai_op(np.ones((c.N1, 1)), 1e3, max_iter=1, tol=1e-15)
+    assert ei.value.code == Y.YGM_ETIMEOUT
+    c2 = Y.Context(2, 2, device=-1)                  # k >= 2: SPAI in the orthogonalised basis
+    with pytest.raises(Y.YgmError) as ei:
+        c2.spai_op(None, 0.0)
+    assert ei.value.code == Y.YGM_EINVAL
+
+
+def test_create_like_copies_the_operators_without_recomputing():
+    f, g, eps, _ = oracle_model(3, 1, eps_seed=5)
+    c = Y.Context(3, 1, eps=eps, device=-1)
+    it, _ = c.spai_op(np.ones((c.N1, 1)) / np.sqrt(c.N1), 10.0, tol=1e-12)
+    d = c.like(precision=Y.YGM_FP32, n_rhs=4, device=-1)
+    assert (d.N1, d.N2, d.q1_nnz) == (c.N1, c.N2, c.q1_nnz) and d.tau_cfl == c.tau_cfl
+    for a, b in zip(c.export_q1(), d.export_q1()):
+        assert np.array_equal(a, b)
+    assert d.q1_info() == c.q1_info()
+    c.close()
+    assert d.export_q1()[0].shape == (d.N1 + 1,)      # independent of the source's lifetime
+    with pytest.raises(Y.YgmError) as ei:
+        d.like(n_rhs=3, device=-1)
+    assert ei.value.code == Y.YGM_EINVAL
