@@ -190,9 +190,10 @@ int ygm_set_q1(ygm_ctx* ctx, const int64_t* rowptr, const int64_t* colind, const
  *   lambda   probing weight >= 0
  *   max_iter / tol  PCG stops when ||r|| <= tol ||r_0|| (relative residual of the system)
  *   iters, rel_residual  (may be NULL) PCG iterations run and the final relative residual
- * Available for contexts whose Q1 is computed in the original basis (order 1; ygm_q1_info
- * ortho = 0).  Errors: YGM_EINVAL (arguments, basis), YGM_ETIMEOUT (PCG did not converge within
- * max_iter; Q1 unchanged), YGM_ENOTSPD.  Synchronises the context stream. */
+ * Where the SPAI is built in the entity-orthonormal basis (ygm_q1_info ortho = 1, orders >= 2),
+ * the same system is solved for Q' = T^-T Q1 T^-1 with M' = T M1 T^T and probes T P2 v_k, and
+ * Q1 = T^T Q' T keeps its pattern.  Errors: YGM_EINVAL (arguments), YGM_ETIMEOUT (PCG did not
+ * converge within max_iter; Q1 unchanged), YGM_ENOTSPD.  Synchronises the context stream. */
 int ygm_spai_op(ygm_ctx* ctx, const double* V, int32_t n_probe, double lambda, int32_t max_iter, double tol,
                 int32_t* iters, double* rel_residual);
 

@@ -116,3 +116,24 @@ def frobenius_error(M1, Q1):
 def eig_residual(Q1, P2, v, lam_k):
     """epsilon_k = ||Q1 P2 v - lam_k v|| / |lam_k| (Eq. eigError)."""
     return float(np.linalg.norm(Q1 @ (P2 @ v) - lam_k * v) / abs(lam_k))
+
+
+def spai_op_q1(fem, M1, P2, V, lam, tol=1e-13, maxiter=20000):
+    """SPAI-OP Q1 under the pattern and basis policy of oracle.spai.gym_q1.
+
+    Order 1: Eq. SPAIOPSylvester on M1 with the S(M1) pattern, warm start the symmetrised column
+    SPAI.  Orders >= 2 (reading R2 of the column SPAI): the same system in the entity-orthonormal
+    basis, M' = T M1 T^T on S(M1^2), probes W' = T P2 V (the probe term (M1 Q1 - 1) P2 v equals
+    T^-1 (M' Q' - 1) T P2 v), warm start the column SPAI of M', and Q1 = T^T Q' T."""
+    from oracle import spai as SP
+    pattern_kind, _ = SP.default_policy(fem.mesh.k)
+    basis = SP.basis_for(fem.mesh.k, pattern_kind)
+    S = SP.pattern(pattern_kind, M1, fem.dof1)
+    if basis == "plain":
+        Q0 = SP.symmetrize(SP.spai_columns(M1, S))
+        return spai_op(M1, S, P2=P2, V=V, lam=lam, q0=Q0, tol=tol, maxiter=maxiter)
+    T = SP.ortho_basis_transform(fem, M1)
+    Mp = (T @ M1 @ T.T).tocsr()
+    Q0 = SP.symmetrize(SP.spai_columns(Mp, S))
+    Qp, info = spai_op(Mp, S, P2=(T @ P2).tocsr(), V=V, lam=lam, q0=Q0, tol=tol, maxiter=maxiter)
+    return SP.symmetrize((T.T @ Qp @ T).tocsr()), info

@@ -820,7 +820,8 @@ struct Builder {
     // ---------------------------------------------------------- entity-orthonormalised basis T
     // T is block diagonal over the mesh entities: the DoFs g of one edge, face or cell are
     // replaced by (M1[g,g])^(-1/2) times themselves (symmetric Lowdin orthonormalisation).
-    Csr ortho_T() {
+    // power = +0.5 gives the inverse map T^-1 (blocks (M1[g,g])^(1/2)).
+    Csr ortho_T(double power = -0.5) {
         const int64_t N1 = L.N1;
         const Csr& Mp = S.M1;
         // entity groups: DoFs of the same class kind/shape/anchor; classes of an entity are
@@ -851,7 +852,7 @@ struct Builder {
                 for (int a = 0; a < m; ++a)
                     for (int c = 0; c < m; ++c) {
                         double s = 0;
-                        for (int q = 0; q < m; ++q) s += V[(size_t)a * m + q] * V[(size_t)c * m + q] / std::sqrt(w[q]);
+                        for (int q = 0; q < m; ++q) s += V[(size_t)a * m + q] * V[(size_t)c * m + q] * std::pow(w[q], power);
                         lrows[g[a]].push_back({g[c], s});
                     }
             }
@@ -1457,15 +1458,128 @@ int repack_q1(Setup& S, int threads_in) {
 // symmetric, so on an entry (i, j):
 //   (U Q1 T + T Q1 U)_ij = G_ij + G_ji + lam sum_p (Y_ip W_jp + W_ip Y_jp),  G = U Q1, Y = U Q1 W,
 //   R_ij = 2 M1_ij + lam sum_p (Z_ip W_jp + W_ip Z_jp),                       Z = M1 W.
+// PCG on the Sylvester system for matrix M, pattern and warm start Q (overwritten with the
+// solution, made exactly symmetric), probes W = P2 V (N x np, column-major) in M's basis.
+static int sylvester_pcg(const Csr& M, Csr& Q, const std::vector<double>& W, int np, double lam, int maxit,
+                         double tol, int threads, int* iters, double* relres, std::string& err) {
+    const int64_t N1 = M.nrows;
+    const Csr& P = Q;
+    const int64_t nq = P.ptr[N1];
+    std::vector<double> Z((size_t)N1 * np);
+    for (int p = 0; p < np; ++p) M.matvec(&W[(size_t)p * N1], &Z[(size_t)p * N1], threads);
+    const Csr U = spgemm(M, M, threads);
+    std::vector<int64_t> rowof(nq), tpos(nq);
+    for (int64_t i = 0; i < N1; ++i)
+        for (int64_t k = P.ptr[i]; k < P.ptr[i + 1]; ++k) rowof[k] = i;
+    for (int64_t k = 0; k < nq; ++k) {
+        const int64_t i = rowof[k], j = P.col[k];
+        const auto b = P.col.begin() + P.ptr[j], e = P.col.begin() + P.ptr[j + 1];
+        const auto it = std::lower_bound(b, e, i);
+        if (it == e || *it != i) {
+            err = "SPAI-OP: the Q1 pattern is not symmetric";
+            return -1;
+        }
+        tpos[k] = it - P.col.begin();
+    }
+    std::vector<double> Ud(N1), Td(N1, 1.0);
+    for (int64_t i = 0; i < N1; ++i) {
+        Ud[i] = U.get(i, i);
+        for (int p = 0; p < np; ++p) Td[i] += lam * W[(size_t)p * N1 + i] * W[(size_t)p * N1 + i];
+    }
+    auto lowrank = [&](const std::vector<double>& Yv, int64_t i, int64_t j) {
+        double t = 0;
+        for (int p = 0; p < np; ++p)
+            t += Yv[(size_t)p * N1 + i] * W[(size_t)p * N1 + j] + W[(size_t)p * N1 + i] * Yv[(size_t)p * N1 + j];
+        return lam * t;
+    };
+    std::vector<double> r(nq), prec(nq);
+    for (int64_t k = 0; k < nq; ++k) {
+        const int64_t i = rowof[k], j = P.col[k];
+        r[k] = 2.0 * M.get(i, j) + (np ? lowrank(Z, i, j) : 0.0);
+        prec[k] = Ud[i] * Td[j] + Td[i] * Ud[j];
+    }
+    // y = A x on the pattern (matrix-free)
+    std::vector<double> G(nq), QW((size_t)N1 * np), Y((size_t)N1 * np);
+    auto apply = [&](const std::vector<double>& x, std::vector<double>& y) {
+        // G = U Q (entries of the pattern only), row-parallel with a dense column -> slot map
+        parallel_for(N1, threads, [&](int64_t b, int64_t e, int) {
+            std::vector<int64_t> slot(N1, -1);
+            for (int64_t i = b; i < e; ++i) {
+                for (int64_t k = P.ptr[i]; k < P.ptr[i + 1]; ++k) {
+                    slot[P.col[k]] = k;
+                    G[k] = 0.0;
+                }
+                for (int64_t a = U.ptr[i]; a < U.ptr[i + 1]; ++a) {
+                    const int64_t m = U.col[a];
+                    const double u = U.val[a];
+                    for (int64_t c = P.ptr[m]; c < P.ptr[m + 1]; ++c) {
+                        const int64_t sl = slot[P.col[c]];
+                        if (sl >= 0) G[sl] += u * x[c];
+                    }
+                }
+                for (int64_t k = P.ptr[i]; k < P.ptr[i + 1]; ++k) slot[P.col[k]] = -1;
+            }
+        });
+        if (np > 0) {
+            parallel_for(N1, threads, [&](int64_t b, int64_t e, int) {
+                for (int64_t i = b; i < e; ++i)
+                    for (int p = 0; p < np; ++p) {
+                        double t = 0;
+                        for (int64_t k = P.ptr[i]; k < P.ptr[i + 1]; ++k) t += x[k] * W[(size_t)p * N1 + P.col[k]];
+                        QW[(size_t)p * N1 + i] = t;
+                    }
+            });
+            for (int p = 0; p < np; ++p) U.matvec(&QW[(size_t)p * N1], &Y[(size_t)p * N1], threads);
+        }
+        parallel_for(nq, threads, [&](int64_t b, int64_t e, int) {
+            for (int64_t k = b; k < e; ++k)
+                y[k] = G[k] + G[tpos[k]] + (np ? lowrank(Y, rowof[k], P.col[k]) : 0.0);
+        });
+    };
+    auto dot = [&](const std::vector<double>& a, const std::vector<double>& b2) {
+        double t = 0;
+        for (int64_t k = 0; k < nq; ++k) t += a[k] * b2[k];
+        return t;
+    };
+    std::vector<double> q(P.val), res(nq), z(nq), pdir(nq), Ap(nq);
+    apply(q, Ap);
+    for (int64_t k = 0; k < nq; ++k) res[k] = r[k] - Ap[k];
+    const double r0 = std::sqrt(dot(r, r));
+    double rn = std::sqrt(dot(res, res));
+    for (int64_t k = 0; k < nq; ++k) z[k] = res[k] / prec[k];
+    pdir = z;
+    double rz = dot(res, z);
+    int it = 0;
+    while (it < maxit && rn > tol * r0) {
+        apply(pdir, Ap);
+        const double alpha = rz / dot(pdir, Ap);
+        for (int64_t k = 0; k < nq; ++k) {
+            q[k] += alpha * pdir[k];
+            res[k] -= alpha * Ap[k];
+        }
+        rn = std::sqrt(dot(res, res));
+        ++it;
+        for (int64_t k = 0; k < nq; ++k) z[k] = res[k] / prec[k];
+        const double rz2 = dot(res, z);
+        for (int64_t k = 0; k < nq; ++k) pdir[k] = z[k] + (rz2 / rz) * pdir[k];
+        rz = rz2;
+    }
+    if (iters) *iters = it;
+    if (relres) *relres = r0 > 0 ? rn / r0 : 0.0;
+    if (!(rn <= tol * r0)) {
+        err = "SPAI-OP: PCG did not reach the tolerance within max_iter (Q1 unchanged)";
+        return -2;
+    }
+    // the solution is symmetric up to the PCG's rounding (Sec. 5.1); store it exactly so
+    for (int64_t k = 0; k < nq; ++k) Q.val[k] = 0.5 * (q[k] + q[tpos[k]]);
+    return 0;
+}
+
 int spai_op(Setup& S, const double* V, int np, double lam, int maxit, double tol, int threads_in, int* iters,
             double* relres) {
     const int threads = default_threads(threads_in);
     const Lattice& L = S.L;
     const int64_t N1 = L.N1;
-    if (S.ortho) {
-        S.err = "SPAI-OP is available for Q1 computed in the original basis (order 1)";
-        return -1;
-    }
     if (np < 0 || (np > 0 && !V) || !(lam >= 0) || !std::isfinite(lam) || maxit < 0 || !(tol > 0)) {
         S.err = "SPAI-OP: need n_probe >= 0 (probe modes when > 0), finite lambda >= 0, max_iter >= 0, tol > 0";
         return -1;
@@ -1477,119 +1591,32 @@ int spai_op(Setup& S, const double* V, int np, double lam, int maxit, double tol
         }
     try {
         Builder B(S, threads);
-        const Csr& P = S.Q1;
-        const int64_t nq = P.ptr[N1];
-        std::vector<double> W((size_t)N1 * np), Z((size_t)N1 * np);
+        std::vector<double> W((size_t)N1 * np);
         if (np > 0) B.make_P2loc();
-        for (int p = 0; p < np; ++p) {
-            B.P2_matvec(V + (size_t)p * N1, &W[(size_t)p * N1]);
-            S.M1.matvec(&W[(size_t)p * N1], &Z[(size_t)p * N1], threads);
-        }
-        const Csr U = spgemm(S.M1, S.M1, threads);
-        std::vector<int64_t> rowof(nq), tpos(nq);
-        for (int64_t i = 0; i < N1; ++i)
-            for (int64_t k = P.ptr[i]; k < P.ptr[i + 1]; ++k) rowof[k] = i;
-        for (int64_t k = 0; k < nq; ++k) {
-            const int64_t i = rowof[k], j = P.col[k];
-            const auto b = P.col.begin() + P.ptr[j], e = P.col.begin() + P.ptr[j + 1];
-            const auto it = std::lower_bound(b, e, i);
-            if (it == e || *it != i) {
-                S.err = "SPAI-OP: the Q1 pattern is not symmetric";
-                return -1;
+        for (int p = 0; p < np; ++p) B.P2_matvec(V + (size_t)p * N1, &W[(size_t)p * N1]);
+        int rc;
+        if (!S.ortho) {
+            Csr Q = S.Q1;
+            rc = sylvester_pcg(S.M1, Q, W, np, lam, maxit, tol, threads, iters, relres, S.err);
+            if (rc) return rc;
+            S.Q1 = std::move(Q);
+        } else {
+            // orders >= 2: Q1 = T^T Q' T with Q' the SPAI-OP of M' = T M1 T^T in the
+            // entity-orthonormal basis, probes W' = T P2 V, warm start Q' = T^-T Q1 T^-1
+            const Csr Tm = B.ortho_T(-0.5), Ti = B.ortho_T(0.5);
+            const Csr Mp = spgemm(spgemm(Tm, S.M1, threads), transpose(Tm), threads);
+            Csr Qp = spgemm(spgemm(transpose(Ti), S.Q1, threads), Ti, threads);
+            std::vector<double> Wp((size_t)N1 * np);
+            for (int p = 0; p < np; ++p) Tm.matvec(&W[(size_t)p * N1], &Wp[(size_t)p * N1], threads);
+            rc = sylvester_pcg(Mp, Qp, Wp, np, lam, maxit, tol, threads, iters, relres, S.err);
+            if (rc) return rc;
+            Csr Q1 = symmetrize(spgemm(spgemm(transpose(Tm), Qp, threads), Tm, threads), threads);
+            if (Q1.ptr != S.Q1.ptr || Q1.col != S.Q1.col) {
+                S.err = "internal: SPAI-OP changed the Q1 pattern";
+                return -3;
             }
-            tpos[k] = it - P.col.begin();
+            S.Q1 = std::move(Q1);
         }
-        std::vector<double> Ud(N1), Td(N1, 1.0);
-        for (int64_t i = 0; i < N1; ++i) {
-            Ud[i] = U.get(i, i);
-            for (int p = 0; p < np; ++p) Td[i] += lam * W[(size_t)p * N1 + i] * W[(size_t)p * N1 + i];
-        }
-        auto lowrank = [&](const std::vector<double>& Yv, int64_t i, int64_t j) {
-            double t = 0;
-            for (int p = 0; p < np; ++p)
-                t += Yv[(size_t)p * N1 + i] * W[(size_t)p * N1 + j] + W[(size_t)p * N1 + i] * Yv[(size_t)p * N1 + j];
-            return lam * t;
-        };
-        std::vector<double> r(nq), prec(nq);
-        for (int64_t k = 0; k < nq; ++k) {
-            const int64_t i = rowof[k], j = P.col[k];
-            r[k] = 2.0 * S.M1.get(i, j) + (np ? lowrank(Z, i, j) : 0.0);
-            prec[k] = Ud[i] * Td[j] + Td[i] * Ud[j];
-        }
-        // y = A x on the pattern (matrix-free)
-        std::vector<double> G(nq), QW((size_t)N1 * np), Y((size_t)N1 * np);
-        auto apply = [&](const std::vector<double>& x, std::vector<double>& y) {
-            // G = U Q (entries of the pattern only), row-parallel with a dense column -> slot map
-            parallel_for(N1, threads, [&](int64_t b, int64_t e, int) {
-                std::vector<int64_t> slot(N1, -1);
-                for (int64_t i = b; i < e; ++i) {
-                    for (int64_t k = P.ptr[i]; k < P.ptr[i + 1]; ++k) {
-                        slot[P.col[k]] = k;
-                        G[k] = 0.0;
-                    }
-                    for (int64_t a = U.ptr[i]; a < U.ptr[i + 1]; ++a) {
-                        const int64_t m = U.col[a];
-                        const double u = U.val[a];
-                        for (int64_t c = P.ptr[m]; c < P.ptr[m + 1]; ++c) {
-                            const int64_t sl = slot[P.col[c]];
-                            if (sl >= 0) G[sl] += u * x[c];
-                        }
-                    }
-                    for (int64_t k = P.ptr[i]; k < P.ptr[i + 1]; ++k) slot[P.col[k]] = -1;
-                }
-            });
-            if (np > 0) {
-                parallel_for(N1, threads, [&](int64_t b, int64_t e, int) {
-                    for (int64_t i = b; i < e; ++i)
-                        for (int p = 0; p < np; ++p) {
-                            double t = 0;
-                            for (int64_t k = P.ptr[i]; k < P.ptr[i + 1]; ++k) t += x[k] * W[(size_t)p * N1 + P.col[k]];
-                            QW[(size_t)p * N1 + i] = t;
-                        }
-                });
-                for (int p = 0; p < np; ++p) U.matvec(&QW[(size_t)p * N1], &Y[(size_t)p * N1], threads);
-            }
-            parallel_for(nq, threads, [&](int64_t b, int64_t e, int) {
-                for (int64_t k = b; k < e; ++k)
-                    y[k] = G[k] + G[tpos[k]] + (np ? lowrank(Y, rowof[k], P.col[k]) : 0.0);
-            });
-        };
-        auto dot = [&](const std::vector<double>& a, const std::vector<double>& b2) {
-            double t = 0;
-            for (int64_t k = 0; k < nq; ++k) t += a[k] * b2[k];
-            return t;
-        };
-        std::vector<double> q(P.val), res(nq), z(nq), pdir(nq), Ap(nq);
-        apply(q, Ap);
-        for (int64_t k = 0; k < nq; ++k) res[k] = r[k] - Ap[k];
-        const double r0 = std::sqrt(dot(r, r));
-        double rn = std::sqrt(dot(res, res));
-        for (int64_t k = 0; k < nq; ++k) z[k] = res[k] / prec[k];
-        pdir = z;
-        double rz = dot(res, z);
-        int it = 0;
-        while (it < maxit && rn > tol * r0) {
-            apply(pdir, Ap);
-            const double alpha = rz / dot(pdir, Ap);
-            for (int64_t k = 0; k < nq; ++k) {
-                q[k] += alpha * pdir[k];
-                res[k] -= alpha * Ap[k];
-            }
-            rn = std::sqrt(dot(res, res));
-            ++it;
-            for (int64_t k = 0; k < nq; ++k) z[k] = res[k] / prec[k];
-            const double rz2 = dot(res, z);
-            for (int64_t k = 0; k < nq; ++k) pdir[k] = z[k] + (rz2 / rz) * pdir[k];
-            rz = rz2;
-        }
-        if (iters) *iters = it;
-        if (relres) *relres = r0 > 0 ? rn / r0 : 0.0;
-        if (!(rn <= tol * r0)) {
-            S.err = "SPAI-OP: PCG did not reach the tolerance within max_iter (Q1 unchanged)";
-            return -2;
-        }
-        // the solution is symmetric up to the PCG's rounding (Sec. 5.1); store it exactly so
-        for (int64_t k = 0; k < nq; ++k) S.Q1.val[k] = 0.5 * (q[k] + q[tpos[k]]);
     } catch (const std::exception& ex) {
         S.err = ex.what();
         return -3;
