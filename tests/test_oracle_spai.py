@@ -136,3 +136,25 @@ def test_dispersion_spai_sm1_matches_printed_value():
     wp, dev = _TABLE["spai_sm1"]
     assert abs(wt / wp - 1) < 3e-4 and abs(w / wp - 1) < 3e-4
     assert abs((wt - w0) / w0 - dev) < 5e-4
+
+
+# ---------------------------------------------------------------- Table SPAIOPeigTable, SPAI rows
+def test_spai_eigen_residual_table_rows():
+    """Sec. 7.2: residual eigenvalue errors of the column SPAI on the 20 x 80 torus, per pattern,
+    against the printed table (tests/golden/spai_eig_table.txt); eigenvectors of the exact
+    generalised problem P2 v = lam M1 v with unit 2-norm."""
+    import scipy.linalg as sl
+    t = Torus2D(20, 80, Lx=5.0, Ly=20.0)
+    M1, C, M2 = t.M1(), t.C(), t.M2()
+    P2 = (C.T @ M2 @ C).tocsr()
+    w, V = sl.eigh(P2.toarray(), M1.toarray())
+    nz = np.where(w > 1e-8 * w[-1])[0]
+    assert len(nz) == 1599 and t.N1 - len(nz) == 1601
+    V = V[:, nz] / np.linalg.norm(V[:, nz], axis=0)
+    lam = w[nz]
+    for row in golden("spai_eig_table.txt"):
+        Q, _ = SP.spai(M1, row[0])
+        eps = np.linalg.norm(Q @ (P2 @ V) - V * lam, axis=0) / np.abs(lam)
+        got = (eps.mean(), eps[:100].mean(), eps[100:].mean())
+        for g, printed in zip(got, map(fraction, row[1:])):
+            assert abs(g - printed) <= 5e-5, (row[0], got)
