@@ -116,7 +116,7 @@ def peaks():
 
 
 # ------------------------------------------------------------------ CPU oracle timing
-def oracle_sample(steps=2000, n=4):
+def oracle_sample(steps=20000, n=4):
     """The FP64 CPU oracle as it stands, on a bounded sample of the workload: the same recipe on an
     n^3 cube (eps seed 2000, same source), `steps` leapfrog steps; returns DoF-updates/s."""
     from oracle import spai as SP
@@ -145,7 +145,7 @@ def run_reference(args, rank, world):
         return
     vals = []
     for i in range(args.warmup + args.steps):
-        v, el, info = oracle_sample()
+        v, el, info = oracle_sample(steps=args.cpu_steps)
         if i >= args.warmup:
             vals.append((v, el))
     value = float(np.mean([v for v, _ in vals]))
@@ -352,7 +352,8 @@ def main():
     ap.add_argument("--n", type=int, default=32)
     ap.add_argument("--order", type=int, default=2)
     ap.add_argument("--leapfrog-steps", type=int, default=2000)
-    ap.add_argument("--cpu-steps", type=int, default=2000)
+    ap.add_argument("--cpu-steps", type=int, default=20000,
+                    help="leapfrog steps of the timed FP64 oracle sample (about 10 s on one core)")
     ap.add_argument("--energy-every", type=int, default=100)
     ap.add_argument("--rhs", type=int, default=1, help="right-hand-side columns (batched excitations)")
     ap.add_argument("--no-accuracy", action="store_true")
