@@ -175,7 +175,8 @@ int ygm_export_q1(const ygm_ctx* ctx, int64_t* rowptr, int64_t* colind, double* 
  * map symplectic (Theorem symplecticity); it must be SPD for stability (Prop. stability).  Its
  * pattern must lie inside this context's stencil (S(1), S(M1) or S(M1^2) of q1_pattern).  The
  * SPD check and tau_CFL are recomputed; the state is kept.  Errors: YGM_EINVAL (pattern,
- * symmetry, sizes), YGM_ENOTSPD.  Synchronises the context stream. */
+ * symmetry, sizes), YGM_ENOTSPD (the previous Q1 is kept), YGM_ECUDA (the device copies could
+ * not be refreshed: destroy the context).  Synchronises the context stream. */
 int ygm_set_q1(ygm_ctx* ctx, const int64_t* rowptr, const int64_t* colind, const double* val);
 
 /* Operator-probed SPAI, SPAI-OP (Sec. 5.1): replace Q1 by the symmetric matrix on the current
@@ -193,7 +194,8 @@ int ygm_set_q1(ygm_ctx* ctx, const int64_t* rowptr, const int64_t* colind, const
  * Where the SPAI is built in the entity-orthonormal basis (ygm_q1_info ortho = 1, orders >= 2),
  * the same system is solved for Q' = T^-T Q1 T^-1 with M' = T M1 T^T and probes T P2 v_k, and
  * Q1 = T^T Q' T keeps its pattern.  Errors: YGM_EINVAL (arguments), YGM_ETIMEOUT (PCG did not
- * converge within max_iter; Q1 unchanged), YGM_ENOTSPD.  Synchronises the context stream. */
+ * converge within max_iter; Q1 unchanged), YGM_ENOTSPD (the previous Q1 is kept), YGM_ECUDA (the
+ * device copies could not be refreshed: destroy the context).  Synchronises the context stream. */
 int ygm_spai_op(ygm_ctx* ctx, const double* V, int32_t n_probe, double lambda, int32_t max_iter, double tol,
                 int32_t* iters, double* rel_residual);
 

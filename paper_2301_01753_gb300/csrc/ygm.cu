@@ -2097,10 +2097,21 @@ int ygm_export_q1(const ygm_ctx* ctx, int64_t* rowptr, int64_t* colind, double* 
     return YGM_OK;
 }
 
+// A Q1 update that failed its SPD check: put the previous Q1 back into the host set-up (the
+// device copies were not touched) and keep the error message.
+static int restore_q1(ygm_ctx* ctx, ygm::Csr&& old, int code) {
+    const std::string msg = ctx->S.err;
+    ctx->S.Q1 = std::move(old);
+    ygm::repack_q1(ctx->S, 0);
+    return fail(ctx, code, msg);
+}
+
 int ygm_set_q1(ygm_ctx* ctx, const int64_t* rowptr, const int64_t* colind, const double* val) {
     if (!ctx || !rowptr || !colind || !val) return fail(ctx, YGM_EINVAL, "NULL argument");
+    ygm::Csr old = ctx->S.Q1;
     int rc = ygm::install_q1(ctx->S, rowptr, colind, val, 0);
-    if (rc) return fail(ctx, rc == -1 ? YGM_EINVAL : YGM_ENOTSPD, ctx->S.err);
+    if (rc == -1) return fail(ctx, YGM_EINVAL, ctx->S.err);
+    if (rc) return restore_q1(ctx, std::move(old), YGM_ENOTSPD);
     if (!ctx->host_only) {
         CK(cudaStreamSynchronize(ctx->stream));
         cudaFree(ctx->q);
@@ -2118,10 +2129,12 @@ int ygm_spai_op(ygm_ctx* ctx, const double* V, int32_t n_probe, double lambda, i
     if (!ctx) return YGM_EINVAL;
     int it = 0;
     double rr = 0.0;
+    ygm::Csr old = ctx->S.Q1;
     int rc = ygm::spai_op(ctx->S, V, n_probe, lambda, max_iter, tol, 0, &it, &rr);
     if (iters) *iters = it;
     if (rel_residual) *rel_residual = rr;
-    if (rc) return fail(ctx, rc == -1 ? YGM_EINVAL : rc == -2 ? YGM_ETIMEOUT : YGM_ENOTSPD, ctx->S.err);
+    if (rc == -1 || rc == -2) return fail(ctx, rc == -1 ? YGM_EINVAL : YGM_ETIMEOUT, ctx->S.err);
+    if (rc) return restore_q1(ctx, std::move(old), YGM_ENOTSPD);
     if (!ctx->host_only) {
         CK(cudaSetDevice(ctx->device));
         CK(cudaStreamSynchronize(ctx->stream));

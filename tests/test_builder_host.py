@@ -68,8 +68,14 @@ def test_set_q1_checks_pattern_symmetry_and_definiteness():
     Q[i, j] += 1.0                                     # breaks symmetry
     with pytest.raises(Y.YgmError):
         c.set_q1(Q.tocsr())
-    with pytest.raises(Y.YgmError):
+    rp0, ci0, va0 = c.export_q1()
+    tau0 = c.tau_cfl
+    with pytest.raises(Y.YgmError) as ei:
         c.set_q1(-g.Q1)                                # negative definite
+    assert ei.value.code == Y.YGM_ENOTSPD
+    rp1, ci1, va1 = c.export_q1()                      # the previous Q1 is kept
+    assert np.array_equal(rp0, rp1) and np.array_equal(ci0, ci1) and np.array_equal(va0, va1)
+    assert c.sizes()[3] == tau0 and c.q1_info()["lmin"] > 0
 
 
 def _probe_modes(f, M1, count):
