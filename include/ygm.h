@@ -199,6 +199,22 @@ int ygm_set_q1(ygm_ctx* ctx, const int64_t* rowptr, const int64_t* colind, const
 int ygm_spai_op(ygm_ctx* ctx, const double* V, int32_t n_probe, double lambda, int32_t max_iter, double tol,
                 int32_t* iters, double* rel_residual);
 
+/* Probe modes for ygm_spai_op (Sec. 5.1: eigenmodes of K = M1^-1 P2 at the frequencies of
+ * interest): the `count` lowest non-kernel eigenpairs of P2 v = omega^2 M1 v of this context's
+ * exact FEEC operators (host FP64; the approximate Q1 is not involved).  Block shift-invert
+ * subspace iteration in the M1 inner product, kept M1-orthogonal to ker C (interior vertex
+ * gradients and the gradient 1-forms); each pair converges to
+ * ||P2 v - omega^2 M1 v|| <= tol omega^2 ||M1 v||.
+ *   V         host output, N1 x count column-major (mode k at V + k * N1), v^T M1 v = 1
+ *   omega_sq  host output, count values, ascending
+ *   iters     (may be NULL) outer iterations run
+ * Degenerate eigenvalues return an M1-orthonormal basis of their eigenspace.  Cost: count + 4 or
+ * more shifted CG solves per iteration, so it is meant for small and medium meshes.  Errors:
+ * YGM_EINVAL (arguments, count above the number of non-kernel modes, an inner solve that failed),
+ * YGM_ETIMEOUT (not converged within max_iter).  Does not touch the device. */
+int ygm_cavity_modes(ygm_ctx* ctx, int32_t count, double* V, double* omega_sq, int32_t max_iter, double tol,
+                     int32_t* iters);
+
 /* SPD check of Q1 (Sec. 5.1, practical considerations): Lanczos estimates of the smallest and
  * largest eigenvalue before any shift, the diagonal shift applied (0 if none), lambda_max(Q1 P2),
  * and which pattern / basis was used (YGM_Q1_*, ortho = 1 for the orthogonalised basis). */

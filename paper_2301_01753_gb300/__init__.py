@@ -18,7 +18,7 @@ YGM_FP64, YGM_FP32 = 0, 1
 YGM_Q1_DEFAULT, YGM_Q1_DIAG, YGM_Q1_SM1, YGM_Q1_SM1SQ = 0, 1, 2, 3
 
 EXPORTED = ["ygm_create", "ygm_create_like", "ygm_sizes", "ygm_set_state", "ygm_get_state", "ygm_project_E", "ygm_step", "ygm_step_noalloc",
-            "ygm_energy", "ygm_energy_history", "ygm_time", "ygm_export_q1", "ygm_set_q1", "ygm_spai_op", "ygm_q1_info",
+            "ygm_energy", "ygm_energy_history", "ygm_time", "ygm_export_q1", "ygm_set_q1", "ygm_spai_op", "ygm_cavity_modes", "ygm_q1_info",
             "ygm_local_blocks", "ygm_kernel_timing", "ygm_kernel_times", "ygm_launch_count",
             "ygm_qapply_counts", "ygm_last_error", "ygm_destroy"]
 KERNEL_KINDS = ["k_qapply", "k_curl_b", "k_curlT_e", "k_source", "k_energy"]
@@ -70,6 +70,7 @@ def load_library(path=LIB_PATH):
         "ygm_export_q1": (C.c_int, [P, pI64, pI64, pD]),
         "ygm_set_q1": (C.c_int, [P, pI64, pI64, pD]),
         "ygm_spai_op": (C.c_int, [P, pD, C.c_int32, D, C.c_int32, D, pI32, pD]),
+        "ygm_cavity_modes": (C.c_int, [P, C.c_int32, pD, pD, C.c_int32, D, pI32]),
         "ygm_q1_info": (C.c_int, [P, pD, pD, pD, pD, pI32, pI32]),
         "ygm_local_blocks": (C.c_int, [P, pI32, pI32, pD, pD]),
         "ygm_kernel_timing": (C.c_int, [P, C.c_int]),
@@ -265,6 +266,17 @@ class Context:
                                      npb, float(lam), int(max_iter), float(tol), C.byref(it), C.byref(rr)))
         self.N1, self.N2, self.q1_nnz, self.tau_cfl = self.sizes()
         return it.value, rr.value
+
+    def cavity_modes(self, count, max_iter=500, tol=1e-10):
+        """Lowest non-kernel eigenpairs of P2 v = omega^2 M1 v (ygm_cavity_modes):
+        returns (omega_sq[count], V[N1, count]) with v^T M1 v = 1."""
+        V = np.empty((count, self.N1), dtype=np.float64)          # row k = mode k (column-major N1 x count)
+        w = np.empty(count, dtype=np.float64)
+        it = C.c_int32()
+        self._check(_lib.ygm_cavity_modes(self._h, int(count), V.ctypes.data_as(C.POINTER(C.c_double)),
+                                          w.ctypes.data_as(C.POINTER(C.c_double)), int(max_iter), float(tol),
+                                          C.byref(it)))
+        return w, V.T.copy()
 
     def q1_info(self):
         lmin, lmax, sh, w2 = C.c_double(), C.c_double(), C.c_double(), C.c_double()

@@ -995,6 +995,23 @@ struct Builder {
         });
     }
 
+    // diagonal of P2 (needs make_P2loc): each incident tet adds its local diagonal entry
+    void P2_diag(double* d) {
+        const int n1 = L.n1;
+        parallel_for(L.N1, threads, [&](int64_t b, int64_t e, int) {
+            for (int64_t g = b; g < e; ++g) {
+                int c, v[3];
+                L.decode1(g, &c, v);
+                double s = 0;
+                for (const Incidence& in : L.inc1[c]) {
+                    int cx = v[0] + in.dcube[0], cy = v[1] + in.dcube[1], cz = v[2] + in.dcube[2];
+                    s += P2loc[(size_t)in.loc * n1 + in.loc] / S.mu[tet_index(cx, cy, cz, in.shape)];
+                }
+                d[g] = s;
+            }
+        });
+    }
+
     // ---------------------------------------------------------- Lanczos helpers
     // Symmetric Lanczos (three-term recurrence) for op self-adjoint in <x, y> = x^T B y;
     // returns the (smallest, largest) Ritz value.  Extreme Ritz values are found by Sturm
@@ -1622,6 +1639,240 @@ int spai_op(Setup& S, const double* V, int np, double lam, int maxit, double tol
         return -3;
     }
     return repack_q1(S, threads);
+}
+
+// ============================================================== cavity modes (probe vectors)
+// Lowest non-kernel eigenpairs of P2 v = lambda M1 v (the modes of K = M1^-1 P2 that Sec. 5.1 takes
+// as SPAI-OP probes).  Block shift-invert subspace iteration in the M1 inner product:
+//   Y = (P2 + sigma M1)^-1 M1 X,  Y <- Y minus its M1-projection on ker P2,  M1-orthonormalise Y,
+//   Rayleigh-Ritz with Y^T P2 Y,  X = Y Z,
+// until every wanted pair has ||P2 x - lambda M1 x|| <= tol lambda ||M1 x||.  ker P2 = ker C is
+// spanned by the gradients of the interior vertex hat functions (signed incidence on the Whitney
+// edge DoFs; an edge runs from its anchor v to v + d) and by the gradient 1-forms of the
+// hierarchical basis (one DoF each).  Inner solves: Jacobi-preconditioned CG.
+namespace {
+// Jacobi-preconditioned CG for SPD op; returns iterations (or -1 without convergence)
+int pcg(const std::function<void(const double*, double*)>& op, const std::vector<double>& dinv, const double* b,
+        double* x, int64_t n, double rtol, int maxit) {
+    std::vector<double> r(b, b + n), z(n), p(n), q(n);
+    std::fill(x, x + n, 0.0);
+    double bn = 0;
+    for (int64_t i = 0; i < n; ++i) bn += b[i] * b[i];
+    bn = std::sqrt(bn);
+    if (bn == 0) return 0;
+    for (int64_t i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
+    p = z;
+    double rz = 0;
+    for (int64_t i = 0; i < n; ++i) rz += r[i] * z[i];
+    for (int it = 1; it <= maxit; ++it) {
+        op(p.data(), q.data());
+        double pq = 0;
+        for (int64_t i = 0; i < n; ++i) pq += p[i] * q[i];
+        const double a = rz / pq;
+        double rn = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            x[i] += a * p[i];
+            r[i] -= a * q[i];
+            rn += r[i] * r[i];
+        }
+        if (std::sqrt(rn) <= rtol * bn) return it;
+        for (int64_t i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
+        double rz2 = 0;
+        for (int64_t i = 0; i < n; ++i) rz2 += r[i] * z[i];
+        for (int64_t i = 0; i < n; ++i) p[i] = z[i] + (rz2 / rz) * p[i];
+        rz = rz2;
+    }
+    return -1;
+}
+}  // namespace
+
+int cavity_modes(Setup& S, int count, double* V, double* lam, int maxit, double tol, int threads_in, int* iters) {
+    const Lattice& L = S.L;
+    const int64_t N1 = L.N1;
+    // the inner loops are light sparse products: worker threads pay off only on large meshes
+    const int threads = N1 < 200000 ? 1 : default_threads(threads_in);
+    if (count < 1 || !V || !lam || maxit < 1 || !(tol > 0)) {
+        S.err = "cavity modes: need count >= 1, output arrays, max_iter >= 1, tol > 0";
+        return -1;
+    }
+    try {
+        Builder B(S, threads);
+        B.make_P2loc();
+        // kernel basis as rows of K^T: interior vertex gradients, then the gradient 1-forms
+        std::vector<std::vector<std::pair<int64_t, double>>> kt;
+        const int n = L.n;
+        for (int z = 1; z < n; ++z)
+            for (int y = 1; y < n; ++y)
+                for (int x = 1; x < n; ++x) {
+                    std::vector<std::pair<int64_t, double>> col;
+                    for (int c = 0; c < (int)L.c1.size(); ++c) {
+                        if (L.c1[c].kind != 0 || L.c1[c].j != 0) continue;
+                        const int d = EDGE_D[L.c1[c].shape];
+                        const int64_t tail = L.index1(c, x, y, z);                                  // edge x -> x + d
+                        const int64_t head = L.index1(c, x - bit(d, 0), y - bit(d, 1), z - bit(d, 2));  // edge x - d -> x
+                        if (tail >= 0) col.push_back({tail, -1.0});
+                        if (head >= 0) col.push_back({head, 1.0});
+                    }
+                    std::sort(col.begin(), col.end());
+                    kt.push_back(col);
+                }
+        for (int c = 0; c < (int)L.c1.size(); ++c)
+            if (!L.c1[c].active)
+                for (int64_t r = 0; r < L.c1[c].box.size; ++r) kt.push_back({{L.c1[c].box.offset + r, 1.0}});
+        const int64_t nK = (int64_t)kt.size();
+        if (count > N1 - nK) {
+            S.err = "cavity modes: count exceeds the number of non-kernel modes";
+            return -1;
+        }
+        Csr Kt;
+        Kt.nrows = nK;
+        Kt.ncols = N1;
+        Kt.ptr.assign(nK + 1, 0);
+        for (int64_t i = 0; i < nK; ++i) Kt.ptr[i + 1] = Kt.ptr[i] + (int64_t)kt[i].size();
+        for (auto& col : kt)
+            for (auto& e : col) {
+                Kt.col.push_back(e.first);
+                Kt.val.push_back(e.second);
+            }
+        kt.clear();
+        const Csr K = transpose(Kt);
+        const Csr L0 = spgemm(spgemm(Kt, S.M1, threads), K, threads);    // K^T M1 K
+        std::vector<double> L0inv(nK), Pd(N1), Md(N1), Ainv(N1);
+        for (int64_t i = 0; i < nK; ++i) L0inv[i] = 1.0 / L0.get(i, i);
+        B.P2_diag(Pd.data());
+        for (int64_t i = 0; i < N1; ++i) Md[i] = S.M1.get(i, i);
+        const double sigma = 1.0 / (L.h * L.n * L.h * L.n);               // 1 / side^2
+        for (int64_t i = 0; i < N1; ++i) Ainv[i] = 1.0 / (Pd[i] + sigma * Md[i]);
+        std::vector<double> t1(N1), t2(N1), kz(nK), kr(nK);
+        // self-check: the basis lies in ker P2
+        {
+            std::vector<double> zz(nK), v(N1), pv(N1);
+            for (int64_t i = 0; i < nK; ++i) zz[i] = std::sin(0.37 * (double)i + 0.1);
+            K.matvec(zz.data(), v.data(), threads);
+            B.P2_matvec(v.data(), pv.data());
+            double a = 0, bnorm = 0, pmax = 0;
+            for (int64_t i = 0; i < N1; ++i) {
+                a += pv[i] * pv[i];
+                bnorm += v[i] * v[i];
+                pmax = std::max(pmax, Pd[i]);
+            }
+            if (std::sqrt(a) > 1e-10 * pmax * std::sqrt(bnorm)) {
+                S.err = "internal: the gradient basis is not in the kernel of P2";
+                return -3;
+            }
+        }
+        auto project = [&](double* x) {        // x <- x - K (K^T M1 K)^-1 K^T M1 x
+            S.M1.matvec(x, t1.data(), threads);
+            Kt.matvec(t1.data(), kr.data(), threads);
+            if (pcg([&](const double* a, double* b) { L0.matvec(a, b, threads); }, L0inv, kr.data(), kz.data(), nK,
+                    1e-13, 20000) < 0)
+                throw std::runtime_error("cavity modes: the kernel projection did not converge");
+            K.matvec(kz.data(), t1.data(), threads);
+            for (int64_t i = 0; i < N1; ++i) x[i] -= t1[i];
+        };
+        auto shifted = [&](const double* a, double* b) {   // (P2 + sigma M1) a
+            B.P2_matvec(a, b);
+            S.M1.matvec(a, t2.data(), threads);
+            for (int64_t i = 0; i < N1; ++i) b[i] += sigma * t2[i];
+        };
+        const int p = count + std::max(4, count / 2);
+        std::vector<double> X((size_t)N1 * p), Y((size_t)N1 * p), MY((size_t)N1 * p), PY((size_t)N1 * p);
+        uint64_t st = 0x9E3779B97F4A7C15ull;                // deterministic start block
+        for (auto& v : X) {
+            st = st * 6364136223846793005ull + 1442695040888963407ull;
+            v = (double)(st >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+        }
+        for (int j = 0; j < p; ++j) project(&X[(size_t)j * N1]);
+        std::vector<double> w, Z, H((size_t)p * p);
+        int it = 0;
+        bool done = false;
+        while (it < maxit && !done) {
+            ++it;
+            for (int j = 0; j < p; ++j) {
+                double* y = &Y[(size_t)j * N1];
+                S.M1.matvec(&X[(size_t)j * N1], t1.data(), threads);
+                std::vector<double> rhs(t1);
+                if (pcg(shifted, Ainv, rhs.data(), y, N1, 1e-12, 50000) < 0)
+                    throw std::runtime_error("cavity modes: the shifted solve did not converge");
+                project(y);
+            }
+            // M1-orthonormalise Y (Gram-Schmidt, twice)
+            for (int pass = 0; pass < 2; ++pass)
+                for (int j = 0; j < p; ++j) {
+                    double* y = &Y[(size_t)j * N1];
+                    for (int i = 0; i < j; ++i) {
+                        const double* mi = &MY[(size_t)i * N1];
+                        double c = 0;
+                        for (int64_t r = 0; r < N1; ++r) c += mi[r] * y[r];
+                        const double* yi = &Y[(size_t)i * N1];
+                        for (int64_t r = 0; r < N1; ++r) y[r] -= c * yi[r];
+                    }
+                    double* my = &MY[(size_t)j * N1];
+                    S.M1.matvec(y, my, threads);
+                    double nn = 0;
+                    for (int64_t r = 0; r < N1; ++r) nn += y[r] * my[r];
+                    nn = std::sqrt(nn);
+                    for (int64_t r = 0; r < N1; ++r) {
+                        y[r] /= nn;
+                        my[r] /= nn;
+                    }
+                }
+            // Rayleigh-Ritz with P2
+            for (int j = 0; j < p; ++j) B.P2_matvec(&Y[(size_t)j * N1], &PY[(size_t)j * N1]);
+            for (int a = 0; a < p; ++a)
+                for (int b2 = 0; b2 < p; ++b2) {
+                    double c = 0;
+                    for (int64_t r = 0; r < N1; ++r) c += Y[(size_t)a * N1 + r] * PY[(size_t)b2 * N1 + r];
+                    H[(size_t)a * p + b2] = c;
+                }
+            for (int a = 0; a < p; ++a)
+                for (int b2 = a + 1; b2 < p; ++b2) H[(size_t)a * p + b2] = H[(size_t)b2 * p + a] =
+                    0.5 * (H[(size_t)a * p + b2] + H[(size_t)b2 * p + a]);
+            jacobi_eigen(p, H, w, Z);
+            std::vector<int> ord(p);
+            for (int j = 0; j < p; ++j) ord[j] = j;
+            std::sort(ord.begin(), ord.end(), [&](int a, int b2) { return w[a] < w[b2]; });
+            double worst = 0;
+            for (int jj = 0; jj < p; ++jj) {
+                const int j = ord[jj];
+                double* x = &X[(size_t)jj * N1];
+                std::vector<double> px(N1, 0.0), mx(N1, 0.0);
+                for (int a = 0; a < p; ++a) {
+                    const double z = Z[(size_t)a * p + j];
+                    const double *ya = &Y[(size_t)a * N1], *pa = &PY[(size_t)a * N1], *ma = &MY[(size_t)a * N1];
+                    for (int64_t r = 0; r < N1; ++r) {
+                        px[r] += z * pa[r];
+                        mx[r] += z * ma[r];
+                    }
+                    if (a == 0)
+                        for (int64_t r = 0; r < N1; ++r) x[r] = z * ya[r];
+                    else
+                        for (int64_t r = 0; r < N1; ++r) x[r] += z * ya[r];
+                }
+                if (jj < count) {
+                    double rn = 0, mn = 0;
+                    for (int64_t r = 0; r < N1; ++r) {
+                        const double d = px[r] - w[j] * mx[r];
+                        rn += d * d;
+                        mn += mx[r] * mx[r];
+                    }
+                    worst = std::max(worst, std::sqrt(rn) / (std::fabs(w[j]) * std::sqrt(mn)));
+                    lam[jj] = w[j];
+                }
+            }
+            done = worst <= tol;
+        }
+        if (iters) *iters = it;
+        if (!done) {
+            S.err = "cavity modes: not converged within max_iter";
+            return -2;
+        }
+        std::copy(X.begin(), X.begin() + (size_t)count * N1, V);
+    } catch (const std::exception& ex) {
+        S.err = ex.what();
+        return -3;
+    }
+    return 0;
 }
 
 // ============================================================== sources and projections

@@ -150,6 +150,9 @@ int repack_q1(Setup& S, int threads);
 // Q1 unchanged), -3 (not SPD after the update).
 int spai_op(Setup& S, const double* V, int np, double lam, int maxit, double tol, int threads, int* iters,
             double* relres);
+// Lowest `count` non-kernel eigenpairs of P2 v = lambda M1 v (v^T M1 v = 1), V column-major N1 x count.
+// Returns 0, -1 (bad input), -2 (not converged), -3 (internal / inner solve failure).
+int cavity_modes(Setup& S, int count, double* V, double* lam, int maxit, double tol, int threads, int* iters);
 
 // Source vector of one dipole: tet index and the n1 weights d . Lambda1_i(x0) (global DoFs).
 int dipole_weights(const Setup& S, const double x[3], const double d[3], std::vector<int64_t>& dofs,

@@ -2148,6 +2148,16 @@ int ygm_spai_op(ygm_ctx* ctx, const double* V, int32_t n_probe, double lambda, i
     return YGM_OK;
 }
 
+int ygm_cavity_modes(ygm_ctx* ctx, int32_t count, double* V, double* omega_sq, int32_t max_iter, double tol,
+                     int32_t* iters) {
+    if (!ctx) return YGM_EINVAL;
+    int it = 0;
+    int rc = ygm::cavity_modes(ctx->S, count, V, omega_sq, max_iter, tol, 0, &it);
+    if (iters) *iters = it;
+    if (rc) return fail(ctx, rc == -1 ? YGM_EINVAL : rc == -2 ? YGM_ETIMEOUT : YGM_EINVAL, ctx->S.err);
+    return YGM_OK;
+}
+
 int ygm_step_noalloc(ygm_ctx* ctx, void* e, const void* b_in, void* b_out, double dt) {
     if (!ctx || !e || !b_in || !b_out) return fail(ctx, YGM_EINVAL, "NULL argument");
     const size_t need = (size_t)ctx->S.L.N1 * ctx->n_rhs * ctx->rs;

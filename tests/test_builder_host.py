@@ -159,3 +159,50 @@ def test_host_spai_op_orthogonal_basis_matches_oracle():
     assert abs(Qb - Qo).max() <= 1e-8 * abs(Qo).max()
     for j in range(V.shape[1]):
         assert OP.eig_residual(Qb, P2, V[:, j], w[j]) < 0.3 * OP.eig_residual(g.Q1, P2, V[:, j], w[j])
+
+
+@pytest.mark.parametrize("n,k,seed", [(3, 1, 5), (4, 1, None), (2, 2, 7)])
+def test_cavity_modes_match_dense_eigenpairs(n, k, seed):
+    """ygm_cavity_modes against a dense generalised eigensolver on the oracle's P2 and M1: the
+    lowest non-kernel eigenvalues (degenerate ones included, N=4 unit cube), M1-orthonormal
+    eigenvectors, and the same eigenspaces."""
+    import scipy.linalg as sl
+    f, g, eps, _ = oracle_model(n, k, eps_seed=seed)
+    M1 = f.M1()
+    P2 = (f.C().T @ f.M2() @ f.C()).tocsr()
+    w, V = sl.eigh(P2.toarray(), M1.toarray())
+    nz = np.where(w > 1e-8 * w[-1])[0][:5]
+    c = Y.Context(n, k, eps=eps, device=-1)
+    wb, Vb = c.cavity_modes(5, tol=1e-10)
+    assert np.allclose(wb, w[nz], rtol=1e-10)
+    Md = M1.toarray()
+    assert np.allclose(Vb.T @ Md @ Vb, np.eye(5), atol=1e-9)
+    assert np.linalg.norm(P2 @ Vb - (Md @ Vb) * wb) <= 1e-8 * wb.max() * np.linalg.norm(Md @ Vb)
+    # eigenspaces: every dense eigenvector of the (closed) cluster lies in the returned span
+    full = [i for i in range(len(w)) if w[i] > 1e-8 * w[-1] and w[i] <= wb[-1] * (1 + 1e-9)]
+    if len(full) == 5:
+        Pv = Vb @ (Vb.T @ Md)                          # M1-orthogonal projector onto span(Vb)
+        assert np.linalg.norm(Pv @ V[:, full] - V[:, full]) < 1e-7 * np.linalg.norm(V[:, full])
+
+
+def test_cavity_modes_as_spai_op_probes():
+    """The workflow of Sec. 5.1 through the C ABI only: compute probe modes, probe them with
+    SPAI-OP, and the probed residual eigenvalue errors fall well below the column SPAI's."""
+    from oracle import spai_op as OP
+    f, g, eps, _ = oracle_model(3, 1, eps_seed=5)
+    P2 = (f.C().T @ f.M2() @ f.C()).tocsr()
+    c = Y.Context(3, 1, eps=eps, device=-1)
+    w, V = c.cavity_modes(3)
+    c.spai_op(V, 1e3, tol=1e-12)
+    rp, ci, va = c.export_q1()
+    Q = sp.csr_matrix((va, ci, rp), shape=(c.N1, c.N1))
+    for j in range(3):
+        assert OP.eig_residual(Q, P2, V[:, j], w[j]) < 0.05 * OP.eig_residual(g.Q1, P2, V[:, j], w[j])
+
+
+def test_cavity_modes_reject_bad_counts():
+    c = Y.Context(2, 1, device=-1)
+    for bad in (0, c.N1):
+        with pytest.raises(Y.YgmError) as ei:
+            c.cavity_modes(bad)
+        assert ei.value.code == Y.YGM_EINVAL
