@@ -206,3 +206,17 @@ def test_cavity_modes_reject_bad_counts():
         with pytest.raises(Y.YgmError) as ei:
             c.cavity_modes(bad)
         assert ei.value.code == Y.YGM_EINVAL
+
+
+def test_option_validation_before_any_set_up():
+    """Bad options are refused by ygm_create before the operators are built (host-only)."""
+    for kw in (dict(n_rhs=3), dict(n_rhs=512), dict(n_rhs=0), dict(precision=7), dict(q1_pattern=9),
+               dict(energy_every=-1)):
+        with pytest.raises(Y.YgmError) as ei:
+            Y.Context(2, 1, device=-1, **kw)
+        assert ei.value.code == Y.YGM_EINVAL, kw
+    with pytest.raises(Y.YgmError) as ei:
+        Y.Context(2, 1, side=0.0, device=-1)
+    assert ei.value.code == Y.YGM_EINVAL
+    with pytest.raises(ValueError):
+        Y.Context(2, 1, eps=np.ones(47), device=-1)   # per-tet arrays must have 6 n^3 entries
