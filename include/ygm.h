@@ -135,8 +135,9 @@ int ygm_step(ygm_ctx* ctx, int64_t n, double dt, const ygm_source* src, int32_t 
 
 /* One leapfrog step on caller-owned device buffers, with no device allocation (no cudaMalloc,
  * cudaFree or allocating library call).  The paper has no counterpart: this entry point exists
- * for callers that cannot allocate device memory -- e.g. code running while a CUDA graph is
- * captured with allocation forbidden, or a process whose memory pool is reserved up front.
+ * for callers that cannot allocate device memory -- e.g. a process whose device memory is
+ * reserved up front by another allocator, or code under a latency budget that rules out
+ * cudaMalloc, which may synchronise the device.
  * State (e_n, b_{n-1/2}) in the context precision: x = Q1 e (into a fixed 16 MiB file-scope
  * device scratch array, not into context memory), b_out = b_in - dt C x, e += dt C^T M2 b_out.
  * No source term, no half steps, no energy recording; the context's own state is untouched.

@@ -1705,9 +1705,9 @@ static int launch_energy(ygm_ctx* ctx, const void* e, const void* x, const void*
 }
 
 // ====================================================================== no-allocation step
-// Callers that must not allocate device memory (code that runs while a CUDA graph is being
-// captured with allocation forbidden, in a process whose memory pool is reserved up front, or
-// under a real-time budget that rules out cudaMalloc latency) still need the Q1 e scratch
+// Callers that must not allocate device memory (a process whose device memory is reserved up
+// front by another allocator, or code under a real-time budget that rules out cudaMalloc and its
+// possible device synchronisation) still need the Q1 e scratch
 // vector of a leapfrog step.  It lives in this fixed, file-scope device array instead: every
 // GPU that loads the library holds these 16 MiB until the process exits.  Host code must not
 // pass the symbol itself to a kernel (on the host it is only a stand-in): its device address

@@ -1,5 +1,6 @@
 """GPU test of ygm_step_noalloc: the leapfrog step for callers that cannot allocate device memory
-(graph capture with allocation forbidden, pre-reserved memory pools).  It must give what the
+(device memory reserved up front by another allocator, latency budgets that rule out
+cudaMalloc).  It must give what the
 regular entry point gives, on two calls in a row, and reject contexts beyond its fixed scratch.
 This file is collected last on purpose."""
 import numpy as np
