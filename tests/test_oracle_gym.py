@@ -1,6 +1,6 @@
 """Pins of the oracle's time stepping: Theorem symplecticity, Eq. eigenvaluePairs, Prop. stability,
-the exactly conserved discrete energy, Gauss' law, the (a, e) / (b, e) equivalence and the
-source work identity."""
+the exactly conserved discrete energy, the tau^2 scaling of the modified Hamiltonian's
+oscillation (Sec. 7.5), Gauss' law, the (a, e) / (b, e) equivalence and the source work identity."""
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -165,3 +165,33 @@ def test_source_work_identity_and_linearity():
     J2 = DipoleSource(f, [dict(src[0], amp=2.0)], tau)
     e2, b2, _ = g.run(np.zeros(f.mesh.N1), np.zeros(f.mesh.N2), tau, 60, source=J2)
     assert np.allclose(e2, 2 * e, rtol=1e-12, atol=1e-14)
+
+
+def test_modified_hamiltonian_oscillation_scales_with_dt_squared():
+    """Sec. 7.5: H~ = e^T Q1 e / 2 + b^T M2 b / 2 oscillates without secular drift, with an amplitude
+    of order tau^2 omega_max^2.  Halving tau must divide the amplitude by ~4, and the deviation over
+    the second half of the run must not exceed the first half's."""
+    f = FEM(KuhnMesh(4, 1))
+    M1 = f.M1()
+    Q, _ = SP.gym_q1(f, M1)
+    g = GYM(f.C(), f.M2(), Q, M1)
+    E0 = lambda x: np.stack([0 * x[:, 0], 0 * x[:, 0], np.sin(np.pi * x[:, 0]) * np.sin(np.pi * x[:, 1])], axis=1)
+    e0 = M1 @ f.edge_interpolant(E0)
+    T = 6 * 2 * np.pi / (np.pi * np.sqrt(2.0))          # six periods of the (1,1,0) mode
+
+    def deviation(tau):
+        n = int(round(T / tau))
+        e, b = e0.copy(), g.half_init(e0, np.zeros(f.mesh.N2), tau)
+        H0 = g.H_tilde(e0, np.zeros(f.mesh.N2))
+        dev = []
+        for _ in range(n):
+            e, b, _, _ = g.step(e, b, tau)
+            dev.append(abs(g.H_tilde(e, g.sync(e, b, tau)) - H0) / H0)
+        dev = np.array(dev)
+        return dev.max(), dev[: n // 2].max(), dev[n // 2:].max()
+
+    tau = 0.2 * g.tau_cfl()
+    a1, h1, h2 = deviation(tau)
+    a2, _, _ = deviation(tau / 2)
+    assert 3.4 < a1 / a2 < 4.6
+    assert h2 <= 1.05 * h1
