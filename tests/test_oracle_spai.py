@@ -128,6 +128,8 @@ def test_dispersion_diagonal_spai_matches_yee_row():
     wp, dev = _TABLE["diagonal_yee"]
     assert abs(w / wp - 1) < 1e-4 and abs(wt / wp - 1) < 3e-4
     assert abs((w - w0) / w0 - dev) < 5e-4
+    # Sec. 7.6: after 200 periods the Yee-like run is ~29 periods ahead of the exact mode
+    assert round(200 * (wt - w0) / w0) == 29
 
 
 def test_dispersion_spai_sm1_matches_printed_value():
@@ -136,6 +138,8 @@ def test_dispersion_spai_sm1_matches_printed_value():
     wp, dev = _TABLE["spai_sm1"]
     assert abs(wt / wp - 1) < 3e-4 and abs(w / wp - 1) < 3e-4
     assert abs((wt - w0) / w0 - dev) < 5e-4
+    # Sec. 7.6: and the SPAI run ~8 periods behind
+    assert round(200 * (wt - w0) / w0) == -8
 
 
 # ---------------------------------------------------------------- Table SPAIOPeigTable, SPAI rows
