@@ -1481,7 +1481,7 @@ static int setup_device(ygm_ctx* ctx) {
     const size_t smem_q = (size_t)ctx->max_slots * (2 * sizeof(long long) + 8 * sizeof(int));
     const size_t smem_e = (size_t)ctx->max_terms * sizeof(long long) + (size_t)(ctx->max_terms + 1) * ctx->rs +
                           (size_t)ctx->max_terms * 6 * sizeof(int);
-    if (smem_q > 227 * 1024 || smem_e > 227 * 1024 || (size_t)(ctx->max_ns + 8) * sizeof(int2) > 48 * 1024)
+    if (smem_q > 227 * 1024 || smem_e > 227 * 1024 || (size_t)ctx->max_ns * sizeof(int) > 48 * 1024)
         return fail(ctx, YGM_EINVAL, "stencil too wide for shared memory");
     // raise-only: the limit is process-wide per kernel, shared by every context (a smaller value
     // set by one context would make another context's launches invalid)
