@@ -16,6 +16,8 @@ The oracle is a plain, slow, obviously-correct restatement of the paper:
                followed by symmetrisation (Sec. 5)
   spai_op.py   operator-probed SPAI: the symmetric Sylvester system of
                Eq. SPAIOPSylvester solved by diagonally preconditioned CG (Sec. 5.1)
+  adjoint.py   reverse sweep of the leapfrog and the eps-derivative of the column
+               SPAI: gradient of a probe-region field energy (order 1)
   gym.py       shear maps / Strang splitting (Eqs. shearMaps, strangSplit),
                the (b, e) leapfrog (Eq. preYeeFEECEqns, Eq. YeeLeapfrog),
                energies, CFL bound (Prop. stability), dipole source
