@@ -216,6 +216,17 @@ int ygm_spai_op(ygm_ctx* ctx, const double* V, int32_t n_probe, double lambda, i
 int ygm_cavity_modes(ygm_ctx* ctx, int32_t count, double* V, double* omega_sq, int32_t max_iter, double tol,
                      int32_t* iters);
 
+/* Derivative of the column SPAI with respect to the per-tet permittivity (Eq. NormalEqSolve,
+ * differentiated): given q1bar = dL/dQ1 for some scalar L, on the pattern of ygm_export_q1 (same
+ * CSR order), returns grad_eps[t] = sum_ij q1bar_ij dQ1_ij / d eps_t for the 6 n^3 tets.
+ * Q1 = (P + P^T) / 2 with P the column SPAI of M1(eps) = sum_T eps_T M1^T; per column l,
+ * dq = (A^T A)^-1 (dA^T r - A^T dA q) with A = M1(:, I_l), r = 1_l - A q, dA = M1^T(:, I_l).
+ * Dependences of L on eps other than through Q1 (e.g. an M1-weighted loss) are the caller's.
+ * Host FP64, reproducible for a given thread count.  Available for order 1 with the column SPAI
+ * (ygm_q1_info ortho = 0); Q1 from ygm_set_q1 or ygm_spai_op is treated as if it were the column
+ * SPAI, which it is not.  Errors: YGM_EINVAL, YGM_ENOTSPD. */
+int ygm_q1_vjp(ygm_ctx* ctx, const double* q1bar, double* grad_eps);
+
 /* SPD check of Q1 (Sec. 5.1, practical considerations): Lanczos estimates of the smallest and
  * largest eigenvalue before any shift, the diagonal shift applied (0 if none), lambda_max(Q1 P2),
  * and which pattern / basis was used (YGM_Q1_*, ortho = 1 for the orthogonalised basis). */

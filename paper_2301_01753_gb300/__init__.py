@@ -18,7 +18,7 @@ YGM_FP64, YGM_FP32 = 0, 1
 YGM_Q1_DEFAULT, YGM_Q1_DIAG, YGM_Q1_SM1, YGM_Q1_SM1SQ = 0, 1, 2, 3
 
 EXPORTED = ["ygm_create", "ygm_create_like", "ygm_sizes", "ygm_set_state", "ygm_get_state", "ygm_project_E", "ygm_step", "ygm_step_noalloc",
-            "ygm_energy", "ygm_energy_history", "ygm_time", "ygm_export_q1", "ygm_set_q1", "ygm_spai_op", "ygm_cavity_modes", "ygm_q1_info",
+            "ygm_energy", "ygm_energy_history", "ygm_time", "ygm_export_q1", "ygm_set_q1", "ygm_spai_op", "ygm_cavity_modes", "ygm_q1_vjp", "ygm_q1_info",
             "ygm_local_blocks", "ygm_kernel_timing", "ygm_kernel_times", "ygm_launch_count",
             "ygm_qapply_counts", "ygm_last_error", "ygm_destroy"]
 KERNEL_KINDS = ["k_qapply", "k_curl_b", "k_curlT_e", "k_source", "k_energy"]
@@ -71,6 +71,7 @@ def load_library(path=LIB_PATH):
         "ygm_set_q1": (C.c_int, [P, pI64, pI64, pD]),
         "ygm_spai_op": (C.c_int, [P, pD, C.c_int32, D, C.c_int32, D, pI32, pD]),
         "ygm_cavity_modes": (C.c_int, [P, C.c_int32, pD, pD, C.c_int32, D, pI32]),
+        "ygm_q1_vjp": (C.c_int, [P, pD, pD]),
         "ygm_q1_info": (C.c_int, [P, pD, pD, pD, pD, pI32, pI32]),
         "ygm_local_blocks": (C.c_int, [P, pI32, pI32, pD, pD]),
         "ygm_kernel_timing": (C.c_int, [P, C.c_int]),
@@ -277,6 +278,16 @@ class Context:
                                           w.ctypes.data_as(C.POINTER(C.c_double)), int(max_iter), float(tol),
                                           C.byref(it)))
         return w, V.T.copy()
+
+    def q1_vjp(self, q1bar):
+        """dL/d eps per tet through Q1, given dL/dQ1 on the ygm_export_q1 pattern (ygm_q1_vjp)."""
+        qb = np.ascontiguousarray(q1bar, dtype=np.float64)
+        if qb.shape != (self.q1_nnz,):
+            raise ValueError(f"q1bar must hold the {self.q1_nnz} stored entries of Q1")
+        g = np.empty(6 * self.n ** 3, dtype=np.float64)
+        self._check(_lib.ygm_q1_vjp(self._h, qb.ctypes.data_as(C.POINTER(C.c_double)),
+                                    g.ctypes.data_as(C.POINTER(C.c_double))))
+        return g
 
     def q1_info(self):
         lmin, lmax, sh, w2 = C.c_double(), C.c_double(), C.c_double(), C.c_double()

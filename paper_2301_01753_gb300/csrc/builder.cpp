@@ -1875,6 +1875,144 @@ int cavity_modes(Setup& S, int count, double* V, double* lam, int maxit, double 
     return 0;
 }
 
+// ============================================================== Q1 vector-Jacobian product in eps
+// dL/d eps_T through Q1 (order 1): Q1 = (P + P^T) / 2, P the column SPAI of Eq. NormalEqSolve, so
+// with Pbar = (Q1bar + Q1bar^T) / 2 on the pattern, per column l (A = M1(:, I_l), I_l the pattern):
+//   q = (A^T A)^-1 A^T 1_l,  r = 1_l - A q,  z = (A^T A)^-1 Pbar(I_l, l),
+//   dL/d eps_T += (dA z)^T r - (A z)^T (dA q),   dA = M1^T(:, I_l) (the element matrix of tet T).
+// Columns are split into one fixed contiguous range per thread and summed in a fixed order, so the
+// result is reproducible for a given thread count.
+int q1_vjp(const Setup& S, const double* q1bar, double* grad, int threads_in) {
+    const Lattice& L = S.L;
+    if (S.ortho) return -1;
+    const int64_t N1 = L.N1, T = 6LL * L.n * L.n * L.n;
+    const Csr& Q = S.Q1;
+    const Csr& M = S.M1;
+    const int n1 = L.n1;
+    // local DoFs of every tet and the tets of every DoF
+    std::vector<int64_t> tdofs((size_t)T * n1);
+    for (int64_t t = 0; t < T; ++t) L.tet_dofs1(t, &tdofs[(size_t)t * n1]);
+    std::vector<int64_t> tptr(N1 + 1, 0), tlist;
+    for (int64_t t = 0; t < T; ++t)
+        for (int a = 0; a < n1; ++a)
+            if (tdofs[(size_t)t * n1 + a] >= 0) ++tptr[tdofs[(size_t)t * n1 + a] + 1];
+    for (int64_t i = 0; i < N1; ++i) tptr[i + 1] += tptr[i];
+    tlist.resize(tptr[N1]);
+    {
+        std::vector<int64_t> fill(tptr.begin(), tptr.end() - 1);
+        for (int64_t t = 0; t < T; ++t)
+            for (int a = 0; a < n1; ++a) {
+                const int64_t g = tdofs[(size_t)t * n1 + a];
+                if (g >= 0) tlist[fill[g]++] = t;
+            }
+    }
+    // Pbar on the Q1 pattern (transpose positions by binary search; the pattern is symmetric)
+    const int64_t nq = Q.ptr[N1];
+    std::vector<double> pbar(nq);
+    for (int64_t i = 0; i < N1; ++i)
+        for (int64_t k = Q.ptr[i]; k < Q.ptr[i + 1]; ++k) {
+            const int64_t j = Q.col[k];
+            const auto b = Q.col.begin() + Q.ptr[j], e = Q.col.begin() + Q.ptr[j + 1];
+            const auto it = std::lower_bound(b, e, i);
+            if (it == e || *it != i) return -1;
+            pbar[k] = 0.5 * (q1bar[k] + q1bar[it - Q.col.begin()]);
+        }
+    const Csr U = spgemm(M, M, 1);     // A^T A = (M1 M1)(I, I) for symmetric M1
+    const int threads = std::max(1, std::min<int>(default_threads(threads_in), (int)std::max<int64_t>(1, N1 / 64)));
+    std::vector<std::vector<double>> part(threads, std::vector<double>(T, 0.0));
+    std::atomic<bool> bad(false);
+    auto work = [&](int th) {
+        const int64_t l0 = N1 * th / threads, l1 = N1 * (th + 1) / threads;
+        std::vector<int32_t> mk(N1, -1);
+        std::vector<double> r(N1, 0.0), az(N1, 0.0), G, rhs;
+        std::vector<int64_t> rows;
+        std::vector<char> rowseen(N1, 0), tseen(T, 0);
+        std::vector<int64_t> tets;
+        std::vector<double> zT(n1), qT(n1), mz(n1), mq(n1);
+        auto& gpart = part[th];
+        for (int64_t l = l0; l < l1; ++l) {
+            const int64_t* I = &Q.col[Q.ptr[l]];
+            const int m = (int)(Q.ptr[l + 1] - Q.ptr[l]);
+            for (int p = 0; p < m; ++p) mk[I[p]] = p;
+            G.assign((size_t)m * m, 0.0);
+            for (int p = 0; p < m; ++p)
+                for (int64_t a = U.ptr[I[p]]; a < U.ptr[I[p] + 1]; ++a) {
+                    const int32_t pb = mk[U.col[a]];
+                    if (pb >= 0) G[(size_t)p * m + pb] = U.val[a];
+                }
+            rhs.assign((size_t)2 * m, 0.0);
+            for (int64_t a = M.ptr[l]; a < M.ptr[l + 1]; ++a)
+                if (mk[M.col[a]] >= 0) rhs[mk[M.col[a]]] = M.val[a];
+            for (int p = 0; p < m; ++p) rhs[m + p] = pbar[Q.ptr[l] + p];
+            if (!cholesky_solve(m, G.data(), rhs.data(), 2)) {
+                bad = true;
+                break;
+            }
+            const double* q = rhs.data();
+            const double* z = rhs.data() + m;
+            // r = 1_l - A q and A z on the rows of A (column I_p of M1 = its row I_p)
+            rows.clear();
+            for (int p = 0; p < m; ++p)
+                for (int64_t a = M.ptr[I[p]]; a < M.ptr[I[p] + 1]; ++a) {
+                    const int64_t row = M.col[a];
+                    if (!rowseen[row]) {
+                        rowseen[row] = 1;
+                        rows.push_back(row);
+                    }
+                    r[row] -= M.val[a] * q[p];
+                    az[row] += M.val[a] * z[p];
+                }
+            r[l] += 1.0;
+            // tets holding a DoF of I_l
+            tets.clear();
+            for (int p = 0; p < m; ++p)
+                for (int64_t a = tptr[I[p]]; a < tptr[I[p] + 1]; ++a)
+                    if (!tseen[tlist[a]]) {
+                        tseen[tlist[a]] = 1;
+                        tets.push_back(tlist[a]);
+                    }
+            std::sort(tets.begin(), tets.end());
+            for (int64_t t : tets) {
+                const int64_t* D = &tdofs[(size_t)t * n1];
+                for (int a = 0; a < n1; ++a) {
+                    const int32_t pos = D[a] >= 0 ? mk[D[a]] : -1;
+                    zT[a] = pos >= 0 ? z[pos] : 0.0;
+                    qT[a] = pos >= 0 ? q[pos] : 0.0;
+                }
+                double c = 0.0;
+                for (int b = 0; b < n1; ++b) {
+                    if (D[b] < 0) continue;
+                    double sz = 0, sq = 0;
+                    for (int a = 0; a < n1; ++a) {
+                        sz += S.M1loc[(size_t)b * n1 + a] * zT[a];
+                        sq += S.M1loc[(size_t)b * n1 + a] * qT[a];
+                    }
+                    c += sz * r[D[b]] - az[D[b]] * sq;
+                }
+                gpart[t] += c;
+                tseen[t] = 0;
+            }
+            for (int64_t row : rows) {
+                rowseen[row] = 0;
+                r[row] = 0.0;
+                az[row] = 0.0;
+            }
+            r[l] = 0.0;
+            for (int p = 0; p < m; ++p) mk[I[p]] = -1;
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int th = 0; th < threads; ++th) pool.emplace_back(work, th);
+    for (auto& th : pool) th.join();
+    if (bad) return -3;
+    for (int64_t t = 0; t < T; ++t) {
+        double s = 0;
+        for (int th = 0; th < threads; ++th) s += part[th][t];
+        grad[t] = s;
+    }
+    return 0;
+}
+
 // ============================================================== sources and projections
 // Gauss-Legendre nodes and weights on [-1, 1] by Newton iteration on P_n (Golub-Welsch not needed
 // for the small orders used here).

@@ -220,3 +220,32 @@ def test_option_validation_before_any_set_up():
     assert ei.value.code == Y.YGM_EINVAL
     with pytest.raises(ValueError):
         Y.Context(2, 1, eps=np.ones(47), device=-1)   # per-tet arrays must have 6 n^3 entries
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_q1_vjp_matches_the_oracle_spai_derivative(n):
+    """ygm_q1_vjp (the differentiated normal equations) against oracle.adjoint.spai_vjp, for a
+    random dL/dQ1 on the pattern (order 1, random eps)."""
+    from oracle import adjoint as AD
+    from oracle import spai as SP
+    from oracle.fem import FEM
+    from oracle.mesh import KuhnMesh
+    eps = synth.tet_eps(5002, n, 1.0, 4.0)
+    f = FEM(KuhnMesh(n, 1), eps=eps)
+    c = Y.Context(n, 1, eps=eps, device=-1)
+    rp, ci, va = c.export_q1()
+    rng = np.random.default_rng(n)
+    qbar = rng.standard_normal(len(va))
+    g = c.q1_vjp(qbar)
+    Qbar = sp.csr_matrix((qbar, ci, rp), shape=(c.N1, c.N1)).toarray()
+    S = SP.pattern("sm1", f.M1(), f.dof1)
+    go = AD.spai_vjp(f, S, 0.5 * (Qbar + Qbar.T) * (S.toarray() != 0))
+    assert np.allclose(g, go, rtol=1e-9, atol=1e-11 * np.abs(go).max())
+    assert np.array_equal(g, c.q1_vjp(qbar))                  # reproducible
+
+
+def test_q1_vjp_refuses_the_orthogonalised_basis():
+    c = Y.Context(2, 2, device=-1)
+    with pytest.raises(Y.YgmError) as ei:
+        c.q1_vjp(np.zeros(c.q1_nnz))
+    assert ei.value.code == Y.YGM_EINVAL
