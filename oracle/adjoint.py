@@ -1,5 +1,6 @@
 """Discrete adjoint of the GYM leapfrog: gradient of a probe-region field energy with respect to
-the per-tet permittivity (order 1, column SPAI on S(M1)).
+the per-tet permittivity, through the Q1 policy of each order (order 1: column SPAI on S(M1);
+orders >= 2: the entity-orthonormal S(M1^2) SPAI of reading R2, see the second block below).
 
 Oracle (test infrastructure; see oracle/__init__.py).  Plain, dense, for tiny meshes.
 
@@ -125,6 +126,98 @@ def loss_and_gradient(make_fem, eps, region, source, tau, nsteps):
     Sd = S.toarray() != 0
     Pbar = 0.5 * (Qbar + Qbar.T) * Sd
     grad = spai_vjp(fem, S, Pbar)
+    for t in np.nonzero(region)[0]:
+        grad[t] += np.sum(MRbar * element_M1(fem, t))
+    return L, grad
+
+
+# ----------------------------------------------------------------------------
+# Orders >= 2: Q1 = T Q' T in the entity-orthonormal basis (reading R2 of the column SPAI)
+#   T = blockdiag_g (M1[g, g])^(-1/2),  M' = T M1 T,  Q' = (P' + P'^T) / 2,  P' = SPAI(M') on S.
+# Reverse mode, T and Q' symmetric:
+#   Q'bar = T Q1bar T,                      Tbar  = Q1bar T Q' + Q' T Q1bar
+#   P'bar = (Q'bar + Q'bar^T) / 2 on S,     M'bar = sum_l [r z^T - (A z) q^T] in the columns I_l
+#   M1bar = T M'bar T,                      Tbar += M'bar T M1 + M1 T M'bar
+#   M1bar[g, g] += V (Gamma o (V^T Tbar[g, g] V)) V^T  (derivative of A^(-1/2), A = M1[g, g] = V w V^T,
+#                  Gamma_ij = (w_i^-1/2 - w_j^-1/2) / (w_i - w_j), or -w_i^-3/2 / 2 when w_i = w_j)
+#   dL/d eps_T = sum_ij M1bar_ij (M1^T)_ij
+# ----------------------------------------------------------------------------
+def _groups(fem):
+    e, f, c = SP.entity_groups(fem)
+    return [list(g) for g in e + f + c]
+
+
+def q1_ortho_of(fem, S):
+    """Q1 of the k >= 2 policy, dense (the same steps as oracle.spai.gym_q1 with the ortho basis)."""
+    M1 = fem.M1()
+    T = SP.ortho_basis_transform(fem, M1)
+    Mp = (T @ M1 @ T.T).tocsr()
+    return SP.symmetrize((T.T @ SP.symmetrize(SP.spai_columns(Mp, S)) @ T).tocsr()).toarray()
+
+
+def spai_vjp_matrix(M, S, Pbar):
+    """dL/dM (dense, all entries) of the column SPAI P = SPAI(M) for a given Pbar on S."""
+    S = sp.csc_matrix(S)
+    N = M.shape[0]
+    Mbar = np.zeros((N, N))
+    for l in range(N):
+        I = S.indices[S.indptr[l]:S.indptr[l + 1]]
+        A = M[:, I]
+        AtA = A.T @ A
+        one = np.zeros(N)
+        one[l] = 1.0
+        q = np.linalg.solve(AtA, A.T @ one)
+        r = one - A @ q
+        z = np.linalg.solve(AtA, Pbar[I, l])
+        Mbar[:, I] += np.outer(r, z) - np.outer(A @ z, q)
+    return Mbar
+
+
+def q1_ortho_vjp(fem, S, Q1bar):
+    """dL/d eps per tet through the k >= 2 Q1 (see the block comment above)."""
+    M1 = fem.M1().toarray()
+    N = M1.shape[0]
+    groups = _groups(fem)
+    T = np.zeros((N, N))
+    eig = []
+    for g in groups:
+        w, V = np.linalg.eigh(M1[np.ix_(g, g)])
+        T[np.ix_(g, g)] = (V / np.sqrt(w)) @ V.T
+        eig.append((w, V))
+    Mp = T @ M1 @ T
+    Pp = SP.spai_columns(sp.csr_matrix(Mp), S).toarray()
+    Qp = 0.5 * (Pp + Pp.T)
+    Sd = sp.csr_matrix(S).toarray() != 0
+    Qpbar = T @ Q1bar @ T
+    Tbar = Q1bar @ T @ Qp + Qp @ T @ Q1bar
+    Ppbar = 0.5 * (Qpbar + Qpbar.T) * Sd
+    Mpbar = spai_vjp_matrix(Mp, S, Ppbar)
+    M1bar = T @ Mpbar @ T
+    Tbar += Mpbar @ T @ M1 + M1 @ T @ Mpbar
+    for g, (w, V) in zip(groups, eig):
+        f = w ** -0.5
+        dw = w[:, None] - w[None, :]
+        same = np.abs(dw) <= 1e-12 * np.abs(w).max()
+        Gam = np.where(same, -0.5 * w[:, None] ** -1.5, (f[:, None] - f[None, :]) / np.where(same, 1.0, dw))
+        M1bar[np.ix_(g, g)] += V @ (Gam * (V.T @ Tbar[np.ix_(g, g)] @ V)) @ V.T
+    return np.array([np.sum(M1bar * element_M1(fem, t)) for t in range(fem.mesh.n_tets)])
+
+
+def loss_and_gradient_policy(make_fem, eps, region, source, tau, nsteps):
+    """loss_and_gradient under the Q1 policy of the order: the column SPAI on S(M1) at k = 1, the
+    entity-orthonormal S(M1^2) SPAI at k >= 2."""
+    fem = make_fem(eps)
+    if fem.mesh.k == 1:
+        return loss_and_gradient(make_fem, eps, region, source, tau, nsteps)
+    S = SP.pattern("sm1sq", fem.M1(), fem.dof1)
+    Q = q1_ortho_of(fem, S)
+    C, M2 = fem.C().toarray(), fem.M2().toarray()
+    MR1, MR2 = region_mass(fem, region)
+    J = source(fem)
+    L, es, xs, bs = forward(C, M2, Q, MR1, MR2, J, tau, nsteps)
+    Qbar, MRbar = reverse(C, M2, Q, MR1, MR2, tau, es, xs, bs)
+    Qbar = Qbar * (S.toarray() != 0)              # T Q' T vanishes off S for every eps (S is entity-closed)
+    grad = q1_ortho_vjp(fem, S, Qbar)
     for t in np.nonzero(region)[0]:
         grad[t] += np.sum(MRbar * element_M1(fem, t))
     return L, grad

@@ -72,3 +72,33 @@ def test_spai_term_is_needed_outside_the_region():
     make, eps0, region, source, tau = _problem()
     _, grad = AD.loss_and_gradient(make, eps0, region, source, tau, STEPS)
     assert np.max(np.abs(grad[~region])) > 1e-2 * np.max(np.abs(grad))
+
+
+def test_order2_gradient_through_the_orthonormal_basis():
+    """k = 2: Q1 = T Q' T with T = blockdiag (M1[g,g])^(-1/2) depending on eps as well (reading R2);
+    the chained gradient against central differences (h = 1e-4 relative: smaller steps drown in the
+    rounding of the recomputed SPAI, larger ones in truncation)."""
+    n, k, steps = 2, 2, 30
+    eps0 = synth.tet_eps(5003, n, 1.0, 4.0)
+    make = lambda eps: FEM(KuhnMesh(n, k), eps=eps)
+    f0 = make(eps0)
+    region = np.all(f0.mesh.tet_vx.mean(axis=1) < 0.5, axis=1)
+    M1 = f0.M1()
+    Q, _ = SP.gym_q1(f0, M1)
+    tau = 0.5 * GYM(f0.C(), f0.M2(), Q, M1).tau_cfl()
+    src = [dict(x=np.array([0.41, 0.52, 0.47]), d=np.array([0.3, 0.2, 1.0]), amp=1.0,
+                omega=np.pi * np.sqrt(5.0), width_steps=5.0)]
+
+    def source(fem):
+        J = DipoleSource(fem, src, tau)
+        return [J((m + 0.5) * tau) for m in range(steps)]
+    L, grad = AD.loss_and_gradient_policy(make, eps0, region, source, tau, steps)
+    assert np.allclose(AD.q1_ortho_of(f0, SP.pattern("sm1sq", M1, f0.dof1)), Q.toarray(), rtol=0, atol=1e-12 * abs(Q).max())
+    for t in (0, 3, 7, 20, 40, 47):
+        h = 1e-4 * eps0[t]
+        ep, em = eps0.copy(), eps0.copy()
+        ep[t] += h
+        em[t] -= h
+        fd = (AD.loss_and_gradient_policy(make, ep, region, source, tau, steps)[0]
+              - AD.loss_and_gradient_policy(make, em, region, source, tau, steps)[0]) / (2 * h)
+        assert abs(grad[t] - fd) <= 1e-6 * np.max(np.abs(grad)), (t, grad[t], fd)
