@@ -222,9 +222,11 @@ int ygm_cavity_modes(ygm_ctx* ctx, int32_t count, double* V, double* omega_sq, i
  * Q1 = (P + P^T) / 2 with P the column SPAI of M1(eps) = sum_T eps_T M1^T; per column l,
  * dq = (A^T A)^-1 (dA^T r - A^T dA q) with A = M1(:, I_l), r = 1_l - A q, dA = M1^T(:, I_l).
  * Dependences of L on eps other than through Q1 (e.g. an M1-weighted loss) are the caller's.
- * Host FP64, reproducible for a given thread count.  Available for order 1 with the column SPAI
- * (ygm_q1_info ortho = 0); Q1 from ygm_set_q1 or ygm_spai_op is treated as if it were the column
- * SPAI, which it is not.  Errors: YGM_EINVAL, YGM_ENOTSPD. */
+ * Orders >= 2 (ygm_q1_info ortho = 1) chain through the entity-orthonormal basis as well:
+ * Q1 = T Q' T, Q' the column SPAI of M' = T M1 T, T = blockdiag (M1[g,g])^(-1/2) over the mesh
+ * entities, its derivative taken in each block's eigenbasis.  Host FP64, reproducible for a given
+ * thread count.  Q1 from ygm_set_q1 or ygm_spai_op is treated as if it were the column SPAI, which
+ * it is not.  Errors: YGM_EINVAL, YGM_ENOTSPD. */
 int ygm_q1_vjp(ygm_ctx* ctx, const double* q1bar, double* grad_eps);
 
 /* SPD check of Q1 (Sec. 5.1, practical considerations): Lanczos estimates of the smallest and

@@ -1882,9 +1882,8 @@ int cavity_modes(Setup& S, int count, double* V, double* lam, int maxit, double 
 //   dL/d eps_T += (dA z)^T r - (A z)^T (dA q),   dA = M1^T(:, I_l) (the element matrix of tet T).
 // Columns are split into one fixed contiguous range per thread and summed in a fixed order, so the
 // result is reproducible for a given thread count.
-int q1_vjp(const Setup& S, const double* q1bar, double* grad, int threads_in) {
+static int q1_vjp_plain(const Setup& S, const double* q1bar, double* grad, int threads_in) {
     const Lattice& L = S.L;
-    if (S.ortho) return -1;
     const int64_t N1 = L.N1, T = 6LL * L.n * L.n * L.n;
     const Csr& Q = S.Q1;
     const Csr& M = S.M1;
@@ -2011,6 +2010,326 @@ int q1_vjp(const Setup& S, const double* q1bar, double* grad, int threads_in) {
         grad[t] = s;
     }
     return 0;
+}
+
+// ---- orders >= 2: Q1 = T Q' T in the entity-orthonormal basis (T = blockdiag M1[g,g]^-1/2)
+// Reverse mode (T, Q' symmetric):
+//   Q'bar = T Q1bar T, P'bar = (Q'bar + Q'bar^T) / 2 on S,   Tbar  = Q1bar T Q' + Q' T Q1bar
+//   column SPAI of M' = T M1 T:  M'bar = sum_l [r z^T - (A z) q^T] in the columns I_l
+//   dL/d eps_t += <M'bar, T M1^t T>  (from M1bar = T M'bar T),   Tbar += M'bar T M1 + M1 T M'bar
+//   M1bar[g,g] += V (Gamma o (V^T Tbar[g,g] V)) V^T  (A^-1/2 differentiated in the eigenbasis of
+//   A = M1[g,g]; Gamma_ij = divided differences of w^-1/2), dL/d eps_t += <M1bar[g,g], M1^t[g,g]>.
+// Only the diagonal blocks of Tbar are formed (T is block diagonal), from sparse row dot products
+// and per-column accumulations, so no product wider than the Q1 pattern is stored.
+static double row_dot(const Csr& A, int64_t i, const Csr& B, int64_t j) {
+    int64_t p = A.ptr[i], pe = A.ptr[i + 1], q = B.ptr[j], qe = B.ptr[j + 1];
+    double s = 0;
+    while (p < pe && q < qe) {
+        if (A.col[p] < B.col[q])
+            ++p;
+        else if (A.col[p] > B.col[q])
+            ++q;
+        else
+            s += A.val[p++] * B.val[q++];
+    }
+    return s;
+}
+
+static int q1_vjp_ortho(Setup& S, const double* q1bar, double* grad, int threads_in) {
+    const Lattice& L = S.L;
+    const int64_t N1 = L.N1, T = 6LL * L.n * L.n * L.n;
+    const int n1 = L.n1;
+    const int nthr = default_threads(threads_in);
+    Builder B(S, nthr);
+    const Csr Tm = B.ortho_T(-0.5), Ti = B.ortho_T(0.5);
+    const Csr& Q1 = S.Q1;
+    const Csr& M1 = S.M1;
+    // groups: the columns of a row of T are the DoFs of its entity
+    std::vector<int64_t> gid(N1, -1), gstart;
+    std::vector<int64_t> gdofs;
+    for (int64_t i = 0; i < N1; ++i) {
+        if (gid[i] >= 0) continue;
+        const int64_t g = (int64_t)gstart.size();
+        gstart.push_back((int64_t)gdofs.size());
+        for (int64_t k = Tm.ptr[i]; k < Tm.ptr[i + 1]; ++k) {
+            gid[Tm.col[k]] = g;
+            gdofs.push_back(Tm.col[k]);
+        }
+    }
+    const int64_t ng = (int64_t)gstart.size();
+    gstart.push_back((int64_t)gdofs.size());
+    std::vector<int64_t> boff(ng + 1, 0);     // Tbar block storage offsets (|g|^2 each)
+    for (int64_t g = 0; g < ng; ++g) {
+        const int64_t m = gstart[g + 1] - gstart[g];
+        boff[g + 1] = boff[g] + m * m;
+    }
+    auto gpos = [&](int64_t dof) {         // position of a DoF inside its group
+        const int64_t g = gid[dof];
+        for (int64_t k = gstart[g]; k < gstart[g + 1]; ++k)
+            if (gdofs[k] == dof) return (int)(k - gstart[g]);
+        return -1;
+    };
+    std::vector<int> posv(N1);
+    for (int64_t i = 0; i < N1; ++i) posv[i] = gpos(i);
+    // Q1bar as a CSR on the Q1 pattern, its transpose, M' = T M1 T, Q' = T^-1 Q1 T^-1, X = T Q'
+    Csr Qb = Q1;
+    std::copy(q1bar, q1bar + Q1.ptr[N1], Qb.val.begin());
+    const Csr QbT = transpose(Qb);
+    const Csr Mp = spgemm(spgemm(Tm, M1, nthr), Tm, nthr);
+    const Csr Qp = spgemm(spgemm(Ti, Q1, nthr), Ti, nthr);
+    const Csr X = spgemm(Tm, Qp, nthr), XT = transpose(X);
+    const Csr Y = spgemm(Tm, M1, nthr), YT = transpose(Y);
+    const Csr Up = spgemm(Mp, Mp, nthr);
+    // P'bar on the pattern of Q' (= S): Q'bar = T Q1bar T, symmetrised
+    const Csr QpbarM = spgemm(spgemm(Tm, Qb, nthr), Tm, nthr);
+    const int64_t nq = Qp.ptr[N1];
+    std::vector<double> pbar(nq);
+    for (int64_t i = 0; i < N1; ++i)
+        for (int64_t k = Qp.ptr[i]; k < Qp.ptr[i + 1]; ++k) {
+            const int64_t j = Qp.col[k];
+            pbar[k] = 0.5 * (QpbarM.get(i, j) + QpbarM.get(j, i));
+        }
+    // Tbar blocks, part 1: Q1bar T Q' + Q' T Q1bar = Q1bar X + X^T Q1bar
+    std::vector<double> tbar(boff[ng], 0.0);
+    parallel_for(ng, nthr, [&](int64_t g0, int64_t g1, int) {
+        for (int64_t g = g0; g < g1; ++g) {
+            const int64_t m = gstart[g + 1] - gstart[g];
+            for (int64_t a = 0; a < m; ++a)
+                for (int64_t b = 0; b < m; ++b) {
+                    const int64_t da = gdofs[gstart[g] + a], db = gdofs[gstart[g] + b];
+                    tbar[boff[g] + a * m + b] = row_dot(Qb, da, XT, db) + row_dot(XT, da, QbT, db);
+                }
+        }
+    });
+    // local DoFs of every tet, the tets of every DoF, and T M1^t T per tet (n1 x n1, local order)
+    std::vector<int64_t> tdofs((size_t)T * n1);
+    for (int64_t t = 0; t < T; ++t) L.tet_dofs1(t, &tdofs[(size_t)t * n1]);
+    std::vector<int64_t> tptr(N1 + 1, 0), tlist;
+    for (int64_t t = 0; t < T; ++t)
+        for (int a = 0; a < n1; ++a)
+            if (tdofs[(size_t)t * n1 + a] >= 0) ++tptr[tdofs[(size_t)t * n1 + a] + 1];
+    for (int64_t i = 0; i < N1; ++i) tptr[i + 1] += tptr[i];
+    tlist.resize(tptr[N1]);
+    {
+        std::vector<int64_t> fill(tptr.begin(), tptr.end() - 1);
+        for (int64_t t = 0; t < T; ++t)
+            for (int a = 0; a < n1; ++a) {
+                const int64_t g = tdofs[(size_t)t * n1 + a];
+                if (g >= 0) tlist[fill[g]++] = t;
+            }
+    }
+    std::vector<double> tmt((size_t)T * n1 * n1);
+    parallel_for(T, nthr, [&](int64_t t0, int64_t t1, int) {
+        std::vector<double> Tl((size_t)n1 * n1), W((size_t)n1 * n1);
+        for (int64_t t = t0; t < t1; ++t) {
+            const int64_t* D = &tdofs[(size_t)t * n1];
+            for (int a = 0; a < n1; ++a)
+                for (int b = 0; b < n1; ++b) Tl[(size_t)a * n1 + b] = (D[a] >= 0 && D[b] >= 0) ? Tm.get(D[a], D[b]) : 0.0;
+            for (int a = 0; a < n1; ++a)         // W = Tl Mloc
+                for (int b = 0; b < n1; ++b) {
+                    double s = 0;
+                    for (int c = 0; c < n1; ++c) s += Tl[(size_t)a * n1 + c] * S.M1loc[(size_t)c * n1 + b];
+                    W[(size_t)a * n1 + b] = s;
+                }
+            double* out = &tmt[(size_t)t * n1 * n1];
+            for (int a = 0; a < n1; ++a)         // out = W Tl
+                for (int b = 0; b < n1; ++b) {
+                    double s = 0;
+                    for (int c = 0; c < n1; ++c) s += W[(size_t)a * n1 + c] * Tl[(size_t)c * n1 + b];
+                    out[(size_t)a * n1 + b] = s;
+                }
+        }
+    });
+    // column loop of the SPAI of M' (fixed contiguous ranges per thread, summed in order)
+    const int threads = std::max(1, std::min<int>(nthr, (int)std::max<int64_t>(1, N1 / 64)));
+    std::vector<std::vector<double>> part(threads, std::vector<double>(T, 0.0));
+    std::vector<std::vector<double>> tpart(threads, std::vector<double>(boff[ng], 0.0));
+    std::atomic<bool> bad(false);
+    auto work = [&](int th) {
+        const int64_t l0 = N1 * th / threads, l1 = N1 * (th + 1) / threads;
+        std::vector<int32_t> mk(N1, -1);
+        std::vector<double> r(N1, 0.0), az(N1, 0.0), wz(N1, 0.0), wq(N1, 0.0), G, rhs;
+        std::vector<int64_t> rows, wrows;
+        std::vector<char> rowseen(N1, 0), wseen(N1, 0), tseen(T, 0);
+        std::vector<int64_t> tets;
+        std::vector<double> zT(n1), qT(n1);
+        auto& gpart = part[th];
+        auto& tb = tpart[th];
+        for (int64_t l = l0; l < l1; ++l) {
+            const int64_t* I = &Qp.col[Qp.ptr[l]];
+            const int m = (int)(Qp.ptr[l + 1] - Qp.ptr[l]);
+            for (int p = 0; p < m; ++p) mk[I[p]] = p;
+            G.assign((size_t)m * m, 0.0);
+            for (int p = 0; p < m; ++p)
+                for (int64_t a = Up.ptr[I[p]]; a < Up.ptr[I[p] + 1]; ++a) {
+                    const int32_t pb = mk[Up.col[a]];
+                    if (pb >= 0) G[(size_t)p * m + pb] = Up.val[a];
+                }
+            rhs.assign((size_t)2 * m, 0.0);
+            for (int64_t a = Mp.ptr[l]; a < Mp.ptr[l + 1]; ++a)
+                if (mk[Mp.col[a]] >= 0) rhs[mk[Mp.col[a]]] = Mp.val[a];
+            for (int p = 0; p < m; ++p) rhs[m + p] = pbar[Qp.ptr[l] + p];
+            if (!cholesky_solve(m, G.data(), rhs.data(), 2)) {
+                bad = true;
+                break;
+            }
+            const double* q = rhs.data();
+            const double* z = rhs.data() + m;
+            rows.clear();
+            for (int p = 0; p < m; ++p)
+                for (int64_t a = Mp.ptr[I[p]]; a < Mp.ptr[I[p] + 1]; ++a) {
+                    const int64_t row = Mp.col[a];
+                    if (!rowseen[row]) {
+                        rowseen[row] = 1;
+                        rows.push_back(row);
+                    }
+                    r[row] -= Mp.val[a] * q[p];
+                    az[row] += Mp.val[a] * z[p];
+                }
+            if (!rowseen[l]) {
+                rowseen[l] = 1;
+                rows.push_back(l);
+            }
+            r[l] += 1.0;
+            // (a) <M'bar, T M1^t T> for the tets holding a DoF of I_l
+            tets.clear();
+            for (int p = 0; p < m; ++p)
+                for (int64_t a = tptr[I[p]]; a < tptr[I[p] + 1]; ++a)
+                    if (!tseen[tlist[a]]) {
+                        tseen[tlist[a]] = 1;
+                        tets.push_back(tlist[a]);
+                    }
+            std::sort(tets.begin(), tets.end());
+            for (int64_t t : tets) {
+                const int64_t* D = &tdofs[(size_t)t * n1];
+                const double* W = &tmt[(size_t)t * n1 * n1];
+                for (int a = 0; a < n1; ++a) {
+                    const int32_t pos = D[a] >= 0 ? mk[D[a]] : -1;
+                    zT[a] = pos >= 0 ? z[pos] : 0.0;
+                    qT[a] = pos >= 0 ? q[pos] : 0.0;
+                }
+                double c = 0.0;
+                for (int b = 0; b < n1; ++b) {
+                    if (D[b] < 0) continue;
+                    double sz = 0, sq = 0;
+                    for (int a = 0; a < n1; ++a) {
+                        sz += W[(size_t)b * n1 + a] * zT[a];
+                        sq += W[(size_t)b * n1 + a] * qT[a];
+                    }
+                    c += sz * r[D[b]] - az[D[b]] * sq;
+                }
+                gpart[t] += c;
+                tseen[t] = 0;
+            }
+            // (b) Tbar += M'bar T M1 + M1 T M'bar on the diagonal blocks, Y = T M1:
+            //   (M'bar Y)[a,b]   = r_a wz_b - az_a wq_b,  wz = sum_p z_p Y[I_p,:], wq likewise
+            //   (Y^T M'bar)[a,b] = z_p (Y^T r)_a - q_p (Y^T az)_a  for b = I_p
+            wrows.clear();
+            for (int p = 0; p < m; ++p)
+                for (int64_t a = Y.ptr[I[p]]; a < Y.ptr[I[p] + 1]; ++a) {
+                    const int64_t c = Y.col[a];
+                    if (!wseen[c]) {
+                        wseen[c] = 1;
+                        wrows.push_back(c);
+                    }
+                    wz[c] += z[p] * Y.val[a];
+                    wq[c] += q[p] * Y.val[a];
+                }
+            for (int64_t a : rows) {
+                const int64_t g = gid[a];
+                const int64_t mg = gstart[g + 1] - gstart[g];
+                const int pa = posv[a];
+                for (int64_t bb = 0; bb < mg; ++bb) {
+                    const int64_t b = gdofs[gstart[g] + bb];
+                    tb[boff[g] + pa * mg + bb] += r[a] * wz[b] - az[a] * wq[b];
+                }
+            }
+            for (int p = 0; p < m; ++p) {
+                const int64_t b = I[p];
+                const int64_t g = gid[b];
+                const int64_t mg = gstart[g + 1] - gstart[g];
+                const int pb = posv[b];
+                for (int64_t aa = 0; aa < mg; ++aa) {
+                    const int64_t a = gdofs[gstart[g] + aa];
+                    double yr = 0, ya = 0;         // (Y^T r)_a, (Y^T az)_a: row a of Y^T against dense r, az
+                    for (int64_t k = YT.ptr[a]; k < YT.ptr[a + 1]; ++k) {
+                        yr += YT.val[k] * r[YT.col[k]];
+                        ya += YT.val[k] * az[YT.col[k]];
+                    }
+                    tb[boff[g] + aa * mg + pb] += z[p] * yr - q[p] * ya;
+                }
+            }
+            for (int64_t c : wrows) {
+                wseen[c] = 0;
+                wz[c] = 0.0;
+                wq[c] = 0.0;
+            }
+            for (int64_t row : rows) {
+                rowseen[row] = 0;
+                r[row] = 0.0;
+                az[row] = 0.0;
+            }
+            for (int p = 0; p < m; ++p) mk[I[p]] = -1;
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int th = 0; th < threads; ++th) pool.emplace_back(work, th);
+    for (auto& th : pool) th.join();
+    if (bad) return -3;
+    for (int th = 0; th < threads; ++th)
+        for (size_t k = 0; k < tbar.size(); ++k) tbar[k] += tpart[th][k];
+    for (int64_t t = 0; t < T; ++t) {
+        double s = 0;
+        for (int th = 0; th < threads; ++th) s += part[th][t];
+        grad[t] = s;
+    }
+    // T = blockdiag f(M1[g,g]), f(w) = w^-1/2: M1bar[g,g] = V (Gamma o (V^T Tbar V)) V^T, then
+    // dL/d eps_t += <M1bar[g,g], M1^t[g,g]> for the tets t holding the entity g
+    for (int64_t g = 0; g < ng; ++g) {
+        const int m = (int)(gstart[g + 1] - gstart[g]);
+        const int64_t* gd = &gdofs[gstart[g]];
+        std::vector<double> A((size_t)m * m), w, V, C((size_t)m * m), Dm((size_t)m * m);
+        for (int a = 0; a < m; ++a)
+            for (int b = 0; b < m; ++b) A[(size_t)a * m + b] = M1.get(gd[a], gd[b]);
+        jacobi_eigen(m, A, w, V);
+        double wmax = 0;
+        for (double x : w) wmax = std::max(wmax, std::fabs(x));
+        for (int i = 0; i < m; ++i)            // C = V^T Tbar V
+            for (int j = 0; j < m; ++j) {
+                double s = 0;
+                for (int a = 0; a < m; ++a)
+                    for (int b = 0; b < m; ++b)
+                        s += V[(size_t)a * m + i] * tbar[boff[g] + (int64_t)a * m + b] * V[(size_t)b * m + j];
+                const double dw = w[i] - w[j];
+                const double gam = std::fabs(dw) <= 1e-12 * wmax ? -0.5 * std::pow(w[i], -1.5)
+                                                                 : (std::pow(w[i], -0.5) - std::pow(w[j], -0.5)) / dw;
+                C[(size_t)i * m + j] = gam * s;
+            }
+        for (int a = 0; a < m; ++a)            // Dm = V C V^T
+            for (int b = 0; b < m; ++b) {
+                double s = 0;
+                for (int i = 0; i < m; ++i)
+                    for (int j = 0; j < m; ++j) s += V[(size_t)a * m + i] * C[(size_t)i * m + j] * V[(size_t)b * m + j];
+                Dm[(size_t)a * m + b] = s;
+            }
+        for (int64_t k = tptr[gd[0]]; k < tptr[gd[0] + 1]; ++k) {
+            const int64_t t = tlist[k];
+            const int64_t* D = &tdofs[(size_t)t * n1];
+            std::vector<int> loc(m, -1);
+            for (int a = 0; a < m; ++a)
+                for (int c = 0; c < n1; ++c)
+                    if (D[c] == gd[a]) loc[a] = c;
+            double s = 0;
+            for (int a = 0; a < m; ++a)
+                for (int b = 0; b < m; ++b) s += Dm[(size_t)a * m + b] * S.M1loc[(size_t)loc[a] * n1 + loc[b]];
+            grad[t] += s;
+        }
+    }
+    return 0;
+}
+
+int q1_vjp(Setup& S, const double* q1bar, double* grad, int threads) {
+    return S.ortho ? q1_vjp_ortho(S, q1bar, grad, threads) : q1_vjp_plain(S, q1bar, grad, threads);
 }
 
 // ============================================================== sources and projections

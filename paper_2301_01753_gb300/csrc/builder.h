@@ -153,9 +153,10 @@ int spai_op(Setup& S, const double* V, int np, double lam, int maxit, double tol
 // Lowest `count` non-kernel eigenpairs of P2 v = lambda M1 v (v^T M1 v = 1), V column-major N1 x count.
 // Returns 0, -1 (bad input), -2 (not converged), -3 (internal / inner solve failure).
 int cavity_modes(Setup& S, int count, double* V, double* lam, int maxit, double tol, int threads, int* iters);
-// dL/d eps (per tet, length 6 n^3) through Q1 for q1bar = dL/dQ1 on the Q1 CSR pattern (order 1).
-// Returns 0, -1 (orthogonalised basis or asymmetric pattern), -3 (a normal matrix not SPD).
-int q1_vjp(const Setup& S, const double* q1bar, double* grad, int threads);
+// dL/d eps (per tet, length 6 n^3) through Q1 for q1bar = dL/dQ1 on the Q1 CSR pattern: the column
+// SPAI (order 1) or the entity-orthonormal SPAI (orders >= 2).  Returns 0, -1 (asymmetric
+// pattern), -3 (a normal matrix not SPD).
+int q1_vjp(Setup& S, const double* q1bar, double* grad, int threads);
 
 // Source vector of one dipole: tet index and the n1 weights d . Lambda1_i(x0) (global DoFs).
 int dipole_weights(const Setup& S, const double x[3], const double d[3], std::vector<int64_t>& dofs,

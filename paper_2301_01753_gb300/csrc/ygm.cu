@@ -2161,7 +2161,7 @@ int ygm_cavity_modes(ygm_ctx* ctx, int32_t count, double* V, double* omega_sq, i
 int ygm_q1_vjp(ygm_ctx* ctx, const double* q1bar, double* grad_eps) {
     if (!ctx || !q1bar || !grad_eps) return fail(ctx, YGM_EINVAL, "NULL argument");
     const int rc = ygm::q1_vjp(ctx->S, q1bar, grad_eps, 0);
-    if (rc == -1) return fail(ctx, YGM_EINVAL, "ygm_q1_vjp: available for order-1 contexts with the column SPAI Q1");
+    if (rc == -1) return fail(ctx, YGM_EINVAL, "ygm_q1_vjp: the Q1 pattern is not symmetric");
     if (rc) return fail(ctx, YGM_ENOTSPD, "ygm_q1_vjp: a column normal matrix is not SPD");
     return YGM_OK;
 }

@@ -244,8 +244,21 @@ def test_q1_vjp_matches_the_oracle_spai_derivative(n):
     assert np.array_equal(g, c.q1_vjp(qbar))                  # reproducible
 
 
-def test_q1_vjp_refuses_the_orthogonalised_basis():
-    c = Y.Context(2, 2, device=-1)
-    with pytest.raises(Y.YgmError) as ei:
-        c.q1_vjp(np.zeros(c.q1_nnz))
-    assert ei.value.code == Y.YGM_EINVAL
+@pytest.mark.parametrize("n,k", [(2, 2), (3, 2)])
+def test_q1_vjp_through_the_orthonormal_basis_matches_the_oracle(n, k):
+    """Orders >= 2: ygm_q1_vjp through Q1 = T Q' T and T = blockdiag (M1[g,g])^(-1/2) (reading R2)
+    against oracle.adjoint.q1_ortho_vjp, itself pinned to central differences."""
+    from oracle import adjoint as AD
+    from oracle import spai as SP
+    from oracle.fem import FEM
+    from oracle.mesh import KuhnMesh
+    eps = synth.tet_eps(5004, n, 1.0, 4.0)
+    f = FEM(KuhnMesh(n, k), eps=eps)
+    c = Y.Context(n, k, eps=eps, device=-1)
+    assert c.q1_info()["ortho"] == 1
+    rp, ci, va = c.export_q1()
+    qbar = np.random.default_rng(k).standard_normal(len(va))
+    g = c.q1_vjp(qbar)
+    Qbar = sp.csr_matrix((qbar, ci, rp), shape=(c.N1, c.N1)).toarray()
+    go = AD.q1_ortho_vjp(f, SP.pattern("sm1sq", f.M1(), f.dof1), Qbar)
+    assert np.abs(g - go).max() <= 1e-10 * np.abs(go).max()
