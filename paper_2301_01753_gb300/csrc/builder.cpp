@@ -995,6 +995,53 @@ struct Builder {
         });
     }
 
+    // P2 = C^T M2 C assembled as a CSR from the local blocks (needs make_P2loc)
+    Csr assemble_P2() {
+        const int n1 = L.n1;
+        const int64_t N1 = L.N1;
+        std::vector<std::vector<int64_t>> rc(N1);
+        std::vector<std::vector<double>> rv(N1);
+        parallel_for(N1, threads, [&](int64_t b, int64_t e, int) {
+            std::vector<std::pair<int64_t, double>> acc;
+            for (int64_t g = b; g < e; ++g) {
+                int c, v[3];
+                L.decode1(g, &c, v);
+                acc.clear();
+                for (const Incidence& in : L.inc1[c]) {
+                    int cx = v[0] + in.dcube[0], cy = v[1] + in.dcube[1], cz = v[2] + in.dcube[2];
+                    const double im = 1.0 / S.mu[tet_index(cx, cy, cz, in.shape)];
+                    for (int r = 0; r < n1; ++r) {
+                        const LocalDof& Ld = L.loc1[in.shape][r];
+                        int64_t gj = L.index1(Ld.cls, cx + Ld.off[0], cy + Ld.off[1], cz + Ld.off[2]);
+                        if (gj >= 0) acc.push_back({gj, im * P2loc[(size_t)in.loc * n1 + r]});
+                    }
+                }
+                std::sort(acc.begin(), acc.end(),
+                          [](const std::pair<int64_t, double>& x, const std::pair<int64_t, double>& y) {
+                              return x.first < y.first;
+                          });
+                for (size_t p = 0; p < acc.size();) {
+                    const int64_t j = acc[p].first;
+                    double sum = 0;
+                    while (p < acc.size() && acc[p].first == j) sum += acc[p++].second;
+                    rc[g].push_back(j);
+                    rv[g].push_back(sum);
+                }
+            }
+        });
+        Csr P;
+        P.nrows = P.ncols = N1;
+        P.ptr.assign(N1 + 1, 0);
+        for (int64_t i = 0; i < N1; ++i) P.ptr[i + 1] = P.ptr[i] + (int64_t)rc[i].size();
+        P.col.resize(P.ptr.back());
+        P.val.resize(P.ptr.back());
+        for (int64_t i = 0; i < N1; ++i) {
+            std::copy(rc[i].begin(), rc[i].end(), P.col.begin() + P.ptr[i]);
+            std::copy(rv[i].begin(), rv[i].end(), P.val.begin() + P.ptr[i]);
+        }
+        return P;
+    }
+
     // diagonal of P2 (needs make_P2loc): each incident tet adds its local diagonal entry
     void P2_diag(double* d) {
         const int n1 = L.n1;
@@ -1517,10 +1564,13 @@ static int sylvester_pcg(const Csr& M, Csr& Q, const std::vector<double>& W, int
     }
     // y = A x on the pattern (matrix-free)
     std::vector<double> G(nq), QW((size_t)N1 * np), Y((size_t)N1 * np);
+    // one dense column -> slot map per worker thread, reset after every row
+    std::vector<std::vector<int64_t>> slots(std::max(1, threads));
     auto apply = [&](const std::vector<double>& x, std::vector<double>& y) {
-        // G = U Q (entries of the pattern only), row-parallel with a dense column -> slot map
-        parallel_for(N1, threads, [&](int64_t b, int64_t e, int) {
-            std::vector<int64_t> slot(N1, -1);
+        // G = U Q (entries of the pattern only), row-parallel
+        parallel_for(N1, threads, [&](int64_t b, int64_t e, int th) {
+            std::vector<int64_t>& slot = slots[th];
+            if (slot.empty()) slot.assign(N1, -1);
             for (int64_t i = b; i < e; ++i) {
                 for (int64_t k = P.ptr[i]; k < P.ptr[i + 1]; ++k) {
                     slot[P.col[k]] = k;
@@ -1698,6 +1748,8 @@ int cavity_modes(Setup& S, int count, double* V, double* lam, int maxit, double 
     try {
         Builder B(S, threads);
         B.make_P2loc();
+        const Csr P2 = B.assemble_P2();
+        auto p2mv = [&](const double* a, double* b) { P2.matvec(a, b, threads); };
         // kernel basis as rows of K^T: interior vertex gradients, then the gradient 1-forms
         std::vector<std::vector<std::pair<int64_t, double>>> kt;
         const int n = L.n;
@@ -1739,7 +1791,7 @@ int cavity_modes(Setup& S, int count, double* V, double* lam, int maxit, double 
         const Csr L0 = spgemm(spgemm(Kt, S.M1, threads), K, threads);    // K^T M1 K
         std::vector<double> L0inv(nK), Pd(N1), Md(N1), Ainv(N1);
         for (int64_t i = 0; i < nK; ++i) L0inv[i] = 1.0 / L0.get(i, i);
-        B.P2_diag(Pd.data());
+        for (int64_t i = 0; i < N1; ++i) Pd[i] = P2.get(i, i);
         for (int64_t i = 0; i < N1; ++i) Md[i] = S.M1.get(i, i);
         const double sigma = 1.0 / (L.h * L.n * L.h * L.n);               // 1 / side^2
         for (int64_t i = 0; i < N1; ++i) Ainv[i] = 1.0 / (Pd[i] + sigma * Md[i]);
@@ -1749,7 +1801,7 @@ int cavity_modes(Setup& S, int count, double* V, double* lam, int maxit, double 
             std::vector<double> zz(nK), v(N1), pv(N1);
             for (int64_t i = 0; i < nK; ++i) zz[i] = std::sin(0.37 * (double)i + 0.1);
             K.matvec(zz.data(), v.data(), threads);
-            B.P2_matvec(v.data(), pv.data());
+            p2mv(v.data(), pv.data());
             double a = 0, bnorm = 0, pmax = 0;
             for (int64_t i = 0; i < N1; ++i) {
                 a += pv[i] * pv[i];
@@ -1765,13 +1817,13 @@ int cavity_modes(Setup& S, int count, double* V, double* lam, int maxit, double 
             S.M1.matvec(x, t1.data(), threads);
             Kt.matvec(t1.data(), kr.data(), threads);
             if (pcg([&](const double* a, double* b) { L0.matvec(a, b, threads); }, L0inv, kr.data(), kz.data(), nK,
-                    1e-13, 20000) < 0)
+                    1e-12, 20000) < 0)
                 throw std::runtime_error("cavity modes: the kernel projection did not converge");
             K.matvec(kz.data(), t1.data(), threads);
             for (int64_t i = 0; i < N1; ++i) x[i] -= t1[i];
         };
         auto shifted = [&](const double* a, double* b) {   // (P2 + sigma M1) a
-            B.P2_matvec(a, b);
+            p2mv(a, b);
             S.M1.matvec(a, t2.data(), threads);
             for (int64_t i = 0; i < N1; ++i) b[i] += sigma * t2[i];
         };
@@ -1792,7 +1844,7 @@ int cavity_modes(Setup& S, int count, double* V, double* lam, int maxit, double 
                 double* y = &Y[(size_t)j * N1];
                 S.M1.matvec(&X[(size_t)j * N1], t1.data(), threads);
                 std::vector<double> rhs(t1);
-                if (pcg(shifted, Ainv, rhs.data(), y, N1, 1e-12, 50000) < 0)
+                if (pcg(shifted, Ainv, rhs.data(), y, N1, 1e-10, 50000) < 0)
                     throw std::runtime_error("cavity modes: the shifted solve did not converge");
                 project(y);
             }
@@ -1818,7 +1870,7 @@ int cavity_modes(Setup& S, int count, double* V, double* lam, int maxit, double 
                     }
                 }
             // Rayleigh-Ritz with P2
-            for (int j = 0; j < p; ++j) B.P2_matvec(&Y[(size_t)j * N1], &PY[(size_t)j * N1]);
+            for (int j = 0; j < p; ++j) p2mv(&Y[(size_t)j * N1], &PY[(size_t)j * N1]);
             for (int a = 0; a < p; ++a)
                 for (int b2 = 0; b2 < p; ++b2) {
                     double c = 0;
