@@ -262,3 +262,14 @@ def test_q1_vjp_through_the_orthonormal_basis_matches_the_oracle(n, k):
     Qbar = sp.csr_matrix((qbar, ci, rp), shape=(c.N1, c.N1)).toarray()
     go = AD.q1_ortho_vjp(f, SP.pattern("sm1sq", f.M1(), f.dof1), Qbar)
     assert np.abs(g - go).max() <= 1e-10 * np.abs(go).max()
+
+
+def test_noalloc_step_argument_checks_without_a_device():
+    """ygm_step_noalloc refuses NULL buffers and host-only contexts before any CUDA call."""
+    import ctypes as C
+    c = Y.Context(2, 1, device=-1)
+    buf = np.zeros(max(c.N1, c.N2))
+    p = buf.ctypes.data_as(C.c_void_p)
+    assert Y._lib.ygm_step_noalloc(c._h, None, p, p, 0.01) == Y.YGM_EINVAL
+    assert Y._lib.ygm_step_noalloc(c._h, p, p, p, 0.01) == Y.YGM_ENODEV
+    assert b"host-only" in Y._lib.ygm_last_error(c._h)
