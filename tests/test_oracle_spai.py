@@ -162,3 +162,27 @@ def test_spai_eigen_residual_table_rows():
         got = (eps.mean(), eps[:100].mean(), eps[100:].mean())
         for g, printed in zip(got, map(fraction, row[1:])):
             assert abs(g - printed) <= 5e-5, (row[0], got)
+
+
+def test_spai_consistency_error_does_not_refine_away():
+    """Sec. 7.1: the sparse approximation Q1 ~ M1^-1 adds a consistency error independent of h
+    (first Strang lemma) that wider stencils reduce.  Lowest cavity eigenvalue of the unit PEC cube
+    (2 pi^2), k = 1: exact FEEC converges at ~h^2; S(1) and S(M1) SPAI errors plateau, S(M1)'s well
+    below S(1)'s."""
+    import scipy.linalg as sl
+    w0 = 2 * np.pi ** 2
+    err = {}
+    for n in (3, 6):
+        f = FEM(KuhnMesh(n, 1))
+        M1 = f.M1()
+        P2 = (f.C().T @ f.M2() @ f.C()).tocsr().toarray()
+        we = sl.eigh(P2, M1.toarray(), eigvals_only=True)
+        err[n, "exact"] = (we[we > 1e-8 * we[-1]][0] - w0) / w0
+        for kind in ("diag", "sm1"):
+            Q, _ = SP.spai(M1, kind)
+            wq = np.sort(np.linalg.eigvals(Q.toarray() @ P2).real)
+            err[n, kind] = (wq[wq > 1e-8 * wq[-1]][0] - w0) / w0
+    assert 3.0 < err[3, "exact"] / err[6, "exact"] < 5.0                 # ~ (6/3)^2
+    for kind in ("diag", "sm1"):
+        assert abs(err[6, kind]) > 0.9 * abs(err[3, kind])                # no convergence
+    assert abs(err[6, "sm1"]) < 0.5 * abs(err[6, "diag"])                  # the wider stencil helps
