@@ -51,7 +51,8 @@ extern "C" {
 #define YGM_ENOTSPD  -3   /* Q1 not SPD even after the allowed diagonal shift */
 #define YGM_ENOMEM   -4   /* host or device allocation failed */
 #define YGM_ECUDA    -5   /* a CUDA call failed (message carries cudaGetErrorString) */
-#define YGM_ETIMEOUT -6   /* a bounded device wait gave up */
+#define YGM_ETIMEOUT -6   /* an iterative host solve (SPAI-OP PCG, cavity modes) reached its
+                             iteration limit without converging */
 #define YGM_ENODEV   -7   /* no CUDA device is available */
 
 #define YGM_FP64 0        /* fields, Q1 and arithmetic in double */
