@@ -186,3 +186,21 @@ def test_spai_consistency_error_does_not_refine_away():
     for kind in ("diag", "sm1"):
         assert abs(err[6, kind]) > 0.9 * abs(err[3, kind])                # no convergence
     assert abs(err[6, "sm1"]) < 0.5 * abs(err[6, "diag"])                  # the wider stencil helps
+
+
+@pytest.mark.parametrize("n,k,tol", [(3, 2, 0.015), (4, 2, 0.015), (2, 3, 0.05), (3, 3, 0.10)])
+def test_default_policy_keeps_the_lowest_cavity_modes(n, k, tol):
+    """Reading R2 (k >= 2: S(M1^2) SPAI in the entity-orthonormal basis): Q1 P2 keeps the three
+    lowest non-kernel eigenvalues of the unit PEC cube within ~1 % (k = 2) and ~8 % (k = 3) of the
+    exact FEEC values M1^-1 P2."""
+    import scipy.linalg as sl
+    f = FEM(KuhnMesh(n, k))
+    M1 = f.M1()
+    P2 = (f.C().T @ f.M2() @ f.C()).tocsr().toarray()
+    we = sl.eigh(P2, M1.toarray(), eigvals_only=True)
+    we = we[we > 1e-8 * we[-1]][:3]
+    Q, info = SP.gym_q1(f, M1)
+    assert info["shift"] == 0.0 and info["lmin"] > 0
+    wq = np.sort(np.linalg.eigvals(Q.toarray() @ P2).real)
+    wq = wq[wq > 1e-8 * wq[-1]][:3]
+    assert np.all(np.abs(wq - we) / we < tol)
