@@ -151,14 +151,14 @@ def test_host_spai_op_orthogonal_basis_matches_oracle():
     P2, w, V = _probe_modes(f, M1, 2)
     c = Y.Context(2, 2, eps=eps, device=-1)
     assert c.q1_info()["ortho"] == 1
-    it, rr = c.spai_op(V, 10.0, tol=1e-11, max_iter=50000)
+    it, rr = c.spai_op(V, 1.0, tol=1e-11, max_iter=50000)
     assert rr <= 1e-11
     rp, ci, va = c.export_q1()
     Qb = sp.csr_matrix((va, ci, rp), shape=(c.N1, c.N1))
-    Qo, info = OP.spai_op_q1(f, M1, P2, V, 10.0, tol=1e-11)
+    Qo, info = OP.spai_op_q1(f, M1, P2, V, 1.0, tol=1e-11)
     assert abs(Qb - Qo).max() <= 1e-8 * abs(Qo).max()
     for j in range(V.shape[1]):
-        assert OP.eig_residual(Qb, P2, V[:, j], w[j]) < 0.3 * OP.eig_residual(g.Q1, P2, V[:, j], w[j])
+        assert OP.eig_residual(Qb, P2, V[:, j], w[j]) < 0.6 * OP.eig_residual(g.Q1, P2, V[:, j], w[j])
 
 
 @pytest.mark.parametrize("n,k,seed", [(3, 1, 5), (4, 1, None), (2, 2, 7)])
