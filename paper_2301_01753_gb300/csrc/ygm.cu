@@ -6,9 +6,12 @@
 //   k_energy   W_n (every K steps, FP64 compensated)       (telescoping invariant of the leapfrog)
 //   k_curlT_e  e_{n+1} = e_n + dt C^T M2 b_{n+1/2}         (shear map Phi^a, Eq. dTIsFiniteDiff)
 //   k_source   e_{n+1} -= dt s(t_{n+1/2}) d . Lambda1(x0)  (current term of Eq. allEOM)
-// Every kernel maps one warp to one x-row of a DoF class (lanes run along x), so all
-// stencil bookkeeping is warp-uniform.  Each output element is written by exactly one
-// lane in a fixed summation order: results are deterministic, no atomics.
+// One column (R = 1): k_qapply_s, k_curl_b_s and k_curlT_e_s give one thread to each lattice
+// point of a (class, z-plane), with every stencil term a constant 32-bit offset into
+// zero-halo padded copies of e, x and b.  R > 1 columns and meshes whose lattice offsets
+// overflow 32 bits use k_qapply_p and the range-checked k_curl_b_r / k_curlT_e_r, which give
+// each (DoF, column) pair a thread.  Each output element is written by exactly one thread
+// in a fixed summation order: results are deterministic, no atomics.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -92,6 +95,8 @@ __device__ __forceinline__ bool in_box(const DCls& D, int u0, int u1, int u2) {
 }
 
 // ------------------------------------------------------------------ x = Q1 e, padded e, full rows
+// Used with R > 1 columns, and with one column when the upper-triangle lattice of k_qapply_s
+// would overflow 32-bit offsets.
 // One thread per row.  Q1 is stored by full rows, slot-major per class and z-plane
 // (qf[class][slot][z][y][x], zero where the neighbour lies outside its box), and e is read from
 // its padded copy, so slot s of every row of a class is the constant offset soff[s] from the
