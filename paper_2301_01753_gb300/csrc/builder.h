@@ -2,8 +2,10 @@
 //
 // Everything here runs once per context: lattice classes and stencils, order-k local
 // bases, exact element integrals, M1(eps), M2(mu), the integer curl, the SPAI Q1
-// (Sec. 5, Eq. NormalEqSolve) and the CFL bound (Prop. stability).  The device kernels
-// only ever see the packed tables produced at the end.
+// (Sec. 5, Eq. NormalEqSolve) and the CFL bound (Prop. stability).  On request it also
+// computes the operator-probed SPAI (Sec. 5.1), the cavity modes used as its probes, and the
+// derivative of the SPAI with respect to the per-tet permittivity.  The device kernels only
+// ever see the packed tables produced at the end.
 #pragma once
 #include <array>
 #include <map>
