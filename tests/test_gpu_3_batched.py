@@ -65,34 +65,36 @@ def test_batched_columns_follow_oracle(n, k, R):
     c.close()
 
 
-def test_batched_equals_single_column_runs_fp32():
-    """R = 32 columns of FP32 state, checked column by column against R = 1 runs."""
-    n, k, R = 5, 2, 32
-    eps = synth.tet_eps(3000, n, 1.0, 4.0)
+# FP32 columns against the FP64 oracle: the same bound as the single-column FP32 parity tests.
+# The batched kernels (full-row Q1, one thread per (row, column)) and the single-column kernels
+# (upper-triangle Q1) sum in different orders, so FP32 columns of the two agree only to the
+# rounding level of each, not bit for bit; both are held to the oracle instead.
+FP32_TOL = 5e-5
+
+
+def test_batched_fp32_columns_follow_oracle():
+    """R = 32 columns of FP32 state, each checked against the FP64 oracle run of its own source."""
+    n, k, R, steps = 5, 2, 32, 60
+    f, g, eps, _ = oracle_model(n, k, eps_seed=3000)
     cb = Y.Context(n, k, eps=eps, precision=Y.YGM_FP32, n_rhs=R, energy_every=5)
+    assert abs(cb.tau_cfl / g.tau_cfl() - 1) < 1e-9
     tau = 0.5 * cb.tau_cfl
     srcs = _sources(R, tau, 3001)
     N1, N2 = cb.N1, cb.N2
     cb.set_state(np.zeros(N1 * R, np.float32), np.zeros(N2 * R, np.float32))
-    cb.step(60, tau, srcs)
+    cb.step(steps, tau, srcs)
     e, b = cb.get_state(synced=True)
-    Wb, Hb = cb.energy()
     Wh = cb.energy_history().reshape(-1, R)
     e, b = _columns(e, N1, R), _columns(b, N2, R)
-    c1 = Y.Context(n, k, eps=eps, precision=Y.YGM_FP32, energy_every=5)
+    z1, z2 = np.zeros(N1), np.zeros(N2)
     for r in (0, 1, 17, 31):
-        s = dict(srcs[r])
-        s["rhs"] = 0
-        c1.set_state(np.zeros(N1, np.float32), np.zeros(N2, np.float32))
-        c1.step(60, tau, [s])
-        e1, b1 = c1.get_state(synced=True)
-        W1, H1 = c1.energy()
-        assert rel_l2(e[:, r], e1) < 1e-6, r
-        assert rel_l2(b[:, r], b1) < 1e-6, r
-        assert abs(Wb[r] - W1[0]) <= 1e-6 * abs(W1[0]), r
-        assert abs(Hb[r] - H1[0]) <= 1e-6 * abs(H1[0]), r
-        assert np.max(np.abs(Wh[:, r] - c1.energy_history())) <= 1e-6 * np.max(np.abs(Wh[:, r])), r
-    c1.close()
+        s = {kk: v for kk, v in srcs[r].items() if kk != "rhs"}
+        s["width_steps"] = 5.0
+        e_or, _, bs_or, W_or = run_oracle(f, g, z1, z2, tau, steps, sources=[s], energy_every=5)
+        assert np.linalg.norm(e_or) > 0
+        assert rel_l2(e[:, r], e_or) < FP32_TOL, r
+        assert rel_l2(b[:, r], bs_or) < FP32_TOL, r
+        assert np.max(np.abs(Wh[:, r] - W_or)) <= FP32_TOL * np.max(np.abs(W_or)), r
     cb.close()
 
 
