@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <array>
 #include <map>
 #include <mutex>
 #include <type_traits>
@@ -42,7 +43,7 @@ struct DCls {            // a DoF class box (1-form or 2-form)
     int st_begin, st_end;    // 1-forms: stencil slots; 2-forms: curl terms
     int inc_begin, inc_end;  // 1-forms: incident tets
     int pbase;               // 1-forms: first element of the class region in the padded copy of e
-    int pad_;
+    int nup;                 // 1-forms: upper (stored) Q1 slots of the class
 };
 // Padded copy of e: every 1-form class owns a cube of NP^3 entries indexed by lattice anchor + H
 // (anchors -H .. n+H), zero outside the class box, so any Q1 neighbour (|d| <= H per axis) of
@@ -164,12 +165,16 @@ __global__ void __launch_bounds__(PBLOCK) k_qapply_p(const PBlk* __restrict__ bl
 // from the row.  Every slot is therefore one 32-bit element offset for Q1 and one for the padded
 // e, and the loop body is two loads and one FMA.  Lower slots point to rows at dz <= 0, and the
 // blocks are ordered by z-plane, so those values were streamed from HBM by the blocks of the
-// same or the previous planes shortly before and are often read again from L2.  Measured at
-// N=32, k=2 (FP32): 1.5x the distinct bytes cross the HBM interface, against 2x for full-row
-// storage; about six planes of blocks are resident at once, which bounds the reuse.  Lattice
-// points outside the row's box (PEC-removed rows, and the wrap-around of neighbour offsets) hold
-// finite values that multiply a zero of the padded e.
-// The slots of a class are visited in padded-e order, so consecutive loads of e share L1 lines.
+// same or the previous planes shortly before and can be read again from L2: the upper loads
+// carry an L2 evict-last hint (the value has one more reader), the lower loads evict-first
+// (last reader).  Lattice points outside the row's box (PEC-removed rows, and the wrap-around of
+// neighbour offsets) hold finite values that multiply a zero of the padded e.
+// Slot order per class: the upper slots, then the lower ones, each group in padded-e order so
+// consecutive loads of e share L1 lines.
+// FP32 sums are compensated (Kahan): the stencil sum cancels strongly (the rows of an
+// approximate inverse of an ill-conditioned mass matrix), and the plain FP32 sum is the largest
+// rounding term of the FP32 step.  The extra adds are hidden behind the memory stream.
+// ENERGY: every row also adds e_i x_i to a per-block FP64 partial (the e^T Q1 e half of W_n).
 constexpr int SBLOCK = 256;
 struct SBlk {            // up to SBLOCK consecutive lattice points (vy * NX + vx) of one (class, z-plane)
     long long q0;        // qs index of the plane's first lattice point (class base + vz * NY * NX)
@@ -183,57 +188,47 @@ struct SymGeo {
     int H, NP;           // padded e geometry
 };
 template <typename real>
-__global__ void __launch_bounds__(SBLOCK) k_qapply_s(const SBlk* __restrict__ blks, const DCls* __restrict__ c1,
-                                                     const int2* __restrict__ soff2, SymGeo g,
-                                                     const real* __restrict__ qs, const real* __restrict__ ep,
-                                                     real* __restrict__ x, real* __restrict__ xp) {
-    extern __shared__ __align__(16) int2 s_o2[];
-    const SBlk B = blks[blockIdx.x];
-    const DCls C = c1[B.cls];
-    const int ns = C.st_end - C.st_begin;
-    for (int s = threadIdx.x; s < ns; s += blockDim.x) s_o2[s] = soff2[C.st_begin + s];
-    __syncthreads();
-    if ((int)threadIdx.x >= B.cnt) return;
-    const int t = B.t0 + (int)threadIdx.x;
-    const int vy = t / g.NX, vx = t - vy * g.NX;
-    const int rx = vx - C.lo[0], ry = vy - C.lo[1];
-    if ((unsigned)rx >= (unsigned)C.num[0] || (unsigned)ry >= (unsigned)C.num[1]) return;
-    const real* __restrict__ q = qs + (B.q0 + t);
-    const int pe = C.pbase + ((B.vz + g.H) * g.NP + (vy + g.H)) * g.NP + vx + g.H;
-    const real* __restrict__ e0 = ep + pe;
-    real acc = real(0);
-    int s = 0;
-    for (; s + 8 <= ns; s += 8) {
-        const int4 o0 = *reinterpret_cast<const int4*>(&s_o2[s]);
-        const int4 o1 = *reinterpret_cast<const int4*>(&s_o2[s + 2]);
-        const int4 o2 = *reinterpret_cast<const int4*>(&s_o2[s + 4]);
-        const int4 o3 = *reinterpret_cast<const int4*>(&s_o2[s + 6]);
+__device__ __forceinline__ real ld_l2hint(const real* p, unsigned long long pol) {
+    real v;
+    if constexpr (std::is_same<real, float>::value)
+        asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    else
+        asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+}
+// running sum: compensated for float, plain FMA for double
+template <typename real>
+struct KSum {
+    real s = real(0), c = real(0);
+    __device__ __forceinline__ void add(real q, real e) {
+        if constexpr (std::is_same<real, float>::value) {
+            const real y = fma(q, e, -c);
+            const real t = s + y;
+            c = (t - s) - y;
+            s = t;
+        } else {
+            s = fma(q, e, s);
+        }
+    }
+};
+template <typename real>
+__device__ __forceinline__ void qs_run(KSum<real>& a, const int2* s_o2, int s, int send, const real* q, const real* e0,
+                                       unsigned long long pol) {
+    for (; s + 8 <= send; s += 8) {
         real qv[8], ev[8];
-        qv[0] = __ldg(q + o0.x);
-        qv[1] = __ldg(q + o0.z);
-        qv[2] = __ldg(q + o1.x);
-        qv[3] = __ldg(q + o1.z);
-        qv[4] = __ldg(q + o2.x);
-        qv[5] = __ldg(q + o2.z);
-        qv[6] = __ldg(q + o3.x);
-        qv[7] = __ldg(q + o3.z);
-        ev[0] = __ldg(e0 + o0.y);
-        ev[1] = __ldg(e0 + o0.w);
-        ev[2] = __ldg(e0 + o1.y);
-        ev[3] = __ldg(e0 + o1.w);
-        ev[4] = __ldg(e0 + o2.y);
-        ev[5] = __ldg(e0 + o2.w);
-        ev[6] = __ldg(e0 + o3.y);
-        ev[7] = __ldg(e0 + o3.w);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc = fma(qv[u], ev[u], acc);
+        for (int u = 0; u < 8; ++u) {
+            const int2 o = s_o2[s + u];
+            qv[u] = ld_l2hint(q + o.x, pol);
+            ev[u] = __ldg(e0 + o.y);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a.add(qv[u], ev[u]);
     }
-    for (; s < ns; ++s) {
+    for (; s < send; ++s) {
         const int2 o = s_o2[s];
-        acc = fma(__ldg(q + o.x), __ldg(e0 + o.y), acc);
+        a.add(ld_l2hint(q + o.x, pol), __ldg(e0 + o.y));
     }
-    x[C.off + ((long long)(B.vz - C.lo[2]) * C.num[1] + ry) * C.num[0] + rx] = acc;
-    xp[pe] = acc;
 }
 
 // ------------------------------------------------------------------ curls on the padded lattice, one column
@@ -253,12 +248,24 @@ struct WTermL {          // one merged C^T M2 weight: w * bp[row + off]
 __device__ __forceinline__ int pad_row(PadGeo g, int vx, int vy, int vz) {
     return ((vz + g.H) * g.NP + (vy + g.H)) * g.NP + vx + g.H;
 }
+// A step size in two parts, hi + lo = ctau to ~2^-48 relative: hi is the nearest value of the
+// state type, lo the rest (0 in FP64).  An FP32 update with hi alone would run the leapfrog at a
+// step rounded by up to 6e-8, a systematic phase drift that grows with the number of steps.
+template <typename real>
+struct Tau {
+    real hi, lo;
+};
+template <typename real>
+static Tau<real> split_tau(double t) {
+    const real hi = (real)t;
+    return Tau<real>{hi, (real)(t - (double)hi)};
+}
 // b_out = b_in - ctau C x; also bp <- b_out
 template <typename real>
 __global__ void __launch_bounds__(SBLOCK) k_curl_b_s(const SBlk* __restrict__ blks, const DCls* __restrict__ c2,
                                                      const CTermL* __restrict__ terms, PadGeo g, int NX,
                                                      const real* __restrict__ xp, const real* b_in, real* b_out,
-                                                     real* __restrict__ bp, real ctau) {
+                                                     real* __restrict__ bp, Tau<real> ctau) {
     const SBlk B = blks[blockIdx.x];
     const DCls C = c2[B.cls];
     if ((int)threadIdx.x >= B.cnt) return;
@@ -274,16 +281,27 @@ __global__ void __launch_bounds__(SBLOCK) k_curl_b_s(const SBlk* __restrict__ bl
         acc += T.sign > 0 ? xv : -xv;
     }
     const long long gi = C.off + ((long long)(B.vz - C.lo[2]) * C.num[1] + ry) * C.num[0] + rx;
-    const real v = b_in[gi] - ctau * acc;
+    const real v = fma(-ctau.lo, acc, fma(-ctau.hi, acc, b_in[gi]));
     b_out[gi] = v;
     bp[C.pbase + p] = v;
 }
-// e += ctau C^T M2 b (uniform mu), from the padded b; also ep <- e
+// A dipole source DoF inside a block of k_curlT_e_s: thread, source index, weight d . Lambda1_i(x0).
+template <typename real>
+struct SrcE {
+    int tid;
+    int src;
+    real w;
+};
+// e += ctau C^T M2 b (uniform mu), from the padded b; also ep <- e.  With amp != NULL the dipole
+// currents of this step are subtracted in the same pass: e_i -= amp[s] w_i for the entries
+// sbeg[block] .. sbeg[block + 1] (amp[s] = dt s_s(t_{n+1/2}), host FP64).  Blocks of classes that
+// carry no curl appear in the launch only when a source DoF lies in them; their stencil is empty.
 template <typename real>
 __global__ void __launch_bounds__(SBLOCK) k_curlT_e_s(const SBlk* __restrict__ blks, const DCls* __restrict__ c1,
                                                       const int* __restrict__ pbeg, const WTermL<real>* __restrict__ terms,
                                                       PadGeo g, int NX, const real* __restrict__ bp, real* __restrict__ e,
-                                                      real ctau, real* __restrict__ ep) {
+                                                      Tau<real> ctau, real* __restrict__ ep, const int* __restrict__ sbeg,
+                                                      const SrcE<real>* __restrict__ sent, const double* __restrict__ amp) {
     extern __shared__ __align__(16) unsigned char s_raw[];
     WTermL<real>* s_t = reinterpret_cast<WTermL<real>*>(s_raw);
     const SBlk B = blks[blockIdx.x];
@@ -309,7 +327,10 @@ __global__ void __launch_bounds__(SBLOCK) k_curlT_e_s(const SBlk* __restrict__ b
     }
     for (; s < nt; ++s) acc = fma(s_t[s].w, __ldg(b0 + s_t[s].off), acc);
     const long long gi = C.off + ((long long)(B.vz - C.lo[2]) * C.num[1] + ry) * C.num[0] + rx;
-    const real v = e[gi] + ctau * acc;
+    real v = fma(ctau.lo, acc, fma(ctau.hi, acc, e[gi]));
+    if (amp)
+        for (int i = sbeg[blockIdx.x]; i < sbeg[blockIdx.x + 1]; ++i)
+            if (sent[i].tid == (int)threadIdx.x) v -= (real)amp[sent[i].src] * sent[i].w;
     e[gi] = v;
     ep[C.pbase + p] = v;
 }
@@ -796,6 +817,44 @@ __device__ Neu block_reduce(Neu v) {
     return v;
 }
 
+// x = Q1 e on the upper-triangle lattice (see the storage notes above k_qapply_s's helpers)
+template <typename real, bool ENERGY>
+__global__ void __launch_bounds__(SBLOCK) k_qapply_s(const SBlk* __restrict__ blks, const DCls* __restrict__ c1,
+                                                     const int2* __restrict__ soff2, SymGeo g,
+                                                     const real* __restrict__ qs, const real* __restrict__ ep,
+                                                     real* __restrict__ x, real* __restrict__ xp, double2* part) {
+    extern __shared__ __align__(16) int2 s_o2[];
+    const SBlk B = blks[blockIdx.x];
+    const DCls C = c1[B.cls];
+    const int ns = C.st_end - C.st_begin;
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) s_o2[s] = soff2[C.st_begin + s];
+    __syncthreads();
+    const int t = B.t0 + (int)threadIdx.x;
+    const int vy = t / g.NX, vx = t - vy * g.NX;
+    const int rx = vx - C.lo[0], ry = vy - C.lo[1];
+    const bool row = (int)threadIdx.x < B.cnt && (unsigned)rx < (unsigned)C.num[0] && (unsigned)ry < (unsigned)C.num[1];
+    if (!ENERGY && !row) return;
+    Neu w{0.0, 0.0};
+    if (row) {
+        unsigned long long keep, drop;
+        asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
+        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(drop));
+        const real* __restrict__ q = qs + (B.q0 + t);
+        const int pe = C.pbase + ((B.vz + g.H) * g.NP + (vy + g.H)) * g.NP + vx + g.H;
+        const real* __restrict__ e0 = ep + pe;
+        KSum<real> a;
+        qs_run(a, s_o2, 0, C.nup, q, e0, keep);
+        qs_run(a, s_o2, C.nup, ns, q, e0, drop);
+        x[C.off + ((long long)(B.vz - C.lo[2]) * C.num[1] + ry) * C.num[0] + rx] = a.s;
+        xp[pe] = a.s;
+        if (ENERGY) w = neu_add(w, (double)e0[0] * (double)a.s);
+    }
+    if (ENERGY) {
+        w = block_reduce(w);
+        if (threadIdx.x == 0) part[blockIdx.x] = make_double2(w.s, w.c);
+    }
+}
+
 // partial[blockIdx] = sum_i e_i x_i over a grid-stride slice (fixed order)
 template <typename real>
 __global__ void __launch_bounds__(BLOCK) k_dot(const real* __restrict__ a, const real* __restrict__ b, long long n,
@@ -844,6 +903,70 @@ __global__ void __launch_bounds__(BLOCK) k_tet_quad(Tables tb, const double* __r
     }
     v = block_reduce(v);
     if (threadIdx.x == 0) part[blockIdx.x] = make_double2(v.s, v.c);
+}
+
+// W_n of one column in one launch after an ENERGY Q1 apply:
+//   out = 1/2 sum(qpart) + 1/2 sum_T (1/mu_T) bn_T^T M2a bo_T
+// qpart holds the per-block e_i x_i partials of k_qapply_s.  Each block sums its tets into a
+// Neumaier pair (the per-tet product runs in the arithmetic type A: float for FP32 contexts,
+// double for FP64); the block that finishes last (ticket counter) merges every partial in
+// block order, so the result does not depend on the block schedule, and resets the counter.
+template <typename real, typename A>
+__global__ void __launch_bounds__(BLOCK) k_tet_energy(Tables tb, const A* __restrict__ M2a, const real* __restrict__ bn,
+                                                      const real* __restrict__ bo, const real* __restrict__ inv_mu,
+                                                      double2* part, const double2* __restrict__ qpart, int nq,
+                                                      unsigned* ticket, double* out) {
+    const int n = tb.n, n2a = tb.n2a;
+    const long long T = 6LL * n * n * n;
+    Neu v{0.0, 0.0};
+    A vn[27], vo[27];
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += (long long)gridDim.x * blockDim.x) {
+        const int sh = (int)(t % 6);
+        const long long cube = t / 6;
+        const int cx = (int)(cube % n), cy = (int)((cube / n) % n), cz = (int)(cube / ((long long)n * n));
+        for (int r = 0; r < n2a; ++r) {
+            const DLoc2 Lr = tb.loc2[sh * n2a + r];
+            const DCls D = tb.c2[Lr.cls];
+            const int ux = cx + Lr.off[0] - D.lo[0], uy = cy + Lr.off[1] - D.lo[1], uz = cz + Lr.off[2] - D.lo[2];
+            if (in_box(D, ux, uy, uz)) {
+                const long long gi = D.off + ((long long)uz * D.num[1] + uy) * D.num[0] + ux;
+                vn[r] = (A)bn[gi];
+                vo[r] = (A)bo[gi];
+            } else {
+                vn[r] = A(0);
+                vo[r] = A(0);
+            }
+        }
+        A q = A(0);
+        for (int r = 0; r < n2a; ++r) {
+            A u = A(0);
+            for (int c = 0; c < n2a; ++c) u = fma(M2a[r * n2a + c], vo[c], u);
+            q = fma(vn[r], u, q);
+        }
+        double qd = (double)q;
+        if (inv_mu) qd *= (double)inv_mu[t];
+        v = neu_add(v, qd);
+    }
+    v = block_reduce(v);
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = make_double2(v.s, v.c);
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    Neu a{0.0, 0.0}, b{0.0, 0.0};
+    for (int i = threadIdx.x; i < nq; i += blockDim.x) a = neu_merge(a, Neu{__ldcg(&qpart[i].x), __ldcg(&qpart[i].y)});
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) b = neu_merge(b, Neu{__ldcg(&part[i].x), __ldcg(&part[i].y)});
+    a = block_reduce(a);
+    __syncthreads();
+    b = block_reduce(b);
+    if (threadIdx.x == 0) {
+        *out = 0.5 * (a.s + a.c) + 0.5 * (b.s + b.c);
+        *ticket = 0u;
+    }
 }
 
 // out[slot] = 0.5 * (sum of parts1) + 0.5 * (sum of parts2), fixed order, one block
@@ -996,6 +1119,14 @@ struct ygm_ctx {
     SBlk *lblks_b = nullptr, *lblks_e = nullptr;
     int nlb = 0, nle = 0;
     int64_t qc_rows[2] = {0, 0}, qc_unique[2] = {0, 0}, qc_stored[2] = {0, 0};   // [active only, all rows]
+    double2* qpart = nullptr;                // per-block e_i x_i partials of an all-rows k_qapply_s
+    unsigned* ticket = nullptr;              // last-block counter of k_tet_energy (kept at 0 between launches)
+    void* M2af = nullptr;                    // M2a in the context precision (k_tet_energy)
+    std::vector<SBlk> h_lblks_e;             // host copy of lblks_e
+    SBlk* lblks_es = nullptr;                // lblks_e + the blocks of curl-free classes holding a source DoF
+    int nle_src = 0;
+    int* sbeg = nullptr;                     // per block of lblks_es: first source entry
+    void* sent = nullptr;                    // SrcE<real> entries
     void* pterms = nullptr;                  // PTerm<real> merged C^T M2 stencil (uniform mu)
     int* pbeg = nullptr;
     // time state
@@ -1039,11 +1170,16 @@ static void time_end(ygm_ctx* ctx) {
 
 static std::string g_create_err;
 static std::mutex g_err_mutex;
-// largest dynamic shared memory each block kernel has been opted in to, per precision
-// (cudaFuncSetAttribute limits are per kernel and process-wide; only ever raised); single-device
-// use assumed for the bookkeeping (the attribute is set on the current device)
+// largest dynamic shared memory each block kernel has been opted in to, per (device, precision):
+// cudaFuncSetAttribute applies to the current device only, and the limit is only ever raised
+// (a smaller value set by one context would make another context's launches invalid)
 static std::mutex g_smem_mutex;
-static size_t g_smem_q[2] = {48 * 1024, 48 * 1024}, g_smem_e[2] = {48 * 1024, 48 * 1024};
+static std::map<std::pair<int, int>, size_t> g_smem_q, g_smem_e;
+static size_t& smem_limit(std::map<std::pair<int, int>, size_t>& m, int dev, int prec) {
+    auto it = m.find({dev, prec});
+    if (it == m.end()) it = m.emplace(std::make_pair(dev, prec), (size_t)48 * 1024).first;
+    return it->second;
+}
 
 #define CK(call)                                                                                   \
     do {                                                                                           \
@@ -1121,11 +1257,21 @@ static int setup_sym(ygm_ctx* ctx, const std::vector<int>& eoff) {
             if (qo > INT32_MAX || qo < INT32_MIN) return 0;
             o2[sidx] = make_int2((int)qo, eoff[sidx]);
         }
-    // slots in padded-e order (neighbour class, dz, dy, dx): consecutive slots read neighbouring
-    // e values, which the L1 then serves (measured 10 % faster than the stencil order at N=32, k=2)
-    for (size_t c = 0; c < L.c1.size(); ++c)
-        std::stable_sort(o2.begin() + S.st_begin[c], o2.begin() + S.st_begin[c + 1],
-                         [](const int2& a, const int2& b) { return a.y < b.y; });
+    // per class: the upper slots, then the lower ones (k_qapply_s gives the two groups different
+    // L2 eviction hints), each group in padded-e order (neighbour class, dz, dy, dx) so that
+    // consecutive slots read neighbouring e values, which the L1 then serves
+    for (size_t c = 0; c < L.c1.size(); ++c) {
+        const int b0 = S.st_begin[c], b1 = S.st_begin[c + 1];
+        std::vector<int> idx(b1 - b0);
+        for (int i = 0; i < b1 - b0; ++i) idx[i] = b0 + i;
+        std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+            const int ua = S.st_slots[a].upper ? 0 : 1, ub = S.st_slots[b].upper ? 0 : 1;
+            return ua != ub ? ua < ub : o2[a].y < o2[b].y;
+        });
+        std::vector<int2> sorted(b1 - b0);
+        for (int i = 0; i < b1 - b0; ++i) sorted[i] = o2[idx[i]];
+        std::copy(sorted.begin(), sorted.end(), o2.begin() + b0);
+    }
     std::vector<SBlk> sb;
     for (int pass = 0; pass < 2; ++pass) {
         for (int vz = 0; vz < L.n; ++vz)
@@ -1182,7 +1328,7 @@ static int setup_device(ygm_ctx* ctx) {
         for (auto& I : L.inc1[c]) inc.push_back(DInc{{I.dcube[0], I.dcube[1], I.dcube[2]}, I.shape, I.loc});
         D.inc_end = (int)inc.size();
         D.pbase = (int)(c * np3);
-        D.pad_ = 0;
+        D.nup = S.n_upper.empty() ? 0 : S.n_upper[c];
     }
     std::vector<DSlot> slots(S.st_slots.size());
     for (size_t s = 0; s < slots.size(); ++s)
@@ -1203,7 +1349,7 @@ static int setup_device(ygm_ctx* ctx) {
         D.qoff = 0;
         D.inc_begin = D.inc_end = 0;
         D.pbase = (int)(c * np3);
-        D.pad_ = 0;
+        D.nup = 0;
         D.st_begin = (int)terms.size();
         if (L.c2[c].active) {
             // find a tet shape and local index carrying this class
@@ -1474,11 +1620,19 @@ static int setup_device(ygm_ctx* ctx) {
         ctx->nlb = (int)lb.size();
         ctx->nle = (int)le.size();
         if ((rc = upload(ctx, &ctx->lblks_b, lb)) || (rc = upload(ctx, &ctx->lblks_e, le))) return rc;
+        ctx->h_lblks_e = le;
         const size_t n2pad = (size_t)np3 * L.c2.size();
         CK(cudaMalloc(&ctx->xp, (size_t)ctx->n1pad * ctx->rs));
         CK(cudaMalloc(&ctx->bp, n2pad * ctx->rs));
         CK(cudaMemsetAsync(ctx->xp, 0, (size_t)ctx->n1pad * ctx->rs, ctx->stream));
         CK(cudaMemsetAsync(ctx->bp, 0, n2pad * ctx->rs, ctx->stream));
+    }
+    if (ctx->use_sym) {
+        // fused energy of one column: e_i x_i partials of the Q1 apply, the tet-sum counter, M2a
+        CK(cudaMalloc((void**)&ctx->qpart, (size_t)std::max(1, ctx->nsblks_all) * sizeof(double2)));
+        CK(cudaMalloc((void**)&ctx->ticket, sizeof(unsigned)));
+        CK(cudaMemsetAsync(ctx->ticket, 0, sizeof(unsigned), ctx->stream));
+        if ((rc = upload_real(ctx, &ctx->M2af, S.M2aloc))) return rc;
     }
     for (int i = 0; i < 2; ++i) CK(cudaEventCreateWithFlags(&ctx->damp_ev[i], cudaEventDisableTiming));
     // dynamic shared memory of the block kernels (slot / term tables of one class); above 48 KB
@@ -1492,23 +1646,25 @@ static int setup_device(ygm_ctx* ctx) {
     // set by one context would make another context's launches invalid)
     {
         std::lock_guard<std::mutex> lk(g_smem_mutex);
-        if (smem_q > g_smem_q[ctx->precision]) {
+        size_t& lim_q = smem_limit(g_smem_q, ctx->device, ctx->precision);
+        size_t& lim_e = smem_limit(g_smem_e, ctx->device, ctx->precision);
+        if (smem_q > lim_q) {
             if (smem_q > 48 * 1024) {
                 if (ctx->precision == YGM_FP64)
                     CK(cudaFuncSetAttribute(k_qapply_b<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_q));
                 else
                     CK(cudaFuncSetAttribute(k_qapply_b<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_q));
             }
-            g_smem_q[ctx->precision] = smem_q;
+            lim_q = smem_q;
         }
-        if (smem_e > g_smem_e[ctx->precision]) {
+        if (smem_e > lim_e) {
             if (smem_e > 48 * 1024) {
                 if (ctx->precision == YGM_FP64)
                     CK(cudaFuncSetAttribute(k_curlT_e_b<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_e));
                 else
                     CK(cudaFuncSetAttribute(k_curlT_e_b<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_e));
             }
-            g_smem_e[ctx->precision] = smem_e;
+            lim_e = smem_e;
         }
     }
     CK(cudaStreamSynchronize(ctx->stream));
@@ -1517,7 +1673,8 @@ static int setup_device(ygm_ctx* ctx) {
 
 // ------------------------------------------------------------------ launch helpers
 // x = Q1 e of the context state, read from the padded copy of e; all_rows = false computes only
-// the rows of the curl-carrying 1-forms (all that C x needs)
+// the rows of the curl-carrying 1-forms (all that C x needs).  On the upper-triangle path an
+// all-rows apply also leaves the per-block e_i x_i partials of W_n in ctx->qpart.
 static int launch_qapply(ygm_ctx* ctx, void* x, bool all_rows) {
     if (ctx->use_sym) {
         const int nb = all_rows ? ctx->nsblks_all : ctx->nsblks_act;
@@ -1525,12 +1682,15 @@ static int launch_qapply(ygm_ctx* ctx, void* x, bool all_rows) {
         const SBlk* blks = ctx->sblks + (all_rows ? ctx->nsblks_act : 0);
         time_begin(ctx, KQ);
         const size_t smem = (size_t)(ctx->max_ns + 8) * sizeof(int2);
-        if (ctx->precision == YGM_FP64)
-            k_qapply_s<double><<<nb, SBLOCK, smem, ctx->stream>>>(blks, ctx->c1, ctx->soff2, ctx->sg, (const double*)ctx->qsd,
-                                                                  (const double*)ctx->ep, (double*)x, (double*)ctx->xp);
-        else
-            k_qapply_s<float><<<nb, SBLOCK, smem, ctx->stream>>>(blks, ctx->c1, ctx->soff2, ctx->sg, (const float*)ctx->qsd,
-                                                                 (const float*)ctx->ep, (float*)x, (float*)ctx->xp);
+        if (ctx->precision == YGM_FP64) {
+            auto k = all_rows ? k_qapply_s<double, true> : k_qapply_s<double, false>;
+            k<<<nb, SBLOCK, smem, ctx->stream>>>(blks, ctx->c1, ctx->soff2, ctx->sg, (const double*)ctx->qsd,
+                                                 (const double*)ctx->ep, (double*)x, (double*)ctx->xp, ctx->qpart);
+        } else {
+            auto k = all_rows ? k_qapply_s<float, true> : k_qapply_s<float, false>;
+            k<<<nb, SBLOCK, smem, ctx->stream>>>(blks, ctx->c1, ctx->soff2, ctx->sg, (const float*)ctx->qsd,
+                                                 (const float*)ctx->ep, (float*)x, (float*)ctx->xp, ctx->qpart);
+        }
         time_end(ctx);
         ctx->launches++;
         return 0;
@@ -1561,11 +1721,11 @@ static int launch_curl_b(ygm_ctx* ctx, const void* x, const void* bin, void* bou
         if (ctx->precision == YGM_FP64)
             k_curl_b_s<double><<<ctx->nlb, SBLOCK, 0, ctx->stream>>>(ctx->lblks_b, ctx->c2, ctx->cterms, ctx->pg, ctx->sg.NX,
                                                                      (const double*)ctx->xp, (const double*)bin, (double*)bout,
-                                                                     (double*)ctx->bp, ctau);
+                                                                     (double*)ctx->bp, split_tau<double>(ctau));
         else
             k_curl_b_s<float><<<ctx->nlb, SBLOCK, 0, ctx->stream>>>(ctx->lblks_b, ctx->c2, ctx->cterms, ctx->pg, ctx->sg.NX,
                                                                     (const float*)ctx->xp, (const float*)bin, (float*)bout,
-                                                                    (float*)ctx->bp, (float)ctau);
+                                                                    (float*)ctx->bp, split_tau<float>(ctau));
     } else if (ctx->rshift) {
         if (ctx->precision == YGM_FP64)
             k_curl_b_r<double><<<ctx->nbblocks, BLOCK, 0, ctx->stream>>>(ctx->c1, ctx->c2, ctx->terms, ctx->bblocks, ctx->rshift,
@@ -1585,18 +1745,31 @@ static int launch_curl_b(ygm_ctx* ctx, const void* x, const void* bin, void* bou
     ctx->launches++;
     return 0;
 }
-static int launch_curlT_e(ygm_ctx* ctx, const void* b, void* e, double ctau) {
+static int launch_source(ygm_ctx* ctx, const double* amp_dev);
+// e += ctau C^T M2 b, then the dipole currents of this step when amp_dev != NULL (amp_dev =
+// this step's dt s(t_{n+1/2}) per source).  The one-column lattice path does both in one pass;
+// the other paths follow the e update with k_source.
+static int launch_curlT_e(ygm_ctx* ctx, const void* b, void* e, double ctau, const double* amp_dev) {
     time_begin(ctx, KE);
     if (ctx->use_sym && ctx->nlb && ctx->wterms && ctx->nle) {   // b was written to its padded copy by k_curl_b_s
         const size_t smem = (size_t)ctx->max_terms * (ctx->precision == YGM_FP64 ? sizeof(WTermL<double>) : sizeof(WTermL<float>));
+        const bool src = amp_dev && ctx->nsrc && ctx->lblks_es;
+        const SBlk* blks = src ? ctx->lblks_es : ctx->lblks_e;
+        const int nb = src ? ctx->nle_src : ctx->nle;
+        const double* amp = src ? amp_dev : nullptr;
         if (ctx->precision == YGM_FP64)
-            k_curlT_e_s<double><<<ctx->nle, SBLOCK, smem, ctx->stream>>>(ctx->lblks_e, ctx->c1, ctx->pbeg,
-                                                                        (const WTermL<double>*)ctx->wterms, ctx->pg, ctx->sg.NX,
-                                                                        (const double*)ctx->bp, (double*)e, ctau, (double*)ctx->ep);
+            k_curlT_e_s<double><<<nb, SBLOCK, smem, ctx->stream>>>(blks, ctx->c1, ctx->pbeg, (const WTermL<double>*)ctx->wterms,
+                                                                  ctx->pg, ctx->sg.NX, (const double*)ctx->bp, (double*)e,
+                                                                  split_tau<double>(ctau), (double*)ctx->ep, ctx->sbeg,
+                                                                  (const SrcE<double>*)ctx->sent, amp);
         else
-            k_curlT_e_s<float><<<ctx->nle, SBLOCK, smem, ctx->stream>>>(ctx->lblks_e, ctx->c1, ctx->pbeg,
-                                                                       (const WTermL<float>*)ctx->wterms, ctx->pg, ctx->sg.NX,
-                                                                       (const float*)ctx->bp, (float*)e, (float)ctau, (float*)ctx->ep);
+            k_curlT_e_s<float><<<nb, SBLOCK, smem, ctx->stream>>>(blks, ctx->c1, ctx->pbeg, (const WTermL<float>*)ctx->wterms,
+                                                                 ctx->pg, ctx->sg.NX, (const float*)ctx->bp, (float*)e,
+                                                                 split_tau<float>(ctau), (float*)ctx->ep, ctx->sbeg,
+                                                                 (const SrcE<float>*)ctx->sent, amp);
+        time_end(ctx);
+        ctx->launches++;
+        return 0;
     } else if (ctx->rshift) {
         if (!ctx->neblocks) {
         } else if (ctx->pterms) {
@@ -1645,6 +1818,7 @@ static int launch_curlT_e(ygm_ctx* ctx, const void* b, void* e, double ctau) {
     }
     time_end(ctx);
     ctx->launches++;
+    if (amp_dev) return launch_source(ctx, amp_dev);
     return 0;
 }
 static int launch_source(ygm_ctx* ctx, const double* amp_dev) {
@@ -1692,6 +1866,20 @@ static int launch_energy(ygm_ctx* ctx, const void* e, const void* x, const void*
         k_finish_r<<<1, 256, 0, ctx->stream>>>(ctx->part, p2, np, R, out);
         time_end(ctx);
         ctx->launches += 3;
+        return 0;
+    }
+    if (ctx->use_sym && ctx->qpart) {
+        // e^T x was summed by the all-rows k_qapply_s that produced x (per-block partials)
+        if (ctx->precision == YGM_FP64)
+            k_tet_energy<double, double><<<np, BLOCK, 0, ctx->stream>>>(ctx->tb, (const double*)ctx->M2af, (const double*)bn,
+                                                                        (const double*)bo, (const double*)ctx->inv_mu, ctx->part,
+                                                                        ctx->qpart, ctx->nsblks_all, ctx->ticket, out);
+        else
+            k_tet_energy<float, float><<<np, BLOCK, 0, ctx->stream>>>(ctx->tb, (const float*)ctx->M2af, (const float*)bn,
+                                                                      (const float*)bo, (const float*)ctx->inv_mu, ctx->part,
+                                                                      ctx->qpart, ctx->nsblks_all, ctx->ticket, out);
+        time_end(ctx);
+        ctx->launches++;
         return 0;
     }
     if (ctx->precision == YGM_FP64) {
@@ -1954,6 +2142,46 @@ static int set_sources(ygm_ctx* ctx, const ygm_source* src, int32_t n_src) {
         ds.end = (int)dofs.size();
         hs.push_back(ds);
     }
+    // one-column lattice path: the source entries of each k_curlT_e_s block, with extra blocks
+    // for curl-free classes (gradient 1-forms) that hold a source DoF
+    std::vector<SBlk> comb;
+    std::vector<int> sb;
+    std::vector<std::pair<int, std::pair<int, std::pair<int, double>>>> ent;   // (block, (tid, (source, w)))
+    if (ctx->use_sym && ctx->nle && ctx->n_rhs == 1) {
+        comb = ctx->h_lblks_e;
+        std::map<std::array<int, 3>, int> blk_of;
+        for (size_t i = 0; i < comb.size(); ++i) blk_of[{comb[i].cls, comb[i].vz, comb[i].t0}] = (int)i;
+        const int NX = ctx->sg.NX;
+        for (int q = 0; q < n_src; ++q)
+            for (int j = hs[q].begin; j < hs[q].end; ++j) {
+                int cls, v[3];
+                ctx->S.L.decode1(dofs[j], &cls, v);
+                const auto& bx = ctx->S.L.c1[cls].box;
+                const int t = v[1] * NX + v[0], base = bx.lo[1] * NX, t1 = (bx.lo[1] + bx.num[1]) * NX;
+                const int t0 = base + (t - base) / SBLOCK * SBLOCK;
+                auto it = blk_of.find({cls, v[2], t0});
+                int bi;
+                if (it == blk_of.end()) {
+                    bi = (int)comb.size();
+                    comb.push_back(SBlk{0, cls, v[2], t0, std::min(SBLOCK, t1 - t0)});
+                    blk_of[{cls, v[2], t0}] = bi;
+                } else {
+                    bi = it->second;
+                }
+                ent.push_back({bi, {t - t0, {q, w[j]}}});
+            }
+        std::stable_sort(ent.begin(), ent.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+        sb.assign(comb.size() + 1, 0);
+        for (const auto& e : ent) sb[e.first + 1]++;
+        for (size_t i = 0; i < comb.size(); ++i) sb[i + 1] += sb[i];
+    }
+    cudaFree(ctx->lblks_es);
+    cudaFree(ctx->sbeg);
+    cudaFree(ctx->sent);
+    ctx->lblks_es = nullptr;
+    ctx->sbeg = nullptr;
+    ctx->sent = nullptr;
+    ctx->nle_src = 0;
     cudaFree(ctx->dsrc);
     cudaFree(ctx->sdofs);
     cudaFree(ctx->sw);
@@ -1966,6 +2194,22 @@ static int set_sources(ygm_ctx* ctx, const ygm_source* src, int32_t n_src) {
     if ((rc = upload(ctx, &ctx->dsrc, hs)) || (rc = upload(ctx, &ctx->sdofs, dofs)) || (rc = upload(ctx, &ctx->spdofs, pdofs)) ||
         (rc = upload_real(ctx, &ctx->sw, w)))
         return rc;
+    if (!ent.empty()) {
+        auto fill = [&](auto* dummy) {
+            using R = std::remove_pointer_t<decltype(dummy)>;
+            std::vector<SrcE<R>> se(ent.size());
+            for (size_t i = 0; i < ent.size(); ++i)
+                se[i] = SrcE<R>{ent[i].second.first, ent[i].second.second.first, (R)ent[i].second.second.second};
+            SrcE<R>* d = nullptr;
+            int r2 = upload(ctx, &d, se);
+            ctx->sent = d;
+            return r2;
+        };
+        if ((rc = upload(ctx, &ctx->lblks_es, comb)) || (rc = upload(ctx, &ctx->sbeg, sb)) ||
+            (rc = ctx->precision == YGM_FP64 ? fill((double*)nullptr) : fill((float*)nullptr)))
+            return rc;
+        ctx->nle_src = (int)comb.size();
+    }
     ctx->nsrc = n_src;
     ctx->src_cache.assign(src, src + n_src);
     return 0;
@@ -2031,15 +2275,32 @@ int ygm_step(ygm_ctx* ctx, int64_t n, double dt, const ygm_source* src, int32_t 
         CK(cudaMemcpyAsync(ctx->damp[bsel], amp, namp * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
         amp_dev = ctx->damp[bsel];
     }
+    if (ctx->energy_every && n > 0) {
+        // the history grows to hold every record of this call (plus the two scratch records of
+        // ygm_energy at its end), so no W_n is ever dropped
+        const int64_t K = ctx->energy_every, first = (ctx->step + K - 1) / K, last = (ctx->step + n - 1) / K;
+        const int64_t need = ctx->hist_n + (last - first + 1) + 2;
+        if (need > ctx->hist_cap) {
+            const int64_t cap = std::max<int64_t>(need, 2 * ctx->hist_cap);
+            double* h = nullptr;
+            CK(cudaMalloc((void**)&h, (size_t)cap * ctx->n_rhs * sizeof(double)));
+            if (ctx->hist_n)
+                CK(cudaMemcpyAsync(h, ctx->hist, (size_t)ctx->hist_n * ctx->n_rhs * sizeof(double), cudaMemcpyDeviceToDevice,
+                                   ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            cudaFree(ctx->hist);
+            ctx->hist = h;
+            ctx->hist_cap = cap;
+        }
+    }
     for (int64_t i = 0; i < n; ++i) {
         void* bo = ctx->b[ctx->cur];
         void* bn = ctx->b[ctx->cur ^ 1];
-        const bool want_w = ctx->energy_every && ctx->step % ctx->energy_every == 0 && ctx->hist_n < ctx->hist_cap - 2;
+        const bool want_w = ctx->energy_every && ctx->step % ctx->energy_every == 0;
         launch_qapply(ctx, ctx->x, want_w);     // W_n needs e^T Q1 e over every row
         launch_curl_b(ctx, ctx->x, bo, bn, dt);
         if (want_w) launch_energy(ctx, ctx->e, ctx->x, bn, bo, ctx->hist + (size_t)ctx->n_rhs * ctx->hist_n++);
-        launch_curlT_e(ctx, bn, ctx->e, dt);
-        if (amp_dev && src_on[i]) launch_source(ctx, amp_dev + (size_t)i * ctx->nsrc);
+        launch_curlT_e(ctx, bn, ctx->e, dt, amp_dev && src_on[i] ? amp_dev + (size_t)i * ctx->nsrc : nullptr);
         ctx->cur ^= 1;
         ctx->step++;
     }
@@ -2078,7 +2339,7 @@ int ygm_energy(ygm_ctx* ctx, double* W, double* Htilde) {
 int ygm_energy_history(ygm_ctx* ctx, double* out, int64_t max_count, int64_t* count) {
     if (ctx && ctx->host_only) return fail(ctx, YGM_ENODEV, "context was created host-only (device = -1)");
     if (!ctx || !count) return fail(ctx, YGM_EINVAL, "NULL argument");
-    int64_t c = std::min<int64_t>(std::min<int64_t>(ctx->hist_n, ctx->hist_cap - 2), max_count);
+    int64_t c = std::min<int64_t>(ctx->hist_n, max_count);
     if (c > 0 && out)
         CK(cudaMemcpyAsync(out, ctx->hist, (size_t)c * ctx->n_rhs * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -2330,7 +2591,8 @@ void ygm_destroy(ygm_ctx* ctx) {
     }
     void* more[] = {ctx->qslots, ctx->qblocks, ctx->eblocks, ctx->bblocks, ctx->pterms, ctx->pbeg,
                     ctx->qsd,    ctx->soff2,   ctx->sblks,   ctx->xp,      ctx->bp,     ctx->wterms,
-                    ctx->cterms, ctx->lblks_b, ctx->lblks_e};
+                    ctx->cterms, ctx->lblks_b, ctx->lblks_e, ctx->qpart,  ctx->ticket, ctx->M2af,
+                    ctx->lblks_es, ctx->sbeg,    ctx->sent};
     for (void* p : more)
         if (p) cudaFree(p);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);

@@ -232,3 +232,18 @@ def test_nonuniform_mu_uses_per_tet_path():
     c.step(80, tau)
     e, b = c.get_state(synced=True)
     assert rel_l2(e, e_or) < FP64_TOL and rel_l2(b, bs_or) < FP64_TOL
+
+
+def test_energy_history_keeps_every_record():
+    """More W_n records than the initial history capacity (65,536): the history grows inside
+    ygm_step, every record is kept, and W_n stays conserved over the whole run."""
+    c = Y.Context(2, 1, precision=Y.YGM_FP64, energy_every=1)
+    rng = np.random.default_rng(21)
+    c.set_state(rng.standard_normal(c.N1), np.zeros(c.N2))
+    tau = 0.5 * c.tau_cfl
+    c.step(40000, tau)
+    c.step(30000, tau)
+    W = c.energy_history(max_count=1 << 20)
+    assert len(W) == 70000
+    assert np.max(np.abs(W - W[0])) / W[0] < 1e-11
+    c.close()
