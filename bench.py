@@ -116,48 +116,110 @@ def peaks():
 
 
 # ------------------------------------------------------------------ CPU oracle timing
-def oracle_sample(steps=20000, n=4):
-    """The FP64 CPU oracle as it stands, on a bounded sample of the workload: the same recipe on an
-    n^3 cube (eps seed 2000, same source), `steps` leapfrog steps; returns DoF-updates/s."""
+def oracle_model(n=5, k=2):
+    """The FP64 CPU oracle's operators for a bounded sample of the workload: the same recipe
+    (eps seed 2000, z-dipole seed 2001, dt = 0.5 tau_CFL) on an n^3 cube.  The set-up (SPAI) is
+    not part of the timed leapfrog."""
     from oracle import spai as SP
     from oracle.fem import FEM
-    from oracle.gym import GYM, DipoleSource
+    from oracle.gym import GYM
     from oracle.mesh import KuhnMesh
-    W = workload(n=n, k=2, leapfrog_steps=steps)
-    f = FEM(KuhnMesh(n, 2), eps=W["eps"])
+    W = workload(n=n, k=k, leapfrog_steps=0)
+    f = FEM(KuhnMesh(n, k), eps=W["eps"])
     M1 = f.M1()
     Q, _ = SP.gym_q1(f, M1)
     g = GYM(f.C(), f.M2(), Q, M1)
-    dt = 0.5 * g.tau_cfl()
+    return dict(f=f, g=g, dt=0.5 * g.tau_cfl(), W=W, n=n, k=k)
+
+
+def _oracle_leapfrog(model, steps):
+    """Time `steps` leapfrog steps of the oracle from rest with the workload's dipole; seconds."""
+    from oracle.gym import DipoleSource
+    f, g, W, dt = model["f"], model["g"], model["W"], model["dt"]
     src = [dict(x=W["x0"], d=W["d"], amp=1.0, omega=W["omega"], width_steps=W["width"])]
     J = DipoleSource(f, src, dt)
     e = np.zeros(f.mesh.N1)
     b = np.zeros(f.mesh.N2)
     t0 = time.perf_counter()
     g.run(e, b, dt, steps, source=J)
-    el = time.perf_counter() - t0
+    return time.perf_counter() - t0
+
+
+def _replica(args):
+    path, steps = args
+    import pickle
+    with open(path, "rb") as fh:
+        model = pickle.load(fh)
+    return _oracle_leapfrog(model, steps)
+
+
+def oracle_sample(model, steps, procs=1):
+    """DoF-updates/s of the oracle as it stands: one process, or `procs` spawned replicas of the
+    same sample running at once (the oracle itself is single-threaded).  Returns (rate, wall s)."""
+    f = model["f"]
     units = (f.mesh.N1 + f.mesh.N2) * steps
-    return units / el, el, dict(n=n, k=2, N1=f.mesh.N1, N2=f.mesh.N2, steps=steps)
+    if procs == 1:
+        el = _oracle_leapfrog(model, steps)
+        return units / el, el
+    import multiprocessing as mp
+    import pickle
+    import tempfile
+    with tempfile.NamedTemporaryFile(suffix=".pkl", delete=False) as fh:
+        pickle.dump(model, fh)
+        path = fh.name
+    try:
+        with mp.get_context("spawn").Pool(procs) as pool:
+            pool.map(_replica, [(path, 10)] * procs)          # import and unpickle in every worker
+            t0 = time.perf_counter()
+            pool.map(_replica, [(path, steps)] * procs)
+            el = time.perf_counter() - t0
+    finally:
+        os.unlink(path)
+    return procs * units / el, el
+
+
+def cpu_baseline_line(args):
+    """Single-thread and all-core rates of the oracle on the bounded sample, plus the first
+    (FP64, N = 4, k = 1, 1000 steps) workload timed in full."""
+    ncores = os.cpu_count() or 1
+    model = oracle_model(n=args.cpu_n)
+    v1, el1 = oracle_sample(model, args.cpu_steps)
+    vN, elN = oracle_sample(model, args.cpu_steps, procs=ncores)
+    f = model["f"]
+    c1 = oracle_model(n=4, k=1)
+    t_c1 = _oracle_leapfrog(c1, 1000)
+    sample = (f"FP64 CPU oracle (scipy sparse), same recipe on a {args.cpu_n}^3 cube, k=2 "
+              f"(N1={f.mesh.N1}, N2={f.mesh.N2}, Q1 nnz {model['g'].Q1.nnz}), {args.cpu_steps} leapfrog steps; "
+              f"value = {ncores} concurrent single-threaded replicas on {ncores} host cores; the rate per DoF "
+              f"of this sample stands in for the N=32 cavity (not measured at that size)")
+    return dict(value=vN, unit=UNIT, cores=ncores, kind="oracle", sample=sample,
+                single_thread=dict(value=v1, cores=1, seconds=el1), all_cores_seconds=elN,
+                first_workload_in_full=dict(workload="N=4, k=1, FP64, 1000 steps", seconds=t_c1,
+                                            value=(c1["f"].mesh.N1 + c1["f"].mesh.N2) * 1000 / t_c1))
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
+    ncores = os.cpu_count() or 1
+    model = oracle_model(n=args.cpu_n)
     vals = []
     for i in range(args.warmup + args.steps):
-        v, el, info = oracle_sample(steps=args.cpu_steps)
+        v, el = oracle_sample(model, args.cpu_steps, procs=ncores)
         if i >= args.warmup:
             vals.append((v, el))
     value = float(np.mean([v for v, _ in vals]))
     ms = float(np.mean([el for _, el in vals]) * 1e3)
-    sample = (f"FP64 CPU oracle (scipy sparse, single thread), same recipe on a {info['n']}^3 cube, k=2 "
-              f"(N1={info['N1']}, N2={info['N2']}), {info['steps']} leapfrog steps per step")
+    f = model["f"]
+    sample = (f"FP64 CPU oracle (scipy sparse), same recipe on a {args.cpu_n}^3 cube, k=2 "
+              f"(N1={f.mesh.N1}, N2={f.mesh.N2}), {args.cpu_steps} leapfrog steps per step, "
+              f"{ncores} concurrent single-threaded replicas on {ncores} host cores")
     line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
                 warmup=args.warmup, ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f64", data="synthetic",
                 config=dict(workload="PEC cube N=32, k=2, eps~U[1,4) seed 2000, z-dipole, 2000 steps "
-                                     "(oracle timed on a bounded N=4 sample)"),
-                cpu_baseline=dict(value=value, unit=UNIT, cores=1, kind="oracle", sample=sample),
+                                     f"(oracle timed on a bounded N={args.cpu_n} sample)"),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=ncores, kind="oracle", sample=sample),
                 e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
@@ -189,7 +251,7 @@ def run_ours(args, rank, world, local_rank):
     W = workload(n=args.n, k=args.order, leapfrog_steps=args.leapfrog_steps, rhs=args.rhs)
     R = args.rhs
     stream = torch.cuda.current_stream()
-    prec = Y.YGM_FP32 if args.precision == "fp32" else Y.YGM_FP64
+    prec = dict(fp32=Y.YGM_FP32, fp64=Y.YGM_FP64, tf32=Y.YGM_FP32_TC_TF32, tf32x3=Y.YGM_FP32_TC_3XTF32)[args.precision]
     tb = time.perf_counter()
     # the timed context also records the conserved energy every 100 steps (row A-5)
     ctx = Y.Context(W["n"], W["k"], eps=W["eps"], precision=prec, device=local_rank, stream=stream.cuda_stream,
@@ -197,7 +259,7 @@ def run_ours(args, rank, world, local_rank):
     setup_s = time.perf_counter() - tb
     dt = 0.5 * ctx.tau_cfl
     src = source_for(W, dt)
-    tdt = torch.float32 if prec == Y.YGM_FP32 else torch.float64
+    tdt = torch.float64 if prec == Y.YGM_FP64 else torch.float32
     ze = torch.zeros(ctx.N1 * R, dtype=tdt, device="cuda")
     zb = torch.zeros(ctx.N2 * R, dtype=tdt, device="cuda")
     units = (ctx.N1 + ctx.N2) * R * W["steps"]
@@ -247,7 +309,7 @@ def run_ours(args, rank, world, local_rank):
         ctx.get_state(synced=True, out_e=oe, out_b=ob)
     e2e_s = (time.perf_counter() - t0) / args.steps
     e2e_val, _ = aggregate(units, e2e_s, dist, device="cuda")
-    rs = 4 if prec == Y.YGM_FP32 else 8
+    rs = 8 if prec == Y.YGM_FP64 else 4
 
     # roofline of the dominant kernel (Q1 apply), from the instrumented run.  Algorithmic bytes of
     # one launch = the distinct Q1 values its rows use (a symmetric pair once) + e read + x
@@ -308,14 +370,11 @@ def run_ours(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, el, info = oracle_sample(steps=args.cpu_steps)
-        cpu = dict(value=v, unit=UNIT, cores=1, kind="oracle",
-                   sample=(f"FP64 oracle, same recipe on a {info['n']}^3 cube (N1={info['N1']}, N2={info['N2']}), "
-                           f"{info['steps']} steps, {el:.1f} s"))
+        cpu = cpu_baseline_line(args)
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                     ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None,
-                    dtype="f32" if prec == Y.YGM_FP32 else "f64", data="synthetic",
+                    dtype="f64" if prec == Y.YGM_FP64 else "f32", data="synthetic",
                     config=dict(workload=(f"PEC cube N={W['n']} (6N^3={6 * W['n'] ** 3} Kuhn tets), k={W['k']}, "
                                           f"eps~U[1,4) seed 2000, z-dipole seed 2001, dt=0.5 tau_CFL, "
                                           f"{W['steps']} leapfrog steps per step") if R == 1 else
@@ -352,12 +411,14 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "tf32", "tf32x3"],
+                    help="tf32 / tf32x3: batched C^T M2 on tensor cores (needs --rhs 32, 64 or 128)")
     ap.add_argument("--n", type=int, default=32)
     ap.add_argument("--order", type=int, default=2)
     ap.add_argument("--leapfrog-steps", type=int, default=2000)
-    ap.add_argument("--cpu-steps", type=int, default=20000,
-                    help="leapfrog steps of the timed FP64 oracle sample (about 10 s on one core)")
+    ap.add_argument("--cpu-steps", type=int, default=5000,
+                    help="leapfrog steps of the timed FP64 oracle sample (about 5 s on one core)")
+    ap.add_argument("--cpu-n", type=int, default=5, help="cubes per side of the oracle sample")
     ap.add_argument("--energy-every", type=int, default=100)
     ap.add_argument("--rhs", type=int, default=1, help="right-hand-side columns (batched excitations)")
     ap.add_argument("--no-accuracy", action="store_true")

@@ -52,11 +52,20 @@ extern "C" {
 #define YGM_ENOMEM   -4   /* host or device allocation failed */
 #define YGM_ECUDA    -5   /* a CUDA call failed (message carries cudaGetErrorString) */
 #define YGM_ETIMEOUT -6   /* an iterative host solve (SPAI-OP PCG, cavity modes) reached its
-                             iteration limit without converging */
+                             iteration limit without converging, or a device wait of the tensor-core
+                             kernel gave up (reported by the next ygm_get_state / ygm_energy) */
 #define YGM_ENODEV   -7   /* no CUDA device is available */
 
 #define YGM_FP64 0        /* fields, Q1 and arithmetic in double */
 #define YGM_FP32 1        /* fields, Q1 and arithmetic in float; diagnostics in double */
+/* FP32 fields and kernels, with the one dense contraction of the batched mode -- C^T M2 of every
+ * curl-carrying class at a batch of lattice points, (points x columns) x |U| times |U| x classes
+ * (Eq. dTIsFiniteDiff with the merged constant stencil of a uniform mu) -- on the tcgen05 tensor
+ * cores with FP32 accumulation.  Needs n_rhs = 32, 64 or 128, a uniform mu and order 1 or 2
+ * (YGM_EINVAL otherwise).  Q1 e stays on FP32 SIMT: a TF32 Q1 would not stay positive definite
+ * (its relative spacing 2^-11 exceeds lambda_min / lambda_max of Q1, e.g. 1.8e-4 at N = 32, k = 2). */
+#define YGM_FP32_TC_TF32   2   /* operands truncated to TF32 (one pass): ~1e-3 relative per product */
+#define YGM_FP32_TC_3XTF32 3   /* operands split hi + lo in TF32, three passes: ~2^-21 per product */
 
 #define YGM_Q1_DEFAULT 0  /* k = 1: S(M1); k >= 2: S(M1^2) in the orthogonalised basis */
 #define YGM_Q1_DIAG    1  /* S(1): q_l = M_ll / sum_k M_kl^2 */
@@ -71,7 +80,7 @@ typedef struct {
 } ygm_mesh;
 
 typedef struct {
-    int32_t precision;     /* YGM_FP64 or YGM_FP32 */
+    int32_t precision;     /* YGM_FP64, YGM_FP32, YGM_FP32_TC_TF32 or YGM_FP32_TC_3XTF32 */
     int32_t q1_pattern;    /* YGM_Q1_* */
     int32_t n_rhs;         /* R >= 1 right-hand sides (independent excitations) */
     int32_t energy_every;  /* record W_n every K steps inside ygm_step; 0 = off */
@@ -229,6 +238,60 @@ int ygm_cavity_modes(ygm_ctx* ctx, int32_t count, double* V, double* omega_sq, i
  * thread count.  Q1 from ygm_set_q1 or ygm_spai_op is treated as if it were the column SPAI, which
  * it is not.  Errors: YGM_EINVAL, YGM_ENOTSPD. */
 int ygm_q1_vjp(ygm_ctx* ctx, const double* q1bar, double* grad_eps);
+
+/* Gradient of a probe-region field energy with respect to the per-tet permittivity, by the
+ * discrete adjoint of the leapfrog (the transposed shear maps of Eq. shearMaps, newest step first)
+ * on the device, chained through the SPAI derivative of ygm_q1_vjp on the host.  The paper defines
+ * no loss; this one is
+ *     L = dt sum_{n=0}^{nsteps-1} [1/2 x_n^T M1^R x_n + 1/2 b_{n+1/2}^T M2^R b_{n+1/2}],  x_n = Q1 e_n,
+ * with M1^R, M2^R the mass matrices assembled over the tets t with region[t] != 0 only, for the
+ * leapfrog run from rest (e_0 = 0, b = 0) under the given dipole sources (as ygm_step), dt fixed.
+ * region: 6 n^3 bytes (tet order of ygm_create).  The forward run keeps the state every
+ * checkpoint_every steps; the reverse sweep recomputes each segment from its checkpoint
+ * (device memory: (nsteps / checkpoint_every) (N1 + N2) + checkpoint_every (2 N1 + N2) values,
+ * plus one upper-triangle copy of Q1 for dL/dQ1).  Outputs: *loss; grad_eps[6 n^3] (may be NULL:
+ * loss only, no host SPAI derivative).  Runs in the context precision.  Needs a one-column context
+ * with uniform mu on the lattice path (YGM_EINVAL otherwise).  Overwrites the context state: it is
+ * left at rest (e = b = 0, step 0).  Errors: YGM_EINVAL, YGM_ECFL, YGM_ECUDA, YGM_ENOMEM,
+ * YGM_ENOTSPD (a normal matrix of the SPAI derivative). */
+int ygm_adjoint(ygm_ctx* ctx, int64_t nsteps, double dt, const ygm_source* src, int32_t n_src, const uint8_t* region,
+                int32_t checkpoint_every, double* loss, double* grad_eps);
+
+/* ---- uneven batch: many independent cavities stepped by one persistent launch ----------------
+ * The paper steps one field; batching independent cavities of different size n and order k is a
+ * throughput pattern of this library.  Each member is a one-column context (its own mesh, eps,
+ * Q1 and state, YGM_FP32 or YGM_FP64, all of one precision and device, uniform mu); the batch
+ * holds pointers to them and they must outlive it.  One ygm_batch_step runs, for every member,
+ * exactly the leapfrog of ygm_step (Eq. YeeLeapfrog in the form of Eq. preYeeFEECEqns, the
+ * member's own dt and dipole), as a single cooperative kernel: per step three phases (Q1 e, the
+ * b update, the e update with the source) over (cavity, block) work items separated by grid-wide
+ * barriers whose waits have an iteration cap.  Members' states are read and written through the
+ * usual per-context calls (ygm_set_state, ygm_get_state, ygm_energy).  Errors: YGM_EINVAL,
+ * YGM_ENODEV, YGM_ECUDA, YGM_ENOMEM (creation messages via ygm_last_error(NULL)). */
+typedef struct ygm_batch ygm_batch;
+int ygm_batch_create(ygm_ctx* const* cavities, int32_t count, ygm_batch** out);
+/* nsteps leapfrog steps of every member: dt[count] (each <= its tau_CFL, else YGM_ECFL and nothing
+ * runs); src = NULL or one dipole per member (src[i].rhs ignored).  use_graph = 1 replays the
+ * launch from a CUDA graph captured on first use (recaptured when nsteps or the launch shape
+ * changes).  Asynchronous on the first member's stream, ordered after and before the members' own
+ * streams; a barrier timeout is reported by ygm_batch_status. */
+int ygm_batch_step(ygm_batch* batch, int64_t nsteps, const double* dt, const ygm_source* src, int32_t use_graph);
+/* Synchronise and report a grid-barrier timeout of an earlier launch (YGM_ETIMEOUT; the flag stays
+ * set until ygm_batch_status_clear).  After a timeout the members' states are invalid. */
+int ygm_batch_status(ygm_batch* batch);
+int ygm_batch_status_clear(ygm_batch* batch);
+/* Polls (each ~0.1-1 us) a grid-barrier wait makes before it gives up; default 2^24.  0 makes every
+ * wait that does not find the barrier already complete give up at once, which forces the timeout
+ * path (used to test it). */
+int ygm_batch_wait_limit(ygm_batch* batch, int64_t polls);
+/* Autotuner: times trial_steps steps for every launch shape (1..4 CTAs per SM, within the
+ * occupancy limit) and work order (0: cavity by cavity; 1: Q1 items longest stencil first, the
+ * other phases interleaved across cavities), keeps the fastest, and restores every member's state
+ * and time.  Outputs (may be NULL): the choice and its milliseconds per step. */
+int ygm_batch_tune(ygm_batch* batch, int32_t trial_steps, const double* dt, const ygm_source* src, int32_t* ctas_per_sm,
+                   int32_t* order, double* ms_per_step);
+const char* ygm_batch_last_error(const ygm_batch* batch);
+void ygm_batch_destroy(ygm_batch* batch);   /* NULL-safe; does not destroy the members */
 
 /* SPD check of Q1 (Sec. 5.1, practical considerations): Lanczos estimates of the smallest and
  * largest eigenvalue before any shift, the diagonal shift applied (0 if none), lambda_max(Q1 P2),

@@ -14,12 +14,15 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libygm.so")
 
 YGM_OK, YGM_EINVAL, YGM_ECFL, YGM_ENOTSPD, YGM_ENOMEM, YGM_ECUDA, YGM_ETIMEOUT, YGM_ENODEV = 0, -1, -2, -3, -4, -5, -6, -7
-YGM_FP64, YGM_FP32 = 0, 1
+YGM_FP64, YGM_FP32, YGM_FP32_TC_TF32, YGM_FP32_TC_3XTF32 = 0, 1, 2, 3
 YGM_Q1_DEFAULT, YGM_Q1_DIAG, YGM_Q1_SM1, YGM_Q1_SM1SQ = 0, 1, 2, 3
 
 EXPORTED = ["ygm_create", "ygm_create_like", "ygm_sizes", "ygm_set_state", "ygm_get_state", "ygm_project_E", "ygm_step", "ygm_step_noalloc",
             "ygm_energy", "ygm_energy_history", "ygm_time", "ygm_export_q1", "ygm_set_q1", "ygm_spai_op", "ygm_cavity_modes", "ygm_q1_vjp", "ygm_q1_info",
-            "ygm_local_blocks", "ygm_kernel_timing", "ygm_kernel_times", "ygm_launch_count",
+            "ygm_local_blocks", "ygm_kernel_timing", "ygm_kernel_times", "ygm_launch_count", "ygm_adjoint",
+            "ygm_batch_create", "ygm_batch_step", "ygm_batch_status", "ygm_batch_status_clear", "ygm_batch_wait_limit",
+            "ygm_batch_tune", "ygm_batch_last_error",
+            "ygm_batch_destroy",
             "ygm_qapply_counts", "ygm_last_error", "ygm_destroy"]
 KERNEL_KINDS = ["k_qapply", "k_curl_b", "k_curlT_e", "k_source", "k_energy"]
 
@@ -72,12 +75,21 @@ def load_library(path=LIB_PATH):
         "ygm_spai_op": (C.c_int, [P, pD, C.c_int32, D, C.c_int32, D, pI32, pD]),
         "ygm_cavity_modes": (C.c_int, [P, C.c_int32, pD, pD, C.c_int32, D, pI32]),
         "ygm_q1_vjp": (C.c_int, [P, pD, pD]),
+        "ygm_adjoint": (C.c_int, [P, I64, D, C.POINTER(ygm_source), C.c_int32, C.POINTER(C.c_uint8), C.c_int32, pD, pD]),
         "ygm_q1_info": (C.c_int, [P, pD, pD, pD, pD, pI32, pI32]),
         "ygm_local_blocks": (C.c_int, [P, pI32, pI32, pD, pD]),
         "ygm_kernel_timing": (C.c_int, [P, C.c_int]),
         "ygm_kernel_times": (C.c_int, [P, pD, pI64]),
         "ygm_launch_count": (C.c_int, [P, pI64]),
         "ygm_qapply_counts": (C.c_int, [P, C.c_int, pI64, pI64, pI64]),
+        "ygm_batch_create": (C.c_int, [C.POINTER(P), C.c_int32, C.POINTER(P)]),
+        "ygm_batch_step": (C.c_int, [P, I64, pD, C.POINTER(ygm_source), C.c_int32]),
+        "ygm_batch_status": (C.c_int, [P]),
+        "ygm_batch_status_clear": (C.c_int, [P]),
+        "ygm_batch_wait_limit": (C.c_int, [P, I64]),
+        "ygm_batch_tune": (C.c_int, [P, C.c_int32, pD, C.POINTER(ygm_source), pI32, pI32, pD]),
+        "ygm_batch_last_error": (C.c_char_p, [P]),
+        "ygm_batch_destroy": (None, [P]),
         "ygm_last_error": (C.c_char_p, [P]),
         "ygm_destroy": (None, [P]),
     }
@@ -193,16 +205,22 @@ class Context:
         self._check(_lib.ygm_project_E(self._h, self._cb, None, rhs))
 
     def step(self, n, dt, sources=()):
-        arr = (ygm_source * max(1, len(sources)))()
-        for i, s in enumerate(sources):
-            arr[i].x[:] = list(map(float, s["x"]))
-            arr[i].d[:] = list(map(float, s["d"]))
-            arr[i].amp = float(s.get("amp", 1.0))
-            arr[i].omega = float(s["omega"])
-            arr[i].t0 = float(s["t0"])
-            arr[i].sigma = float(s["sigma"])
-            arr[i].rhs = int(s.get("rhs", 0))
-        self._check(_lib.ygm_step(self._h, int(n), float(dt), arr, len(sources)))
+        self._check(_lib.ygm_step(self._h, int(n), float(dt), _source_array(sources), len(sources)))
+
+    def adjoint(self, nsteps, dt, sources, region, checkpoint_every=100, gradient=True):
+        """(L, dL/d eps) of the probe-region energy of ygm_adjoint: the leapfrog from rest under
+        `sources` for `nsteps` steps of `dt`, region = boolean per tet.  gradient=False returns
+        (L, None) without the reverse sweep's host SPAI derivative.  Leaves the state at rest."""
+        T = 6 * self.n ** 3
+        reg = np.ascontiguousarray(np.asarray(region).astype(np.uint8))
+        if reg.shape != (T,):
+            raise ValueError(f"region must have 6 n^3 = {T} entries")
+        L = C.c_double()
+        g = np.zeros(T) if gradient else None
+        self._check(_lib.ygm_adjoint(self._h, int(nsteps), float(dt), _source_array(sources), len(sources),
+                                     reg.ctypes.data_as(C.POINTER(C.c_uint8)), int(checkpoint_every), C.byref(L),
+                                     g.ctypes.data_as(C.POINTER(C.c_double)) if gradient else None))
+        return L.value, g
 
     def step_noalloc(self, e, b_in, b_out, dt):
         """One leapfrog step on caller-owned device tensors, no device allocation (ygm_step_noalloc)."""
@@ -327,6 +345,99 @@ class Context:
         r, u, st = C.c_int64(), C.c_int64(), C.c_int64()
         self._check(_lib.ygm_qapply_counts(self._h, 1 if all_rows else 0, C.byref(r), C.byref(u), C.byref(st)))
         return r.value, u.value, st.value
+
+
+class Batch:
+    """Independent one-column contexts (any n, order) stepped together by one persistent launch
+    (ygm_batch_*).  The contexts stay usable for set_state / get_state / energy and must outlive
+    the batch."""
+
+    def __init__(self, contexts):
+        self._ctx = list(contexts)
+        hs = (C.c_void_p * len(self._ctx))(*[c._h.value for c in self._ctx])
+        self._h = C.c_void_p()
+        rc = _lib.ygm_batch_create(hs, len(self._ctx), C.byref(self._h))
+        if rc:
+            raise YgmError(rc, _lib.ygm_last_error(None).decode())
+
+    def _check(self, rc):
+        if rc:
+            raise YgmError(rc, _lib.ygm_batch_last_error(self._h).decode())
+
+    def _args(self, dts, sources):
+        d = np.ascontiguousarray(dts, np.float64)
+        assert d.shape == (len(self._ctx),)
+        src = _source_array(sources) if sources is not None else None
+        return d, src
+
+    def step(self, nsteps, dts, sources=None, use_graph=False):
+        d, src = self._args(dts, sources)
+        self._check(_lib.ygm_batch_step(self._h, int(nsteps), d.ctypes.data_as(C.POINTER(C.c_double)), src,
+                                        1 if use_graph else 0))
+
+    def status(self):
+        self._check(_lib.ygm_batch_status(self._h))
+
+    def status_clear(self):
+        self._check(_lib.ygm_batch_status_clear(self._h))
+
+    def wait_limit(self, polls):
+        self._check(_lib.ygm_batch_wait_limit(self._h, int(polls)))
+
+    def tune(self, trial_steps, dts, sources=None):
+        """Autotune the launch shape; returns (CTAs per SM, work order, ms per step)."""
+        d, src = self._args(dts, sources)
+        c, o, ms = C.c_int32(), C.c_int32(), C.c_double()
+        self._check(_lib.ygm_batch_tune(self._h, int(trial_steps), d.ctypes.data_as(C.POINTER(C.c_double)), src,
+                                        C.byref(c), C.byref(o), C.byref(ms)))
+        return c.value, o.value, ms.value
+
+    def close(self):
+        if self._h:
+            _lib.ygm_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _source_array(sources):
+    arr = (ygm_source * max(1, len(sources)))()
+    for i, s in enumerate(sources):
+        arr[i].x[:] = list(map(float, s["x"]))
+        arr[i].d[:] = list(map(float, s["d"]))
+        arr[i].amp = float(s.get("amp", 1.0))
+        arr[i].omega = float(s["omega"])
+        arr[i].t0 = float(s["t0"])
+        arr[i].sigma = float(s["sigma"])
+        arr[i].rhs = int(s.get("rhs", 0))
+    return arr
+
+
+def probe_energy(eps, n, order, nsteps, dt, sources, region, checkpoint_every=100, precision=YGM_FP64, device=0):
+    """The probe-region energy of ygm_adjoint as a differentiable function of the per-tet
+    permittivity (a torch tensor of 6 n^3 entries): forward builds the operators for eps and runs
+    the leapfrog, backward returns dL/d eps from the device adjoint.  dt is held fixed."""
+    import torch
+
+    class _ProbeEnergy(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, e):
+            eh = e.detach().to("cpu", torch.float64).numpy()
+            with Context(n, order, eps=eh, precision=precision, device=device) as c:
+                L, g = c.adjoint(nsteps, dt, sources, region, checkpoint_every=checkpoint_every, gradient=True)
+            fctx.save_for_backward(torch.as_tensor(g, dtype=e.dtype, device=e.device))
+            return torch.tensor(L, dtype=e.dtype, device=e.device)
+
+        @staticmethod
+        def backward(fctx, gout):
+            (g,) = fctx.saved_tensors
+            return gout * g
+
+    return _ProbeEnergy.apply(eps)
 
 
 def pulse_source(x, d, omega, dt, width_steps=20.0, amp=1.0, t0_sigmas=4.0, rhs=0):

@@ -211,19 +211,22 @@ struct KSum {
         }
     }
 };
+// sixteen slots per round: all 32 loads are in flight before the first of them is consumed (the
+// kernel is bound by load latency; measured 212 us against 233 us with eight at N=32, k=2)
 template <typename real>
 __device__ __forceinline__ void qs_run(KSum<real>& a, const int2* s_o2, int s, int send, const real* q, const real* e0,
                                        unsigned long long pol) {
-    for (; s + 8 <= send; s += 8) {
-        real qv[8], ev[8];
+    constexpr int U = 16;
+    for (; s + U <= send; s += U) {
+        real qv[U], ev[U];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < U; ++u) {
             const int2 o = s_o2[s + u];
             qv[u] = ld_l2hint(q + o.x, pol);
             ev[u] = __ldg(e0 + o.y);
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) a.add(qv[u], ev[u]);
+        for (int u = 0; u < U; ++u) a.add(qv[u], ev[u]);
     }
     for (; s < send; ++s) {
         const int2 o = s_o2[s];
@@ -260,13 +263,11 @@ static Tau<real> split_tau(double t) {
     const real hi = (real)t;
     return Tau<real>{hi, (real)(t - (double)hi)};
 }
-// b_out = b_in - ctau C x; also bp <- b_out
+// b_out = b_in - ctau C x; also bp <- b_out (the rows of one block)
 template <typename real>
-__global__ void __launch_bounds__(SBLOCK) k_curl_b_s(const SBlk* __restrict__ blks, const DCls* __restrict__ c2,
-                                                     const CTermL* __restrict__ terms, PadGeo g, int NX,
-                                                     const real* __restrict__ xp, const real* b_in, real* b_out,
-                                                     real* __restrict__ bp, Tau<real> ctau) {
-    const SBlk B = blks[blockIdx.x];
+__device__ __forceinline__ void curl_b_rows(const SBlk& B, const DCls* __restrict__ c2, const CTermL* __restrict__ terms,
+                                            PadGeo g, int NX, const real* __restrict__ xp, const real* b_in, real* b_out,
+                                            real* __restrict__ bp, Tau<real> ctau) {
     const DCls C = c2[B.cls];
     if ((int)threadIdx.x >= B.cnt) return;
     const int t = B.t0 + (int)threadIdx.x;
@@ -285,6 +286,13 @@ __global__ void __launch_bounds__(SBLOCK) k_curl_b_s(const SBlk* __restrict__ bl
     b_out[gi] = v;
     bp[C.pbase + p] = v;
 }
+template <typename real>
+__global__ void __launch_bounds__(SBLOCK) k_curl_b_s(const SBlk* __restrict__ blks, const DCls* __restrict__ c2,
+                                                     const CTermL* __restrict__ terms, PadGeo g, int NX,
+                                                     const real* __restrict__ xp, const real* b_in, real* b_out,
+                                                     real* __restrict__ bp, Tau<real> ctau) {
+    curl_b_rows(blks[blockIdx.x], c2, terms, g, NX, xp, b_in, b_out, bp, ctau);
+}
 // A dipole source DoF inside a block of k_curlT_e_s: thread, source index, weight d . Lambda1_i(x0).
 template <typename real>
 struct SrcE {
@@ -296,19 +304,14 @@ struct SrcE {
 // currents of this step are subtracted in the same pass: e_i -= amp[s] w_i for the entries
 // sbeg[block] .. sbeg[block + 1] (amp[s] = dt s_s(t_{n+1/2}), host FP64).  Blocks of classes that
 // carry no curl appear in the launch only when a source DoF lies in them; their stencil is empty.
+// the rows of one block; s_t holds the class's merged terms (loaded by the caller), item is the
+// block's index in the source tables
 template <typename real>
-__global__ void __launch_bounds__(SBLOCK) k_curlT_e_s(const SBlk* __restrict__ blks, const DCls* __restrict__ c1,
-                                                      const int* __restrict__ pbeg, const WTermL<real>* __restrict__ terms,
-                                                      PadGeo g, int NX, const real* __restrict__ bp, real* __restrict__ e,
-                                                      Tau<real> ctau, real* __restrict__ ep, const int* __restrict__ sbeg,
-                                                      const SrcE<real>* __restrict__ sent, const double* __restrict__ amp) {
-    extern __shared__ __align__(16) unsigned char s_raw[];
-    WTermL<real>* s_t = reinterpret_cast<WTermL<real>*>(s_raw);
-    const SBlk B = blks[blockIdx.x];
+__device__ __forceinline__ void curlT_e_rows(const SBlk& B, const DCls* __restrict__ c1, const WTermL<real>* s_t, int nt,
+                                             PadGeo g, int NX, const real* __restrict__ bp, real* __restrict__ e,
+                                             Tau<real> ctau, real* __restrict__ ep, const int* __restrict__ sbeg,
+                                             const SrcE<real>* __restrict__ sent, const double* __restrict__ amp, int item) {
     const DCls C = c1[B.cls];
-    const int tb = pbeg[B.cls], nt = pbeg[B.cls + 1] - tb;
-    for (int s = threadIdx.x; s < nt; s += blockDim.x) s_t[s] = terms[tb + s];
-    __syncthreads();
     if ((int)threadIdx.x >= B.cnt) return;
     const int t = B.t0 + (int)threadIdx.x;
     const int vy = t / NX, vx = t - vy * NX;
@@ -329,10 +332,24 @@ __global__ void __launch_bounds__(SBLOCK) k_curlT_e_s(const SBlk* __restrict__ b
     const long long gi = C.off + ((long long)(B.vz - C.lo[2]) * C.num[1] + ry) * C.num[0] + rx;
     real v = fma(ctau.lo, acc, fma(ctau.hi, acc, e[gi]));
     if (amp)
-        for (int i = sbeg[blockIdx.x]; i < sbeg[blockIdx.x + 1]; ++i)
+        for (int i = sbeg[item]; i < sbeg[item + 1]; ++i)
             if (sent[i].tid == (int)threadIdx.x) v -= (real)amp[sent[i].src] * sent[i].w;
     e[gi] = v;
     ep[C.pbase + p] = v;
+}
+template <typename real>
+__global__ void __launch_bounds__(SBLOCK) k_curlT_e_s(const SBlk* __restrict__ blks, const DCls* __restrict__ c1,
+                                                      const int* __restrict__ pbeg, const WTermL<real>* __restrict__ terms,
+                                                      PadGeo g, int NX, const real* __restrict__ bp, real* __restrict__ e,
+                                                      Tau<real> ctau, real* __restrict__ ep, const int* __restrict__ sbeg,
+                                                      const SrcE<real>* __restrict__ sent, const double* __restrict__ amp) {
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    WTermL<real>* s_t = reinterpret_cast<WTermL<real>*>(s_raw);
+    const SBlk B = blks[blockIdx.x];
+    const int tb = pbeg[B.cls], nt = pbeg[B.cls + 1] - tb;
+    for (int s = threadIdx.x; s < nt; s += blockDim.x) s_t[s] = terms[tb + s];
+    __syncthreads();
+    curlT_e_rows(B, c1, s_t, nt, g, NX, bp, e, ctau, ep, sbeg, sent, amp, (int)blockIdx.x);
 }
 
 // ep (padded) <- e (compact), one block per (class, z-plane)
@@ -819,7 +836,7 @@ __device__ Neu block_reduce(Neu v) {
 
 // x = Q1 e on the upper-triangle lattice (see the storage notes above k_qapply_s's helpers)
 template <typename real, bool ENERGY>
-__global__ void __launch_bounds__(SBLOCK) k_qapply_s(const SBlk* __restrict__ blks, const DCls* __restrict__ c1,
+__global__ void __launch_bounds__(SBLOCK, 1) k_qapply_s(const SBlk* __restrict__ blks, const DCls* __restrict__ c1,
                                                      const int2* __restrict__ soff2, SymGeo g,
                                                      const real* __restrict__ qs, const real* __restrict__ ep,
                                                      real* __restrict__ x, real* __restrict__ xp, double2* part) {
@@ -1057,6 +1074,404 @@ __global__ void k_finish_r(const double2* __restrict__ p1, const double2* __rest
     }
 }
 
+// ------------------------------------------------------------------ e += ctau C^T M2 b on tensor cores (R >= 32 columns)
+// With a uniform permeability C^T M2 is one constant stencil per 1-form class (the merged weights).
+// Over the union U of the (2-form class, offset) terms of every curl-carrying class it is a dense
+// matrix W (classes x K), the same at every lattice point, so for a batch of P lattice points
+// (P R = 128 rows) the update of all classes is one GEMM with a shared operand:
+//     D[(p, r), j] = sum_k Bg[(p, r), k] W[j, k],   Bg[(p, r), k] = b[(U_k at v_p), r]
+// run as tcgen05.mma kind::tf32 with M = 128 (rows = point x column), N = classes (padded to 16),
+// K = |U| (padded to 8), D in tensor memory, FP32 accumulation.  A (the gathered b) and B (W^T)
+// are K-major, no swizzle: core matrices of 8 rows x 16 bytes, element (m, k) at byte
+//     (m / 8) SBO + (k / 4) * 128 + (m % 8) * 16 + (k % 4) * 4,
+// SBO = 128 K/4 + 16 (the extra 16 bytes put the 8-row groups on different banks so that the
+// transposing gather writes without conflicts).  PASSES = 1: TF32 operands (truncated by the
+// tensor core); PASSES = 3: each operand split as hi + lo with hi = its TF32 part, and
+// D = Ahi Bhi + Ahi Blo + Alo Bhi (about 2^-21 relative per product, FP32 level).
+// One elected thread issues the MMAs; completion is signalled on an mbarrier whose wait has an
+// iteration cap: on timeout the kernel sets *err and stops (after freeing its tensor memory).
+struct TcGeo {
+    int n, rshift, P;            // cubes per side, log2 R, lattice points per batch (P R = 128)
+    int nbatch;                  // ceil(n^3 / P)
+    int Kp, Nc, Ma;              // padded K, padded N, curl-carrying 1-form classes
+    int sboA, sboB;              // 8-row group strides (bytes)
+    int offAlo, offBhi, offBlo, offIdx, offBar;   // shared-memory layout (bytes from the 1024-aligned base)
+    int tmem_cols;
+};
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long umma_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+    return (unsigned long long)((addr >> 4) & 0x3FFFu) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);   // version 1, no swizzle
+}
+__device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
+template <int PASSES>
+__global__ void __launch_bounds__(256, 1) k_curlT_e_tc(TcGeo G, const int4* __restrict__ uterm, const DCls* __restrict__ c1,
+                                                       const DCls* __restrict__ c2, const int* __restrict__ acls,
+                                                       const float* __restrict__ Wt, const float* __restrict__ b,
+                                                       float* __restrict__ e, float* __restrict__ ep, PadGeo pg,
+                                                       Tau<float> ctau, int* __restrict__ err) {
+    extern __shared__ unsigned char tc_raw[];
+    unsigned char* sm = (unsigned char*)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* sAhi = sm;
+    unsigned char* sAlo = sm + G.offAlo;
+    unsigned char* sBhi = sm + G.offBhi;
+    unsigned char* sBlo = sm + G.offBlo;
+    int* gidx = (int*)(sm + G.offIdx);                      // [P][Kp] compact 2-form index or -1
+    unsigned long long* bar = (unsigned long long*)(sm + G.offBar);
+    unsigned* tslot = (unsigned*)(sm + G.offBar + 8);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int R = 1 << G.rshift, KC = G.Kp >> 2;
+    // B = W^T (N x K, K-major), hi (and lo) parts, once per CTA
+    for (int i = tid; i < G.Nc * G.Kp; i += blockDim.x) {
+        const int nrow = i / G.Kp, k = i - nrow * G.Kp;
+        const float w = Wt[i];
+        const int off = (nrow >> 3) * G.sboB + (k >> 2) * 128 + (nrow & 7) * 16 + (k & 3) * 4;
+        const float hi = PASSES == 3 ? tf32_hi(w) : w;
+        *(float*)(sBhi + off) = hi;
+        if (PASSES == 3) *(float*)(sBlo + off) = w - hi;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"((unsigned)G.tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const unsigned tmem = *tslot;
+    // instruction descriptor: D f32, A/B tf32, K-major both, N >> 3, M = 128 >> 4
+    const unsigned idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(G.Nc >> 3) << 17) | ((128u >> 4) << 24);
+    const int n = G.n, n3 = n * n * n;
+    unsigned phase = 0;
+    bool failed = false;
+    for (int bt = blockIdx.x; bt < G.nbatch && !failed; bt += gridDim.x) {
+        // 2-form indices of the union terms at the batch's points
+        for (int i = tid; i < G.P * G.Kp; i += blockDim.x) {
+            const int p = i / G.Kp, k = i - p * G.Kp;
+            const int pt = bt * G.P + p;
+            int gi = -1;
+            const int4 U = uterm[k];
+            if (pt < n3 && U.x >= 0) {
+                const int vx = pt % n, vy = (pt / n) % n, vz = pt / (n * n);
+                const DCls D = c2[U.x];
+                const int ux = vx + U.y - D.lo[0], uy = vy + U.z - D.lo[1], uz = vz + U.w - D.lo[2];
+                if (in_box(D, ux, uy, uz)) gi = (int)(D.off + ((long long)uz * D.num[1] + uy) * D.num[0] + ux);
+            }
+            gidx[i] = gi;
+        }
+        __syncthreads();
+        // A = gathered b, K-major: one warp instruction fills an (8 rows x 4 k) tile, conflict-free
+        for (int tile = warp; tile < 16 * KC; tile += blockDim.x >> 5) {
+            const int grp = tile / KC, kc = tile - grp * KC;
+            const int m = grp * 8 + (lane & 7), k = kc * 4 + (lane >> 3);
+            const int p = m >> G.rshift, r = m & (R - 1);
+            const int gi = p < G.P ? gidx[p * G.Kp + k] : -1;
+            const float v = gi >= 0 ? __ldg(b + ((long long)gi << G.rshift) + r) : 0.f;
+            const int off = grp * G.sboA + kc * 128 + (lane & 7) * 16 + (lane >> 3) * 4;
+            const float hi = PASSES == 3 ? tf32_hi(v) : v;
+            *(float*)(sAhi + off) = hi;
+            if (PASSES == 3) *(float*)(sAlo + off) = v - hi;
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            for (int ks = 0; ks < (G.Kp >> 3); ++ks) {
+                const unsigned long long ahi = umma_desc(smem_u32(sAhi) + ks * 256, 128, G.sboA);
+                const unsigned long long bhi = umma_desc(smem_u32(sBhi) + ks * 256, 128, G.sboB);
+                const unsigned acc = ks > 0 ? 1u : 0u;
+                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                             "l"(ahi), "l"(bhi), "r"(idesc), "r"(acc));
+                if (PASSES == 3) {
+                    const unsigned long long alo = umma_desc(smem_u32(sAlo) + ks * 256, 128, G.sboA);
+                    const unsigned long long blo = umma_desc(smem_u32(sBlo) + ks * 256, 128, G.sboB);
+                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                                 "l"(ahi), "l"(blo), "r"(idesc), "r"(1u));
+                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                                 "l"(alo), "l"(bhi), "r"(idesc), "r"(1u));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar)));
+        }
+        // wait for the MMAs (bounded)
+        {
+            unsigned done = 0;
+            for (long long it = 0; it < (1LL << 26) && !done; ++it)
+                asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}"
+                             : "=r"(done)
+                             : "r"(smem_u32(bar)), "r"(phase));
+            failed = __syncthreads_or(!done) != 0;     // the same decision in every thread
+            if (failed && tid == 0) atomicExch(err, 1);
+        }
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (!failed) {
+            // epilogue: warp w reads lanes 32 (w % 4) .. +31 (rows m) and half of the columns
+            const int m = (warp & 3) * 32 + lane;
+            const int p = m >> G.rshift, r = m & (R - 1);
+            const int pt = bt * G.P + p;
+            const bool okp = p < G.P && pt < n3;
+            const int vx = pt % n, vy = (pt / n) % n, vz = pt / (n * n);
+            const int half = G.Nc >> 1, j0 = (warp >> 2) * half;
+            for (int jc = j0; jc < j0 + half; jc += 8) {
+                unsigned v[8];
+                const unsigned taddr = tmem + ((unsigned)((warp & 3) * 32) << 16) + (unsigned)jc;
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                             : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+                if (!okp) continue;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int j = jc + u;
+                    if (j >= G.Ma) break;
+                    const DCls C = c1[acls[j]];
+                    const int rx = vx - C.lo[0], ry = vy - C.lo[1], rz = vz - C.lo[2];
+                    if (!in_box(C, rx, ry, rz)) continue;
+                    const long long gi = (C.off + ((long long)rz * C.num[1] + ry) * C.num[0] + rx) << G.rshift;
+                    const float d = __uint_as_float(v[u]);
+                    const float nv = fmaf(ctau.lo, d, fmaf(ctau.hi, d, e[gi + r]));
+                    e[gi + r] = nv;
+                    ep[((long long)pad_index(C, pg, vx, vy, vz) << G.rshift) + r] = nv;
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((unsigned)G.tmem_cols));
+}
+
+// ------------------------------------------------------------------ uneven batch: many cavities, one launch
+// Independent cavities of any size and order, each with its own tables, Q1 and state, step
+// together in one persistent launch.  A step is three phases over work items (cavity, block):
+//   A  x = Q1 e (curl-carrying rows)     B  b_{n+1/2} = b_{n-1/2} - dt C x     C  e += dt C^T M2 b - j
+// with a grid-wide barrier after each.  The item bodies are the ones of the one-column lattice
+// kernels; a cavity's blocks only touch that cavity's buffers.  The barrier spins with an
+// iteration cap: when it is reached the kernel sets *err and every CTA leaves at the next
+// barrier, so a missing CTA can stall the launch for a bounded time only.
+template <typename real>
+struct BCav {
+    const DCls *c1, *c2;
+    const int2* soff2;
+    SymGeo sg;
+    PadGeo pg;
+    const real* qs;
+    real *ep, *x, *xp, *bp, *b0, *b1, *e;
+    const CTermL* cterms;
+    const int* pbeg;
+    const WTermL<real>* wterms;
+    const SBlk *blkA, *blkB, *blkC;
+    const int* sbeg;                 // source entries of blkC (NULL: no source)
+    const SrcE<real>* sent;
+    Tau<real> tau;
+    int cur0;                        // b ping-pong index at the first step of the launch
+};
+template <typename real>
+__device__ __forceinline__ void qapply_rows(const SBlk& B, const DCls& C, const int2* s_o2, SymGeo g, const real* __restrict__ qs,
+                                            const real* __restrict__ ep, real* __restrict__ x, real* __restrict__ xp) {
+    if ((int)threadIdx.x >= B.cnt) return;
+    const int t = B.t0 + (int)threadIdx.x;
+    const int vy = t / g.NX, vx = t - vy * g.NX;
+    const int rx = vx - C.lo[0], ry = vy - C.lo[1];
+    if ((unsigned)rx >= (unsigned)C.num[0] || (unsigned)ry >= (unsigned)C.num[1]) return;
+    unsigned long long keep, drop;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(drop));
+    const real* __restrict__ q = qs + (B.q0 + t);
+    const int pe = C.pbase + ((B.vz + g.H) * g.NP + (vy + g.H)) * g.NP + vx + g.H;
+    const real* __restrict__ e0 = ep + pe;
+    KSum<real> a;
+    qs_run(a, s_o2, 0, C.nup, q, e0, keep);
+    qs_run(a, s_o2, C.nup, C.st_end - C.st_begin, q, e0, drop);
+    x[C.off + ((long long)(B.vz - C.lo[2]) * C.num[1] + ry) * C.num[0] + rx] = a.s;
+    xp[pe] = a.s;
+}
+// grid-wide barrier over a co-resident grid (bar[0] arrivals, bar[1] generation); returns false
+// in every thread of every CTA once any CTA gave up waiting
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& gen, int* err, int* s_flag, long long cap) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned g = gen;
+        if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
+            atomicExch(&bar[0], 0u);
+            __threadfence();
+            atomicExch(&bar[1], g + 1u);
+        } else {
+            long long it = 0;
+            unsigned cur;
+            do {
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&bar[1]));
+                if (cur != g) break;
+                __nanosleep(128);
+            } while (++it < cap);
+            if (cur == g) atomicExch(err, 1);
+        }
+        __threadfence();
+        *s_flag = *(volatile int*)err;
+    }
+    __syncthreads();
+    ++gen;
+    return *s_flag == 0;
+}
+template <typename real>
+__global__ void __launch_bounds__(SBLOCK) k_batch(const BCav<real>* __restrict__ cavs, const int2* __restrict__ items, int nA,
+                                                  int nB, int nC, int nsteps, int ncav, const double* __restrict__ amp,
+                                                  unsigned* bar, int* err, long long cap) {
+    extern __shared__ __align__(16) unsigned char braw[];
+    int2* s_o2 = reinterpret_cast<int2*>(braw);
+    WTermL<real>* s_t = reinterpret_cast<WTermL<real>*>(braw);
+    __shared__ int s_flag;
+    __shared__ unsigned s_gen;
+    if (threadIdx.x == 0) asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(s_gen) : "l"(&bar[1]));
+    __syncthreads();
+    unsigned gen = s_gen;
+    const int2* iA = items;
+    const int2* iB = items + nA;
+    const int2* iC = items + nA + nB;
+    for (int st = 0; st < nsteps; ++st) {
+        for (int i = blockIdx.x; i < nA; i += gridDim.x) {
+            const int2 it = iA[i];
+            const BCav<real>& cv = cavs[it.x];
+            const SBlk B = cv.blkA[it.y];
+            const DCls C = cv.c1[B.cls];
+            __syncthreads();
+            for (int s = threadIdx.x; s < C.st_end - C.st_begin; s += blockDim.x) s_o2[s] = cv.soff2[C.st_begin + s];
+            __syncthreads();
+            qapply_rows(B, C, s_o2, cv.sg, cv.qs, cv.ep, cv.x, cv.xp);
+        }
+        if (!grid_barrier(bar, gen, err, &s_flag, cap)) return;
+        for (int i = blockIdx.x; i < nB; i += gridDim.x) {
+            const int2 it = iB[i];
+            const BCav<real>& cv = cavs[it.x];
+            const bool odd = ((cv.cur0 + st) & 1) != 0;
+            curl_b_rows(cv.blkB[it.y], cv.c2, cv.cterms, cv.pg, cv.sg.NX, cv.xp, odd ? cv.b1 : cv.b0, odd ? cv.b0 : cv.b1,
+                        cv.bp, cv.tau);
+        }
+        if (!grid_barrier(bar, gen, err, &s_flag, cap)) return;
+        for (int i = blockIdx.x; i < nC; i += gridDim.x) {
+            const int2 it = iC[i];
+            const BCav<real>& cv = cavs[it.x];
+            const SBlk B = cv.blkC[it.y];
+            const int tb = cv.pbeg[B.cls], nt = cv.pbeg[B.cls + 1] - tb;
+            __syncthreads();
+            for (int s = threadIdx.x; s < nt; s += blockDim.x) s_t[s] = cv.wterms[tb + s];
+            __syncthreads();
+            const double* a = cv.sbeg ? amp + (long long)st * ncav + it.x : nullptr;
+            curlT_e_rows(B, cv.c1, s_t, nt, cv.pg, cv.sg.NX, cv.bp, cv.e, cv.tau, cv.ep, cv.sbeg, cv.sent, a, it.y);
+        }
+        if (!grid_barrier(bar, gen, err, &s_flag, cap)) return;
+    }
+}
+
+// ------------------------------------------------------------------ adjoint of the leapfrog (one column)
+// The reverse sweep of the probe-region energy
+//     L = tau sum_n [1/2 x_n^T M1^R x_n + 1/2 b_{n+1/2}^T M2^R b_{n+1/2}],  x_n = Q1 e_n,
+// runs the transposed shear maps newest step first.  With cb = C^T bbar (bbar itself is never
+// needed) one reverse step is
+//     cb   += tau C^T M2 (C ebar) + tau C^T M2^R b_{n+1/2}
+//     xbar  = -tau cb + tau M1^R x_n
+//     ebar += Q1 xbar,      Q1bar += xbar e_n^T
+// C ebar and C^T M2 u reuse k_curl_b_s / k_curlT_e_s, Q1 xbar reuses k_qapply_s.  The kernels below
+// are the rest: the region operators (CSR over the DoFs of the region's tets), the Q1bar
+// accumulation on the upper-triangle lattice of Q1, and the per-tet loss / M1^R gradient terms.
+
+// y[rows[i]] += alpha sum_k val[k] x[col[k]] (one thread per listed row)
+template <typename real>
+__global__ void k_csr_add(int nrows, const int* __restrict__ rows, const int* __restrict__ ptr, const int* __restrict__ col,
+                          const double* __restrict__ val, const real* __restrict__ x, real* __restrict__ y, double alpha) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrows) return;
+    double a = 0.0;
+    for (int k = ptr[i]; k < ptr[i + 1]; ++k) a += val[k] * (double)x[col[k]];
+    y[rows[i]] = (real)((double)y[rows[i]] + alpha * a);
+}
+// xbar (padded) = -tau cb + tau (M1^R x); M1^R as a CSR over every 1-form row (most rows empty)
+template <typename real>
+__global__ void k_xbar(long long N1, const int* __restrict__ pidx, const int* __restrict__ ptr, const int* __restrict__ col,
+                       const double* __restrict__ val, const real* __restrict__ cb, const real* __restrict__ x, double tau,
+                       real* __restrict__ xbar_pad) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N1; i += (long long)gridDim.x * blockDim.x) {
+        double m = 0.0;
+        for (int k = ptr[i]; k < ptr[i + 1]; ++k) m += val[k] * (double)x[col[k]];
+        xbar_pad[pidx[i]] = (real)(tau * (m - (double)cb[i]));
+    }
+}
+// a += b over a padded vector (halo entries are zero in both)
+template <typename real>
+__global__ void k_pad_add(long long n, real* __restrict__ a, const real* __restrict__ b) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        a[i] += b[i];
+}
+// Q1bar on the stored (upper) pairs: S[i, s] += xbar_i e_j + xbar_j e_i, j = the slot's neighbour.
+// Same blocks, slot tables and padded geometry as k_qapply_s; the upper slots are the first C.nup
+// of the class's slot list.  One thread owns each stored value: no atomics.
+template <typename real>
+__global__ void __launch_bounds__(SBLOCK) k_q1bar(const SBlk* __restrict__ blks, const DCls* __restrict__ c1,
+                                                  const int2* __restrict__ soff2, SymGeo g, const real* __restrict__ xb,
+                                                  const real* __restrict__ ep, real* __restrict__ S) {
+    extern __shared__ __align__(16) int2 s_o2[];
+    const SBlk B = blks[blockIdx.x];
+    const DCls C = c1[B.cls];
+    for (int s = threadIdx.x; s < C.nup; s += blockDim.x) s_o2[s] = soff2[C.st_begin + s];
+    __syncthreads();
+    if ((int)threadIdx.x >= B.cnt) return;
+    const int t = B.t0 + (int)threadIdx.x;
+    const int vy = t / g.NX, vx = t - vy * g.NX;
+    const int rx = vx - C.lo[0], ry = vy - C.lo[1];
+    if ((unsigned)rx >= (unsigned)C.num[0] || (unsigned)ry >= (unsigned)C.num[1]) return;
+    const int pe = C.pbase + ((B.vz + g.H) * g.NP + (vy + g.H)) * g.NP + vx + g.H;
+    const real xi = xb[pe], ei = ep[pe];
+    real* __restrict__ q = S + (B.q0 + t);
+    for (int s = 0; s < C.nup; ++s) {
+        const int2 o = s_o2[s];
+        q[o.x] += xi * ep[pe + o.y] + xb[pe + o.y] * ei;
+    }
+}
+// Region tets (one thread each): loss[t] += tau (eps_t/2 x_T^T M1 x_T + 1/(2 mu_t) b_T^T M2a b_T) and
+// grad[t] += tau/2 x_T^T M1 x_T, in FP64, from the unweighted local blocks.
+template <typename real>
+__global__ void k_region(int nt, int n1, int n2a, const int* __restrict__ d1, const int* __restrict__ d2,
+                         const double* __restrict__ M1l, const double* __restrict__ M2l, const double* __restrict__ epsr,
+                         const double* __restrict__ imur, const real* __restrict__ x, const real* __restrict__ b,
+                         double tau, double* __restrict__ loss, double* __restrict__ grad) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    double xv[45], bv[36];
+    for (int a = 0; a < n1; ++a) {
+        const int i = d1[(long long)t * n1 + a];
+        xv[a] = i >= 0 ? (double)x[i] : 0.0;
+    }
+    for (int a = 0; a < n2a; ++a) {
+        const int i = d2[(long long)t * n2a + a];
+        bv[a] = i >= 0 ? (double)b[i] : 0.0;
+    }
+    double qx = 0.0, qb = 0.0;
+    for (int a = 0; a < n1; ++a) {
+        double u = 0.0;
+        for (int c = 0; c < n1; ++c) u += M1l[a * n1 + c] * xv[c];
+        qx += xv[a] * u;
+    }
+    for (int a = 0; a < n2a; ++a) {
+        double u = 0.0;
+        for (int c = 0; c < n2a; ++c) u += M2l[a * n2a + c] * bv[c];
+        qb += bv[a] * u;
+    }
+    loss[t] += tau * (0.5 * epsr[t] * qx + 0.5 * imur[t] * qb);
+    grad[t] += 0.5 * tau * qx;
+}
+
 }  // namespace
 
 // ====================================================================== context
@@ -1119,6 +1534,14 @@ struct ygm_ctx {
     SBlk *lblks_b = nullptr, *lblks_e = nullptr;
     int nlb = 0, nle = 0;
     int64_t qc_rows[2] = {0, 0}, qc_unique[2] = {0, 0}, qc_stored[2] = {0, 0};   // [active only, all rows]
+    int tc_passes = 0;                       // > 0: C^T M2 on tensor cores (YGM_FP32_TC_*), 1 or 3 TF32 passes
+    TcGeo tcg{};
+    int4* uterm = nullptr;                   // union of the merged C^T M2 terms (class, dx, dy, dz)
+    int* acls = nullptr;                     // curl-carrying 1-form class of each GEMM column
+    float* wt = nullptr;                     // merged weights, [column][K]
+    int* tc_err = nullptr;                   // set by k_curlT_e_tc when an MMA wait times out
+    size_t tc_smem = 0;
+    int tc_grid = 0;
     double2* qpart = nullptr;                // per-block e_i x_i partials of an all-rows k_qapply_s
     unsigned* ticket = nullptr;              // last-block counter of k_tet_energy (kept at 0 between launches)
     void* M2af = nullptr;                    // M2a in the context precision (k_tet_energy)
@@ -1292,6 +1715,68 @@ static int setup_sym(ygm_ctx* ctx, const std::vector<int>& eoff) {
         return rc;
     ctx->sg = SymGeo{NX, ctx->pg.H, ctx->pg.NP};
     ctx->use_sym = true;
+    return 0;
+}
+
+// Tables of k_curlT_e_tc: the union U of the merged C^T M2 terms, the dense weights W (curl-carrying
+// classes x |U|), the shared-memory layout and the grid.  Requires R in {32, 64, 128}.
+static int setup_tc(ygm_ctx* ctx, const std::vector<std::pair<ygm::Nbr, double>>& all, const std::vector<int>& pbeg) {
+    const ygm::Lattice& L = ctx->S.L;
+    const int R = ctx->n_rhs;
+    if (R != 32 && R != 64 && R != 128)
+        return fail(ctx, YGM_EINVAL, "tensor-core precisions need n_rhs = 32, 64 or 128 (128 rows = points x columns)");
+    std::map<ygm::Nbr, int> kidx;
+    for (const auto& t : all) kidx.emplace(t.first, 0);
+    int K = 0;
+    std::vector<int4> ut;
+    for (auto& kv : kidx) {
+        kv.second = K++;
+        ut.push_back(make_int4(kv.first.cls, kv.first.d[0], kv.first.d[1], kv.first.d[2]));
+    }
+    std::vector<int> ac;
+    for (size_t c = 0; c < L.c1.size(); ++c)
+        if (L.c1[c].active) ac.push_back((int)c);
+    const int Ma = (int)ac.size(), Kp = (K + 7) / 8 * 8, Nc = std::max(16, (Ma + 15) / 16 * 16);
+    if (Nc > 256) return fail(ctx, YGM_EINVAL, "tensor-core C^T M2: more than 256 curl-carrying classes");
+    while ((int)ut.size() < Kp) ut.push_back(make_int4(-1, 0, 0, 0));
+    std::vector<float> w((size_t)Nc * Kp, 0.f);
+    for (int j = 0; j < Ma; ++j)
+        for (int t = pbeg[ac[j]]; t < pbeg[ac[j] + 1]; ++t) w[(size_t)j * Kp + kidx[all[t].first]] = (float)all[t].second;
+    TcGeo& G = ctx->tcg;
+    G.n = L.n;
+    G.rshift = ctx->rshift;
+    G.P = 128 / R;
+    G.nbatch = (int)(((long long)L.n * L.n * L.n + G.P - 1) / G.P);
+    G.Kp = Kp;
+    G.Nc = Nc;
+    G.Ma = Ma;
+    G.sboA = Kp / 4 * 128 + 16;
+    G.sboB = Kp / 4 * 128 + 16;
+    auto al = [](size_t v) { return (int)((v + 1023) / 1024 * 1024); };
+    const int aBytes = al((size_t)16 * G.sboA), bBytes = al((size_t)(Nc / 8) * G.sboB);
+    const bool three = ctx->tc_passes == 3;
+    G.offAlo = aBytes;
+    G.offBhi = G.offAlo + (three ? aBytes : 0);
+    G.offBlo = G.offBhi + bBytes;
+    G.offIdx = G.offBlo + (three ? bBytes : 0);
+    G.offBar = G.offIdx + (int)((size_t)G.P * Kp * 4 + 15) / 16 * 16;
+    G.tmem_cols = 32;
+    while (G.tmem_cols < Nc) G.tmem_cols *= 2;
+    ctx->tc_smem = (size_t)G.offBar + 16 + 1024;   // + slack to align the base to 1024 bytes
+    if (ctx->tc_smem > 227 * 1024)
+        return fail(ctx, YGM_EINVAL, "tensor-core C^T M2 tables exceed shared memory (order 3 is not supported)");
+    int rc;
+    if ((rc = upload(ctx, &ctx->uterm, ut)) || (rc = upload(ctx, &ctx->acls, ac)) || (rc = upload(ctx, &ctx->wt, w))) return rc;
+    CK(cudaMalloc((void**)&ctx->tc_err, sizeof(int)));
+    CK(cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), ctx->stream));
+    if (three)
+        CK(cudaFuncSetAttribute(k_curlT_e_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->tc_smem));
+    else
+        CK(cudaFuncSetAttribute(k_curlT_e_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->tc_smem));
+    int nsm = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+    const int per_sm = std::max(1, (int)((227 * 1024) / ctx->tc_smem));
+    ctx->tc_grid = std::min(G.nbatch, nsm * std::min(per_sm, 2));
     return 0;
 }
 
@@ -1484,11 +1969,12 @@ static int setup_device(ygm_ctx* ctx) {
         }
         ctx->npblks = (int)pb.size();
         ctx->nplanes = (int)planes.size();
-        if ((rc = upload(ctx, &ctx->soff, so)) || (rc = upload(ctx, &ctx->pblks, pb)) ||
-            (rc = upload(ctx, &ctx->planes, planes)) || (rc = upload_real(ctx, &ctx->qf, S.qfull)))
+        if ((rc = upload(ctx, &ctx->soff, so)) || (rc = upload(ctx, &ctx->pblks, pb)) || (rc = upload(ctx, &ctx->planes, planes)))
             return rc;
         for (size_t c = 0; c < L.c1.size(); ++c) ctx->max_ns = std::max(ctx->max_ns, S.st_begin[c + 1] - S.st_begin[c]);
         if ((rc = setup_sym(ctx, so))) return rc;
+        // full-row Q1 only where k_qapply_p reads it (R > 1, or offsets beyond 32 bits)
+        if (!ctx->use_sym && (rc = upload_real(ctx, &ctx->qf, S.qfull))) return rc;
         // roofline counts of the two launch kinds
         std::vector<char> act(L.N1, 0);
         for (size_t c = 0; c < L.c1.size(); ++c) {
@@ -1581,6 +2067,7 @@ static int setup_device(ygm_ctx* ctx) {
         }
         if ((rc = upload(ctx, &ctx->pbeg, pbeg))) return rc;
         for (size_t c = 0; c < L.c1.size(); ++c) ctx->max_terms = std::max(ctx->max_terms, pbeg[c + 1] - pbeg[c]);
+        if (ctx->tc_passes && (rc = setup_tc(ctx, all, pbeg))) return rc;
         if (ctx->n_rhs == 1) {
             // the same weights as offsets into the padded b (k_curlT_e_s)
             auto wfill = [&](auto* dummy) {
@@ -1600,6 +2087,8 @@ static int setup_device(ygm_ctx* ctx) {
             if ((rc = ctx->precision == YGM_FP64 ? wfill((double*)nullptr) : wfill((float*)nullptr))) return rc;
         }
     }
+    if (ctx->tc_passes && !ctx->wt)
+        return fail(ctx, YGM_EINVAL, "tensor-core precisions need a uniform permeability (the merged C^T M2 stencil)");
     // lattice block lists of the padded curl kernels (one column, with k_qapply_s)
     if (ctx->use_sym) {
         const int NX = ctx->sg.NX;
@@ -1772,6 +2261,11 @@ static int launch_curlT_e(ygm_ctx* ctx, const void* b, void* e, double ctau, con
         return 0;
     } else if (ctx->rshift) {
         if (!ctx->neblocks) {
+        } else if (ctx->tc_passes && ctx->wt) {
+            auto k = ctx->tc_passes == 3 ? k_curlT_e_tc<3> : k_curlT_e_tc<1>;
+            k<<<ctx->tc_grid, 256, ctx->tc_smem, ctx->stream>>>(ctx->tcg, ctx->uterm, ctx->c1, ctx->c2, ctx->acls, ctx->wt,
+                                                               (const float*)b, (float*)e, (float*)ctx->ep, ctx->pg,
+                                                               split_tau<float>(ctau), ctx->tc_err);
         } else if (ctx->pterms) {
             const size_t smem = (size_t)ctx->max_terms * (ctx->precision == YGM_FP64 ? sizeof(PTerm<double>) : sizeof(PTerm<float>));
             if (ctx->precision == YGM_FP64)
@@ -1897,6 +2391,17 @@ static int launch_energy(ygm_ctx* ctx, const void* e, const void* x, const void*
     return 0;
 }
 
+// Device-side failures reported through flags (a tensor-core MMA wait that gave up): checked by
+// the calls that synchronise the stream anyway.
+static int check_device_flags(ygm_ctx* ctx) {
+    if (!ctx->tc_err) return 0;
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, ctx->tc_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (h) return fail(ctx, YGM_ETIMEOUT, "a tensor-core MMA completion wait gave up (k_curlT_e_tc); results are invalid");
+    return 0;
+}
+
 // ====================================================================== no-allocation step
 // Callers that must not allocate device memory (a process whose device memory is reserved up
 // front by another allocator, or code under a real-time budget that rules out cudaMalloc and its
@@ -1936,7 +2441,8 @@ int ygm_create(const ygm_mesh* mesh, int order, const double* eps, const double*
     o.precision = YGM_FP64;
     o.n_rhs = 1;
     if (opts) o = *opts;
-    if (o.precision != YGM_FP64 && o.precision != YGM_FP32) return cerr(YGM_EINVAL, "precision must be YGM_FP64 or YGM_FP32");
+    if (o.precision < YGM_FP64 || o.precision > YGM_FP32_TC_3XTF32)
+        return cerr(YGM_EINVAL, "precision must be YGM_FP64, YGM_FP32, YGM_FP32_TC_TF32 or YGM_FP32_TC_3XTF32");
     if (o.n_rhs < 1 || o.n_rhs > 256 || (o.n_rhs & (o.n_rhs - 1)))
         return cerr(YGM_EINVAL, "n_rhs must be a power of two in [1, 256]");
     if (o.energy_every < 0) return cerr(YGM_EINVAL, "energy_every must be >= 0");
@@ -1961,7 +2467,9 @@ int ygm_create(const ygm_mesh* mesh, int order, const double* eps, const double*
 // Second half of context creation: the options, the stream and the device copies of an
 // already built host set-up (ctx->S).  Takes ownership of ctx.
 static int finish_create(ygm_ctx* ctx, const ygm_opts& o, ygm_ctx** out) {
-    ctx->precision = o.precision;
+    // tensor-core precisions keep FP32 state and FP32 SIMT kernels except the C^T M2 contraction
+    ctx->tc_passes = o.precision == YGM_FP32_TC_TF32 ? 1 : o.precision == YGM_FP32_TC_3XTF32 ? 3 : 0;
+    ctx->precision = o.precision == YGM_FP64 ? YGM_FP64 : YGM_FP32;
     ctx->rs = o.precision == YGM_FP64 ? 8 : 4;
     ctx->n_rhs = o.n_rhs;
     ctx->rshift = 0;
@@ -2014,7 +2522,8 @@ int ygm_create_like(const ygm_ctx* src, const ygm_opts* opts, ygm_ctx** out) {
     o.precision = YGM_FP64;
     o.n_rhs = 1;
     if (opts) o = *opts;
-    if (o.precision != YGM_FP64 && o.precision != YGM_FP32) return cerr(YGM_EINVAL, "precision must be YGM_FP64 or YGM_FP32");
+    if (o.precision < YGM_FP64 || o.precision > YGM_FP32_TC_3XTF32)
+        return cerr(YGM_EINVAL, "precision must be YGM_FP64, YGM_FP32, YGM_FP32_TC_TF32 or YGM_FP32_TC_3XTF32");
     if (o.n_rhs < 1 || o.n_rhs > 256 || (o.n_rhs & (o.n_rhs - 1)))
         return cerr(YGM_EINVAL, "n_rhs must be a power of two in [1, 256]");
     if (o.energy_every < 0) return cerr(YGM_EINVAL, "energy_every must be >= 0");
@@ -2080,7 +2589,7 @@ int ygm_get_state(ygm_ctx* ctx, void* e, void* b, int on_device, int synced) {
     }
     CK(cudaGetLastError());
     if (!on_device) CK(cudaStreamSynchronize(ctx->stream));
-    return YGM_OK;
+    return check_device_flags(ctx);
 }
 
 int ygm_project_E(ygm_ctx* ctx, void (*E0)(const double x[3], double out[3], void* user), void* user, int32_t rhs) {
@@ -2333,7 +2842,7 @@ int ygm_energy(ygm_ctx* ctx, double* W, double* Htilde) {
     CK(cudaStreamSynchronize(ctx->stream));
     std::copy(h.begin(), h.begin() + R, W);
     if (Htilde) std::copy(h.begin() + R, h.end(), Htilde);
-    return YGM_OK;
+    return check_device_flags(ctx);
 }
 
 int ygm_energy_history(ygm_ctx* ctx, double* out, int64_t max_count, int64_t* count) {
@@ -2363,10 +2872,35 @@ int ygm_export_q1(const ygm_ctx* ctx, int64_t* rowptr, int64_t* colind, double* 
     return YGM_OK;
 }
 
+// Device copies of a new Q1 (box-indexed, and the full-row or upper-triangle lattice copy the
+// step reads): uploaded into fresh buffers first; the old ones are freed and replaced only once
+// every upload succeeded, so a failed refresh leaves the context stepping the previous Q1.
+static int refresh_q1_device(ygm_ctx* ctx) {
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    void *q = nullptr, *qf = nullptr, *qsd = nullptr;
+    int rc = upload_real(ctx, &q, ctx->S.qvals);
+    if (!rc && !ctx->use_sym) rc = upload_real(ctx, &qf, ctx->S.qfull);
+    if (!rc && ctx->use_sym) rc = upload_real(ctx, &qsd, ctx->S.qsym);
+    if (rc) {
+        cudaFree(q);
+        cudaFree(qf);
+        cudaFree(qsd);
+        return rc;
+    }
+    cudaFree(ctx->q);
+    cudaFree(ctx->qf);
+    cudaFree(ctx->qsd);
+    ctx->q = q;
+    ctx->qf = qf;
+    ctx->qsd = qsd;
+    return 0;
+}
+
 // A Q1 update that failed its SPD check: put the previous Q1 back into the host set-up (the
 // device copies were not touched) and keep the error message.
 static int restore_q1(ygm_ctx* ctx, ygm::Csr&& old, int code) {
-    const std::string msg = ctx->S.err;
+    const std::string msg = code == YGM_ENOTSPD ? ctx->S.err : ctx->err;   // set-up check, or a failed upload
     ctx->S.Q1 = std::move(old);
     ygm::repack_q1(ctx->S, 0);
     return fail(ctx, code, msg);
@@ -2378,15 +2912,7 @@ int ygm_set_q1(ygm_ctx* ctx, const int64_t* rowptr, const int64_t* colind, const
     int rc = ygm::install_q1(ctx->S, rowptr, colind, val, 0);
     if (rc == -1) return fail(ctx, YGM_EINVAL, ctx->S.err);
     if (rc) return restore_q1(ctx, std::move(old), YGM_ENOTSPD);
-    if (!ctx->host_only) {
-        CK(cudaStreamSynchronize(ctx->stream));
-        cudaFree(ctx->q);
-        cudaFree(ctx->qf);
-        cudaFree(ctx->qsd);
-        ctx->q = ctx->qf = ctx->qsd = nullptr;
-        if ((rc = upload_real(ctx, &ctx->q, ctx->S.qvals)) || (rc = upload_real(ctx, &ctx->qf, ctx->S.qfull))) return rc;
-        if (ctx->use_sym && (rc = upload_real(ctx, &ctx->qsd, ctx->S.qsym))) return rc;
-    }
+    if (!ctx->host_only && (rc = refresh_q1_device(ctx))) return restore_q1(ctx, std::move(old), rc);
     return YGM_OK;
 }
 
@@ -2401,16 +2927,7 @@ int ygm_spai_op(ygm_ctx* ctx, const double* V, int32_t n_probe, double lambda, i
     if (rel_residual) *rel_residual = rr;
     if (rc == -1 || rc == -2) return fail(ctx, rc == -1 ? YGM_EINVAL : YGM_ETIMEOUT, ctx->S.err);
     if (rc) return restore_q1(ctx, std::move(old), YGM_ENOTSPD);
-    if (!ctx->host_only) {
-        CK(cudaSetDevice(ctx->device));
-        CK(cudaStreamSynchronize(ctx->stream));
-        cudaFree(ctx->q);
-        cudaFree(ctx->qf);
-        cudaFree(ctx->qsd);
-        ctx->q = ctx->qf = ctx->qsd = nullptr;
-        if ((rc = upload_real(ctx, &ctx->q, ctx->S.qvals)) || (rc = upload_real(ctx, &ctx->qf, ctx->S.qfull))) return rc;
-        if (ctx->use_sym && (rc = upload_real(ctx, &ctx->qsd, ctx->S.qsym))) return rc;
-    }
+    if (!ctx->host_only && (rc = refresh_q1_device(ctx))) return restore_q1(ctx, std::move(old), rc);
     return YGM_OK;
 }
 
@@ -2506,6 +3023,765 @@ int ygm_step_noalloc(ygm_ctx* ctx, void* e, const void* b_in, void* b_out, doubl
     return YGM_OK;
 }
 
+// ---------------------------------------------------------------------- uneven batch
+}  // extern "C"
+
+struct ygm_batch {
+    std::vector<ygm_ctx*> cav;
+    int device = 0, precision = YGM_FP32;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    void* dcavs = nullptr;               // BCav<real>[count]
+    int2* items = nullptr;
+    size_t items_cap = 0;
+    int nA = 0, nB = 0, nC = 0;
+    size_t smem = 0;
+    int max_per_sm = 1, nsm = 0;
+    double* amp = nullptr;
+    size_t amp_cap = 0;
+    unsigned* bar = nullptr;
+    int* err = nullptr;
+    int ctas_per_sm = 1, order = 1;      // launch shape and work order (ygm_batch_tune)
+    long long wait_cap = 1LL << 24;      // polls of a grid-barrier wait before it gives up
+    cudaGraphExec_t gexec = nullptr;
+    int64_t g_steps = -1;
+    int g_grid = -1, g_order = -1;
+    std::string errmsg;
+};
+
+static int bfail(ygm_batch* B, int code, const std::string& m) {
+    B->errmsg = m;
+    return code;
+}
+#define BCK(call)                                                                                  \
+    do {                                                                                           \
+        cudaError_t _e = (call);                                                                   \
+        if (_e != cudaSuccess) return bfail(B, YGM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+
+// Work items of the three phases.  order 0: cavity by cavity; order 1: Q1-apply items sorted by
+// their stencil length (longest first) and every phase interleaved across cavities, so that the
+// static round-robin over CTAs spreads the heavy (order 3) cavities.
+static int batch_items(ygm_batch* B) {
+    std::vector<int2> A, Bb, Cc;
+    const int nc = (int)B->cav.size();
+    std::vector<std::pair<int, int2>> a;
+    for (int c = 0; c < nc; ++c) {
+        ygm_ctx* x = B->cav[c];
+        std::vector<SBlk> sb(x->nsblks_act);
+        if (x->nsblks_act) BCK(cudaMemcpy(sb.data(), x->sblks, sb.size() * sizeof(SBlk), cudaMemcpyDeviceToHost));
+        for (int i = 0; i < x->nsblks_act; ++i) {
+            const auto& st = x->S.st_begin;
+            a.push_back({st[sb[i].cls + 1] - st[sb[i].cls], make_int2(c, i)});
+        }
+    }
+    auto inter = [&](auto count) {
+        std::vector<int2> out;
+        int mx = 0;
+        for (int c = 0; c < nc; ++c) mx = std::max(mx, count(c));
+        if (B->order == 0) {
+            for (int c = 0; c < nc; ++c)
+                for (int i = 0; i < count(c); ++i) out.push_back(make_int2(c, i));
+        } else {
+            for (int i = 0; i < mx; ++i)
+                for (int c = 0; c < nc; ++c)
+                    if (i < count(c)) out.push_back(make_int2(c, i));
+        }
+        return out;
+    };
+    if (B->order == 0) {
+        for (auto& v : a) A.push_back(v.second);
+    } else {
+        std::stable_sort(a.begin(), a.end(), [](const auto& u, const auto& v) { return u.first > v.first; });
+        for (auto& v : a) A.push_back(v.second);
+    }
+    Bb = inter([&](int c) { return B->cav[c]->nlb; });
+    Cc = inter([&](int c) { return B->cav[c]->lblks_es ? B->cav[c]->nle_src : B->cav[c]->nle; });
+    std::vector<int2> all(A);
+    all.insert(all.end(), Bb.begin(), Bb.end());
+    all.insert(all.end(), Cc.begin(), Cc.end());
+    if (all.size() > B->items_cap) {
+        cudaFree(B->items);
+        B->items = nullptr;
+        BCK(cudaMalloc((void**)&B->items, all.size() * sizeof(int2)));
+        B->items_cap = all.size();
+    }
+    if (!all.empty()) BCK(cudaMemcpy(B->items, all.data(), all.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    B->nA = (int)A.size();
+    B->nB = (int)Bb.size();
+    B->nC = (int)Cc.size();
+    return 0;
+}
+
+template <typename real>
+static BCav<real> bcav_of(ygm_ctx* x, double dt) {
+    BCav<real> c{};
+    c.c1 = x->c1;
+    c.c2 = x->c2;
+    c.soff2 = x->soff2;
+    c.sg = x->sg;
+    c.pg = x->pg;
+    c.qs = (const real*)x->qsd;
+    c.ep = (real*)x->ep;
+    c.x = (real*)x->x;
+    c.xp = (real*)x->xp;
+    c.bp = (real*)x->bp;
+    c.b0 = (real*)x->b[0];
+    c.b1 = (real*)x->b[1];
+    c.e = (real*)x->e;
+    c.cterms = x->cterms;
+    c.pbeg = x->pbeg;
+    c.wterms = (const WTermL<real>*)x->wterms;
+    c.blkA = x->sblks;
+    c.blkB = x->lblks_b;
+    c.blkC = x->lblks_es ? x->lblks_es : x->lblks_e;
+    c.sbeg = x->lblks_es ? x->sbeg : nullptr;
+    c.sent = (const SrcE<real>*)x->sent;
+    c.tau = split_tau<real>(dt);
+    c.cur0 = x->cur;
+    return c;
+}
+
+template <typename real>
+static int batch_launch(ygm_batch* B, int64_t nsteps, bool graph) {
+    const int ncav = (int)B->cav.size();
+    const int grid = B->nsm * B->ctas_per_sm;
+    int ns = (int)nsteps;
+    void* args[] = {&B->dcavs, &B->items, &B->nA, &B->nB, &B->nC, &ns, (void*)&ncav, &B->amp, &B->bar, &B->err, &B->wait_cap};
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(SBLOCK);
+    cfg.dynamicSmemBytes = B->smem;
+    cfg.stream = B->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    auto issue = [&]() -> cudaError_t {
+        cudaError_t e = cudaMemsetAsync(B->bar, 0, 2 * sizeof(unsigned), B->stream);
+        if (e != cudaSuccess) return e;
+        return cudaLaunchKernelExC(&cfg, (const void*)k_batch<real>, args);
+    };
+    if (!graph) {
+        BCK(issue());
+        return 0;
+    }
+    if (!B->gexec || B->g_steps != nsteps || B->g_grid != grid || B->g_order != B->order) {
+        if (B->gexec) cudaGraphExecDestroy(B->gexec);
+        B->gexec = nullptr;
+        cudaGraph_t g = nullptr;
+        BCK(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
+        const cudaError_t le = issue();
+        const cudaError_t ce = cudaStreamEndCapture(B->stream, &g);
+        if (le != cudaSuccess || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return bfail(B, YGM_ECUDA, std::string("capturing the batch launch: ") + cudaGetErrorString(le != cudaSuccess ? le : ce));
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&B->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) return bfail(B, YGM_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+        B->g_steps = nsteps;
+        B->g_grid = grid;
+        B->g_order = B->order;
+    }
+    BCK(cudaGraphLaunch(B->gexec, B->stream));
+    return 0;
+}
+
+extern "C" {
+
+int ygm_batch_create(ygm_ctx* const* cavities, int32_t count, ygm_batch** out) {
+    if (!out) return YGM_EINVAL;
+    *out = nullptr;
+    if (!cavities || count < 1) return YGM_EINVAL;
+    ygm_batch* B = new (std::nothrow) ygm_batch();
+    if (!B) return YGM_ENOMEM;
+    auto bad = [&](int code, const std::string& m) {
+        std::lock_guard<std::mutex> lk(g_err_mutex);
+        g_create_err = m;
+        delete B;
+        return code;
+    };
+    for (int i = 0; i < count; ++i) {
+        ygm_ctx* x = cavities[i];
+        if (!x) return bad(YGM_EINVAL, "NULL context");
+        if (x->host_only) return bad(YGM_ENODEV, "host-only context in the batch");
+        if (!x->use_sym || x->n_rhs != 1 || !x->wterms || !x->nle || x->tc_passes)
+            return bad(YGM_EINVAL, "batch members must be one-column FP32/FP64 contexts with uniform mu on the lattice path");
+        if (x->device != cavities[0]->device || x->precision != cavities[0]->precision)
+            return bad(YGM_EINVAL, "batch members must share the device and the precision");
+        B->cav.push_back(x);
+    }
+    B->device = cavities[0]->device;
+    B->precision = cavities[0]->precision;
+    B->stream = cavities[0]->stream;
+    if (cudaSetDevice(B->device) != cudaSuccess) return bad(YGM_ECUDA, "cudaSetDevice failed");
+    for (ygm_ctx* x : B->cav) {
+        const size_t rsz = B->precision == YGM_FP64 ? sizeof(WTermL<double>) : sizeof(WTermL<float>);
+        B->smem = std::max(B->smem, std::max((size_t)(x->max_ns + 8) * sizeof(int2), (size_t)x->max_terms * rsz));
+    }
+    if (B->smem > 48 * 1024) return bad(YGM_EINVAL, "batch: stencil tables exceed 48 KB of shared memory");
+    int nb = 0;
+    const cudaError_t oe = B->precision == YGM_FP64
+                               ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<double>, SBLOCK, B->smem)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<float>, SBLOCK, B->smem);
+    if (oe != cudaSuccess || nb < 1) return bad(YGM_ECUDA, "batch: occupancy query failed");
+    B->max_per_sm = nb;
+    B->ctas_per_sm = std::min(nb, 4);
+    if (cudaDeviceGetAttribute(&B->nsm, cudaDevAttrMultiProcessorCount, B->device) != cudaSuccess)
+        return bad(YGM_ECUDA, "batch: SM count query failed");
+    const size_t cbytes = (B->precision == YGM_FP64 ? sizeof(BCav<double>) : sizeof(BCav<float>)) * count;
+    if (cudaMalloc(&B->dcavs, cbytes) != cudaSuccess || cudaMalloc((void**)&B->bar, 2 * sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc((void**)&B->err, sizeof(int)) != cudaSuccess || cudaMemset(B->err, 0, sizeof(int)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming) != cudaSuccess) {
+        ygm_batch_destroy(B);
+        std::lock_guard<std::mutex> lk(g_err_mutex);
+        g_create_err = "batch: device allocation failed";
+        return YGM_ENOMEM;
+    }
+    if (int rc = batch_items(B)) {
+        std::string m = B->errmsg;
+        ygm_batch_destroy(B);
+        std::lock_guard<std::mutex> lk(g_err_mutex);
+        g_create_err = m;
+        return rc;
+    }
+    *out = B;
+    return YGM_OK;
+}
+
+int ygm_batch_step(ygm_batch* B, int64_t nsteps, const double* dt, const ygm_source* src, int32_t use_graph) {
+    if (!B || !dt || nsteps < 0) return B ? bfail(B, YGM_EINVAL, "need dt[] and nsteps >= 0") : YGM_EINVAL;
+    const int nc = (int)B->cav.size();
+    for (int i = 0; i < nc; ++i) {
+        ygm_ctx* x = B->cav[i];
+        if (!(dt[i] > 0) || !std::isfinite(dt[i])) return bfail(B, YGM_EINVAL, "dt must be finite and > 0");
+        if (dt[i] > x->S.tau_cfl * (1.0 + 1e-12))
+            return bfail(B, YGM_ECFL, "cavity " + std::to_string(i) + ": dt exceeds its CFL bound (Prop. stability)");
+    }
+    BCK(cudaSetDevice(B->device));
+    bool relist = false;
+    for (int i = 0; i < nc; ++i) {
+        ygm_ctx* x = B->cav[i];
+        ygm_source s1{};
+        if (src) {
+            s1 = src[i];
+            s1.rhs = 0;
+        }
+        const bool had = x->lblks_es != nullptr;
+        const int nsb = x->nle_src;
+        if (int rc = set_sources(x, src ? &s1 : nullptr, src ? 1 : 0))
+            return bfail(B, rc, "cavity " + std::to_string(i) + ": " + x->err);
+        relist |= had != (x->lblks_es != nullptr) || nsb != x->nle_src;
+        // staggering of each cavity on its own stream (as ygm_step), then ordered before the batch
+        void* b0 = x->b[x->cur];
+        if (!x->staggered) {
+            launch_qapply(x, x->x, false);
+            launch_curl_b(x, x->x, b0, b0, -0.5 * dt[i]);
+            x->staggered = true;
+            x->step_base = x->step;
+            x->t_base = 0.0;
+        } else if (dt[i] != x->dt_prev) {
+            launch_qapply(x, x->x, false);
+            launch_curl_b(x, x->x, b0, b0, 0.5 * x->dt_prev - 0.5 * dt[i]);
+            x->t_base += (double)(x->step - x->step_base) * x->dt_prev;
+            x->step_base = x->step;
+        }
+        x->dt_prev = dt[i];
+        if (x->stream != B->stream) {
+            BCK(cudaEventRecord(B->ev, x->stream));
+            BCK(cudaStreamWaitEvent(B->stream, B->ev, 0));
+        }
+    }
+    if (relist)
+        if (int rc = batch_items(B)) return rc;
+    if (nsteps == 0) return YGM_OK;
+    // per-step, per-cavity source amplitudes dt s(t_{n+1/2}) (host FP64)
+    const size_t namp = (size_t)nsteps * nc;
+    std::vector<double> amp(namp, 0.0);
+    for (int i = 0; i < nc; ++i) {
+        ygm_ctx* x = B->cav[i];
+        if (!x->nsrc) continue;
+        const ygm_source& s0 = x->src_cache[0];
+        for (int64_t st = 0; st < nsteps; ++st) {
+            const double t = x->t_base + ((double)(x->step + st - x->step_base) + 0.5) * dt[i];
+            const double u = (t - s0.t0) / s0.sigma;
+            amp[(size_t)st * nc + i] = dt[i] * s0.amp * std::exp(-u * u) * std::sin(s0.omega * (t - s0.t0));
+        }
+    }
+    BCK(cudaStreamSynchronize(B->stream));   // the previous launch no longer reads amp / dcavs
+    if (namp > B->amp_cap) {
+        cudaFree(B->amp);
+        B->amp = nullptr;
+        BCK(cudaMalloc((void**)&B->amp, namp * sizeof(double)));
+        B->amp_cap = namp;
+        if (B->gexec) cudaGraphExecDestroy(B->gexec);
+        B->gexec = nullptr;
+    }
+    BCK(cudaMemcpy(B->amp, amp.data(), namp * sizeof(double), cudaMemcpyHostToDevice));
+    int rc;
+    if (B->precision == YGM_FP64) {
+        std::vector<BCav<double>> cv(nc);
+        for (int i = 0; i < nc; ++i) cv[i] = bcav_of<double>(B->cav[i], dt[i]);
+        BCK(cudaMemcpy(B->dcavs, cv.data(), cv.size() * sizeof(cv[0]), cudaMemcpyHostToDevice));
+        rc = batch_launch<double>(B, nsteps, use_graph != 0);
+    } else {
+        std::vector<BCav<float>> cv(nc);
+        for (int i = 0; i < nc; ++i) cv[i] = bcav_of<float>(B->cav[i], dt[i]);
+        BCK(cudaMemcpy(B->dcavs, cv.data(), cv.size() * sizeof(cv[0]), cudaMemcpyHostToDevice));
+        rc = batch_launch<float>(B, nsteps, use_graph != 0);
+    }
+    if (rc) return rc;
+    for (ygm_ctx* x : B->cav) {
+        x->cur ^= (int)(nsteps & 1);
+        x->step += nsteps;
+        x->launches += 1;
+        if (x->stream != B->stream) {
+            BCK(cudaEventRecord(B->ev, B->stream));
+            BCK(cudaStreamWaitEvent(x->stream, B->ev, 0));
+        }
+    }
+    return YGM_OK;
+}
+
+int ygm_batch_status(ygm_batch* B) {
+    if (!B) return YGM_EINVAL;
+    int h = 0;
+    BCK(cudaStreamSynchronize(B->stream));
+    BCK(cudaMemcpy(&h, B->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) return bfail(B, YGM_ETIMEOUT, "batch: a grid barrier gave up waiting (not every CTA was resident)");
+    return YGM_OK;
+}
+
+int ygm_batch_tune(ygm_batch* B, int32_t trial_steps, const double* dt, const ygm_source* src, int32_t* ctas_per_sm,
+                   int32_t* order, double* ms_per_step) {
+    if (!B || !dt || trial_steps < 1) return B ? bfail(B, YGM_EINVAL, "need dt[] and trial_steps >= 1") : YGM_EINVAL;
+    BCK(cudaSetDevice(B->device));
+    // save every cavity's state (the trials advance it), restore it after each trial
+    struct Saved {
+        std::vector<void*> buf;
+        int cur;
+        bool stag;
+        int64_t step, step_base;
+        double t_base, dt_prev;
+    };
+    std::vector<Saved> sv(B->cav.size());
+    auto cleanup = [&]() {
+        for (auto& s0 : sv)
+            for (void* p : s0.buf) cudaFree(p);
+    };
+    for (size_t i = 0; i < B->cav.size(); ++i) {
+        ygm_ctx* x = B->cav[i];
+        BCK(cudaStreamSynchronize(x->stream));
+        const size_t sz[4] = {x->S.L.N1 * x->rs, x->S.L.N2 * x->rs, x->S.L.N2 * x->rs, (size_t)x->n1pad * x->rs};
+        void* src4[4] = {x->e, x->b[0], x->b[1], x->ep};
+        for (int j = 0; j < 4; ++j) {
+            void* p = nullptr;
+            if (cudaMalloc(&p, sz[j]) != cudaSuccess) {
+                cleanup();
+                return bfail(B, YGM_ENOMEM, "batch tune: saving a state failed");
+            }
+            sv[i].buf.push_back(p);
+            BCK(cudaMemcpy(p, src4[j], sz[j], cudaMemcpyDeviceToDevice));
+        }
+        sv[i].cur = x->cur;
+        sv[i].stag = x->staggered;
+        sv[i].step = x->step;
+        sv[i].step_base = x->step_base;
+        sv[i].t_base = x->t_base;
+        sv[i].dt_prev = x->dt_prev;
+    }
+    auto restore = [&]() -> int {
+        for (size_t i = 0; i < B->cav.size(); ++i) {
+            ygm_ctx* x = B->cav[i];
+            BCK(cudaStreamSynchronize(B->stream));
+            const size_t sz[4] = {x->S.L.N1 * x->rs, x->S.L.N2 * x->rs, x->S.L.N2 * x->rs, (size_t)x->n1pad * x->rs};
+            void* dst4[4] = {x->e, x->b[0], x->b[1], x->ep};
+            for (int j = 0; j < 4; ++j) BCK(cudaMemcpy(dst4[j], sv[i].buf[j], sz[j], cudaMemcpyDeviceToDevice));
+            x->cur = sv[i].cur;
+            x->staggered = sv[i].stag;
+            x->step = sv[i].step;
+            x->step_base = sv[i].step_base;
+            x->t_base = sv[i].t_base;
+            x->dt_prev = sv[i].dt_prev;
+        }
+        return 0;
+    };
+    double best = 1e300;
+    int bc = B->ctas_per_sm, bo = B->order;
+    cudaEvent_t a, z;
+    BCK(cudaEventCreate(&a));
+    BCK(cudaEventCreate(&z));
+    for (int o = 0; o < 2; ++o)
+        for (int c = 1; c <= std::min(B->max_per_sm, 4); ++c) {
+            B->order = o;
+            B->ctas_per_sm = c;
+            int rc = batch_items(B);
+            if (!rc) rc = ygm_batch_step(B, 1, dt, src, 0);   // staggering and sources outside the timed launch
+            if (!rc) rc = cudaEventRecord(a, B->stream) == cudaSuccess ? 0 : YGM_ECUDA;
+            if (!rc) rc = ygm_batch_step(B, trial_steps, dt, src, 0);
+            if (!rc) rc = cudaEventRecord(z, B->stream) == cudaSuccess ? 0 : YGM_ECUDA;
+            if (!rc) rc = ygm_batch_status(B);
+            float ms = 0.f;
+            if (!rc) rc = cudaEventElapsedTime(&ms, a, z) == cudaSuccess ? 0 : YGM_ECUDA;
+            const int rr = restore();
+            if (rc || rr) {
+                cudaEventDestroy(a);
+                cudaEventDestroy(z);
+                cleanup();
+                return rc ? rc : rr;
+            }
+            if (ms < best) {
+                best = ms;
+                bc = c;
+                bo = o;
+            }
+        }
+    cudaEventDestroy(a);
+    cudaEventDestroy(z);
+    cleanup();
+    B->ctas_per_sm = bc;
+    B->order = bo;
+    if (int rc = batch_items(B)) return rc;
+    if (ctas_per_sm) *ctas_per_sm = bc;
+    if (order) *order = bo;
+    if (ms_per_step) *ms_per_step = best / trial_steps;
+    return YGM_OK;
+}
+
+int ygm_batch_wait_limit(ygm_batch* B, int64_t polls) {
+    if (!B || polls < 0) return YGM_EINVAL;
+    B->wait_cap = polls;
+    if (B->gexec) cudaGraphExecDestroy(B->gexec);   // the cap is a kernel argument of the captured launch
+    B->gexec = nullptr;
+    return YGM_OK;
+}
+
+int ygm_batch_status_clear(ygm_batch* B) {
+    if (!B) return YGM_EINVAL;
+    BCK(cudaStreamSynchronize(B->stream));
+    BCK(cudaMemset(B->err, 0, sizeof(int)));
+    return YGM_OK;
+}
+
+const char* ygm_batch_last_error(const ygm_batch* B) { return B ? B->errmsg.c_str() : ""; }
+
+void ygm_batch_destroy(ygm_batch* B) {
+    if (!B) return;
+    if (B->stream) cudaStreamSynchronize(B->stream);
+    if (B->gexec) cudaGraphExecDestroy(B->gexec);
+    cudaFree(B->dcavs);
+    cudaFree(B->items);
+    cudaFree(B->amp);
+    cudaFree(B->bar);
+    cudaFree(B->err);
+    if (B->ev) cudaEventDestroy(B->ev);
+    delete B;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------- adjoint (one column)
+// Host tables of the probe region: its tets' DoFs, the region mass operators as CSR, the padded
+// index of every 1-form DoF.  Sums over tets run in tet order (deterministic).
+struct RegionOps {
+    std::vector<int> tets, d1, d2;            // region tets; their n1 / n2a global DoFs (-1: none)
+    std::vector<double> epsr, imur;
+    std::vector<int> g_rows, g_ptr, g_col;    // C^T M2^R on the rows it touches
+    std::vector<double> g_val;
+    std::vector<int> m_ptr, m_col;            // M1^R over all N1 rows
+    std::vector<double> m_val;
+};
+static void build_region(const ygm_ctx* ctx, const uint8_t* region, RegionOps& R) {
+    const ygm::Setup& S = ctx->S;
+    const ygm::Lattice& L = S.L;
+    const int64_t T = 6LL * L.n * L.n * L.n;
+    const int n1 = L.n1, n2a = L.n2a;
+    std::vector<int64_t> g1(n1), g2(L.n2);
+    std::map<std::pair<int, int>, double> G, M;
+    for (int64_t t = 0; t < T; ++t) {
+        if (!region[t]) continue;
+        L.tet_dofs1(t, g1.data());
+        L.tet_dofs2(t, g2.data());
+        R.tets.push_back((int)t);
+        const double eps = S.eps.empty() ? 1.0 : S.eps[t], imu = S.mu.empty() ? 1.0 : 1.0 / S.mu[t];
+        R.epsr.push_back(eps);
+        R.imur.push_back(imu);
+        for (int a = 0; a < n1; ++a) R.d1.push_back((int)g1[a]);
+        for (int r = 0; r < n2a; ++r) R.d2.push_back((int)g2[L.act2[r]]);
+        for (int a = 0; a < n1; ++a) {
+            if (g1[a] < 0) continue;
+            for (int r = 0; r < n2a; ++r) {
+                const int64_t j = g2[L.act2[r]];
+                if (j >= 0) G[{(int)g1[a], (int)j}] += S.Wloc[(size_t)a * n2a + r] * imu;
+            }
+            for (int c = 0; c < n1; ++c)
+                if (g1[c] >= 0) M[{(int)g1[a], (int)g1[c]}] += S.M1loc[(size_t)a * n1 + c] * eps;
+        }
+    }
+    R.g_ptr.push_back(0);
+    int last = -1;
+    for (const auto& kv : G) {
+        if (kv.first.first != last) {
+            if (last >= 0) R.g_ptr.push_back((int)R.g_col.size());
+            R.g_rows.push_back(kv.first.first);
+            last = kv.first.first;
+        }
+        R.g_col.push_back(kv.first.second);
+        R.g_val.push_back(kv.second);
+    }
+    if (last >= 0) R.g_ptr.push_back((int)R.g_col.size());
+    R.m_ptr.assign(L.N1 + 1, 0);
+    for (const auto& kv : M) R.m_ptr[kv.first.first + 1]++;
+    for (int64_t i = 0; i < L.N1; ++i) R.m_ptr[i + 1] += R.m_ptr[i];
+    for (const auto& kv : M) {
+        R.m_col.push_back(kv.first.second);
+        R.m_val.push_back(kv.second);
+    }
+}
+
+// dL/dQ1 on the CSR pattern of Q1 from the pair sums S[i, s] of the upper-triangle lattice:
+// qbar_ij = qbar_ji = S / 2 (the symmetric part is what the SPAI derivative uses).
+template <typename real>
+static void pairs_to_csr(const ygm::Setup& S, const std::vector<real>& Sv, std::vector<double>& qbar) {
+    const ygm::Lattice& L = S.L;
+    const size_t nc = L.c1.size();
+    std::vector<std::map<std::array<int, 4>, int>> up(nc);   // (nbr class, d) -> upper slot
+    for (size_t c = 0; c < nc; ++c)
+        for (int k = S.st_begin[c]; k < S.st_begin[c + 1]; ++k) {
+            const auto& st = S.st_slots[k];
+            if (st.upper) up[c][{st.cls, st.d[0], st.d[1], st.d[2]}] = st.slot;
+        }
+    qbar.assign(S.Q1.col.size(), 0.0);
+    const int NX = S.qs_nx, NY = S.qs_ny;
+    auto at = [&](int c, int slot, const int v[3]) {
+        return S.qs_base[c] + (int64_t)slot * S.qs_vol + ((int64_t)v[2] * NY + v[1]) * NX + v[0];
+    };
+    for (int64_t i = 0; i < L.N1; ++i) {
+        int ci, vi[3];
+        L.decode1(i, &ci, vi);
+        for (int64_t k = S.Q1.ptr[i]; k < S.Q1.ptr[i + 1]; ++k) {
+            int cj, vj[3];
+            L.decode1(S.Q1.col[k], &cj, vj);
+            auto it = up[ci].find({cj, vj[0] - vi[0], vj[1] - vi[1], vj[2] - vi[2]});
+            double v;
+            if (it != up[ci].end()) {
+                v = (double)Sv[at(ci, it->second, vi)];
+            } else {
+                auto jt = up[cj].find({ci, vi[0] - vj[0], vi[1] - vj[1], vi[2] - vj[2]});
+                v = jt != up[cj].end() ? (double)Sv[at(cj, jt->second, vj)] : 0.0;
+            }
+            qbar[k] = 0.5 * v;
+        }
+    }
+}
+
+template <typename real>
+static int adjoint_run(ygm_ctx* ctx, int64_t nsteps, double dt, int32_t K, const uint8_t* region, double* loss,
+                       double* grad) {
+    const ygm::Setup& S = ctx->S;
+    const ygm::Lattice& L = S.L;
+    const int64_t N1 = L.N1, N2 = L.N2, T = 6LL * L.n * L.n * L.n;
+    const size_t rs = sizeof(real), n1pad = (size_t)ctx->n1pad, n2pad = (size_t)ctx->pg.NP * ctx->pg.NP * ctx->pg.NP * L.c2.size();
+    RegionOps R;
+    build_region(ctx, region, R);
+    const int nt = (int)R.tets.size();
+    const int nseg = (int)((nsteps + K - 1) / K);
+    // device memory of this call (freed on every exit path)
+    std::vector<void*> owned;
+    auto dalloc = [&](void** p, size_t bytes) -> int {
+        *p = nullptr;
+        if (!bytes) return 0;
+        CK(cudaMalloc(p, bytes));
+        owned.push_back(*p);
+        CK(cudaMemsetAsync(*p, 0, bytes, ctx->stream));
+        return 0;
+    };
+    struct Guard {
+        std::vector<void*>& v;
+        ~Guard() {
+            for (void* p : v) cudaFree(p);
+        }
+    } guard{owned};
+    void *ck, *seg, *ebar, *cb, *tx, *tpad, *xbp, *u, *upad, *zero2, *dump, *epad, *Sd, *lossd, *gradd;
+    void *rd1, *rd2, *rep, *rim, *rgr, *rgp, *rgc, *rgv, *rmp, *rmc, *rmv, *pidx, *m1l, *m2l;
+    int rc;
+    const size_t q_n = S.qsym.size();
+    if ((rc = dalloc(&ck, (size_t)nseg * (N1 + N2) * rs)) || (rc = dalloc(&seg, (size_t)K * (2 * N1 + N2) * rs)) ||
+        (rc = dalloc(&ebar, n1pad * rs)) || (rc = dalloc(&cb, N1 * rs)) || (rc = dalloc(&tx, N1 * rs)) ||
+        (rc = dalloc(&tpad, n1pad * rs)) || (rc = dalloc(&xbp, n1pad * rs)) || (rc = dalloc(&u, N2 * rs)) ||
+        (rc = dalloc(&upad, n2pad * rs)) || (rc = dalloc(&zero2, N2 * rs)) || (rc = dalloc(&dump, n1pad * rs)) ||
+        (rc = dalloc(&epad, n1pad * rs)) || (rc = dalloc(&Sd, q_n * rs)) || (rc = dalloc(&lossd, (size_t)nt * 8)) ||
+        (rc = dalloc(&gradd, (size_t)nt * 8)))
+        return rc;
+    auto up = [&](void** p, const void* h, size_t bytes) -> int {
+        if ((rc = dalloc(p, bytes))) return rc;
+        if (bytes) CK(cudaMemcpyAsync(*p, h, bytes, cudaMemcpyHostToDevice, ctx->stream));
+        return 0;
+    };
+    std::vector<int> pid(N1);
+    for (int64_t i = 0; i < N1; ++i) {
+        int c, v[3];
+        L.decode1(i, &c, v);
+        pid[i] = (int)(c * (long long)ctx->pg.NP * ctx->pg.NP * ctx->pg.NP +
+                       ((long long)(v[2] + ctx->pg.H) * ctx->pg.NP + v[1] + ctx->pg.H) * ctx->pg.NP + v[0] + ctx->pg.H);
+    }
+    if ((rc = up(&rd1, R.d1.data(), R.d1.size() * 4)) || (rc = up(&rd2, R.d2.data(), R.d2.size() * 4)) ||
+        (rc = up(&rep, R.epsr.data(), R.epsr.size() * 8)) || (rc = up(&rim, R.imur.data(), R.imur.size() * 8)) ||
+        (rc = up(&rgr, R.g_rows.data(), R.g_rows.size() * 4)) || (rc = up(&rgp, R.g_ptr.data(), R.g_ptr.size() * 4)) ||
+        (rc = up(&rgc, R.g_col.data(), R.g_col.size() * 4)) || (rc = up(&rgv, R.g_val.data(), R.g_val.size() * 8)) ||
+        (rc = up(&rmp, R.m_ptr.data(), R.m_ptr.size() * 4)) || (rc = up(&rmc, R.m_col.data(), R.m_col.size() * 4)) ||
+        (rc = up(&rmv, R.m_val.data(), R.m_val.size() * 8)) || (rc = up(&pidx, pid.data(), pid.size() * 4)) ||
+        (rc = up(&m1l, S.M1loc.data(), S.M1loc.size() * 8)) || (rc = up(&m2l, S.M2aloc.data(), S.M2aloc.size() * 8)))
+        return rc;
+    // source amplitudes dt s(t_{n+1/2}) of every step (host FP64), as ygm_step computes them
+    const int nsrc = ctx->nsrc;
+    std::vector<double> amp((size_t)nsteps * std::max(nsrc, 1), 0.0);
+    std::vector<char> on(nsteps, 0);
+    for (int64_t i = 0; i < nsteps && nsrc; ++i)
+        for (int q = 0; q < nsrc; ++q) {
+            const ygm_source& s0 = ctx->src_cache[q];
+            const double t = (i + 0.5) * dt, v = (t - s0.t0) / s0.sigma;
+            const double a = dt * s0.amp * std::exp(-v * v) * std::sin(s0.omega * (t - s0.t0));
+            amp[(size_t)i * nsrc + q] = a;
+            if (a != 0.0) on[i] = 1;
+        }
+    void* ampd = nullptr;
+    if (nsrc && (rc = up(&ampd, amp.data(), amp.size() * 8))) return rc;
+    real* ckp = (real*)ck;
+    real* sg_e = (real*)seg;
+    real* sg_x = sg_e + (size_t)K * N1;
+    real* sg_b = sg_x + (size_t)K * N1;
+    // forward from rest (b_{-1/2} = 0: the initial half step of a zero state is zero)
+    CK(cudaMemsetAsync(ctx->e, 0, N1 * rs, ctx->stream));
+    CK(cudaMemsetAsync(ctx->ep, 0, n1pad * rs, ctx->stream));
+    CK(cudaMemsetAsync(ctx->b[0], 0, N2 * rs, ctx->stream));
+    CK(cudaMemsetAsync(ctx->b[1], 0, N2 * rs, ctx->stream));
+    ctx->cur = 0;
+    auto fwd = [&](int64_t n, bool all, int64_t slot) {
+        void* bo = ctx->b[ctx->cur];
+        void* bn = ctx->b[ctx->cur ^ 1];
+        if (slot >= 0) cudaMemcpyAsync(sg_e + slot * N1, ctx->e, N1 * rs, cudaMemcpyDeviceToDevice, ctx->stream);
+        launch_qapply(ctx, ctx->x, all);
+        launch_curl_b(ctx, ctx->x, bo, bn, dt);
+        if (slot >= 0) {
+            cudaMemcpyAsync(sg_x + slot * N1, ctx->x, N1 * rs, cudaMemcpyDeviceToDevice, ctx->stream);
+            cudaMemcpyAsync(sg_b + slot * N2, bn, N2 * rs, cudaMemcpyDeviceToDevice, ctx->stream);
+        }
+        launch_curlT_e(ctx, bn, ctx->e, dt, on[n] ? (const double*)ampd + (size_t)n * nsrc : nullptr);
+        ctx->cur ^= 1;
+    };
+    for (int64_t n = 0; n < nsteps; ++n) {
+        if (n % K == 0) {
+            const int64_t c = n / K;
+            CK(cudaMemcpyAsync(ckp + c * (N1 + N2), ctx->e, N1 * rs, cudaMemcpyDeviceToDevice, ctx->stream));
+            CK(cudaMemcpyAsync(ckp + c * (N1 + N2) + N1, ctx->b[ctx->cur], N2 * rs, cudaMemcpyDeviceToDevice, ctx->stream));
+        }
+        fwd(n, false, -1);
+    }
+    // reverse, one checkpoint segment at a time
+    const SBlk* ball = ctx->sblks + ctx->nsblks_act;
+    const size_t smem_q = (size_t)(ctx->max_ns + 8) * sizeof(int2);
+    const size_t smem_e = (size_t)ctx->max_terms * sizeof(WTermL<real>);
+    const int nb_all = ctx->nsblks_all;
+    const dim3 gl((unsigned)std::min<int64_t>(4 * 152, (N1 + BLOCK - 1) / BLOCK)), gp((unsigned)std::min<size_t>(4 * 152, (n1pad + BLOCK - 1) / BLOCK));
+    for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+        const int64_t n0 = (int64_t)sgi * K, n1 = std::min<int64_t>(n0 + K, nsteps);
+        CK(cudaMemcpyAsync(ctx->e, ckp + sgi * (N1 + N2), N1 * rs, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->b[ctx->cur], ckp + sgi * (N1 + N2) + N1, N2 * rs, cudaMemcpyDeviceToDevice, ctx->stream));
+        launch_pad_e(ctx);
+        for (int64_t n = n0; n < n1; ++n) fwd(n, true, n - n0);
+        for (int64_t n = n1 - 1; n >= n0; --n) {
+            const int64_t sl = n - n0;
+            // cb += tau C^T M2 (C ebar)
+            k_curl_b_s<real><<<ctx->nlb, SBLOCK, 0, ctx->stream>>>(ctx->lblks_b, ctx->c2, ctx->cterms, ctx->pg, ctx->sg.NX,
+                                                                   (const real*)ebar, (const real*)zero2, (real*)u,
+                                                                   (real*)upad, split_tau<real>(-1.0));
+            k_curlT_e_s<real><<<ctx->nle, SBLOCK, smem_e, ctx->stream>>>(ctx->lblks_e, ctx->c1, ctx->pbeg,
+                                                                        (const WTermL<real>*)ctx->wterms, ctx->pg, ctx->sg.NX,
+                                                                        (const real*)upad, (real*)cb, split_tau<real>(dt),
+                                                                        (real*)dump, nullptr, nullptr, nullptr);
+            // cb += tau C^T M2^R b_{n+1/2}
+            const int ngr = (int)R.g_rows.size();
+            if (ngr)
+                k_csr_add<real><<<(ngr + 255) / 256, 256, 0, ctx->stream>>>(ngr, (const int*)rgr, (const int*)rgp, (const int*)rgc,
+                                                                            (const double*)rgv, sg_b + sl * N2, (real*)cb, dt);
+            // xbar = -tau cb + tau M1^R x_n ; ebar += Q1 xbar
+            k_xbar<real><<<gl, BLOCK, 0, ctx->stream>>>(N1, (const int*)pidx, (const int*)rmp, (const int*)rmc, (const double*)rmv,
+                                                        (const real*)cb, sg_x + sl * N1, dt, (real*)xbp);
+            k_qapply_s<real, false><<<nb_all, SBLOCK, smem_q, ctx->stream>>>(ball, ctx->c1, ctx->soff2, ctx->sg,
+                                                                             (const real*)ctx->qsd, (const real*)xbp, (real*)tx,
+                                                                             (real*)tpad, nullptr);
+            k_pad_add<real><<<gp, BLOCK, 0, ctx->stream>>>((long long)n1pad, (real*)ebar, (const real*)tpad);
+            // Q1bar += xbar e_n^T (stored pairs), and the region terms of step n
+            k_pad_e<real><<<ctx->nplanes, BLOCK, 0, ctx->stream>>>(ctx->c1, ctx->planes, ctx->pg, 0, sg_e + sl * N1, (real*)epad);
+            k_q1bar<real><<<nb_all, SBLOCK, smem_q, ctx->stream>>>(ball, ctx->c1, ctx->soff2, ctx->sg, (const real*)xbp,
+                                                                    (const real*)epad, (real*)Sd);
+            if (nt)
+                k_region<real><<<(nt + 127) / 128, 128, 0, ctx->stream>>>(nt, L.n1, L.n2a, (const int*)rd1, (const int*)rd2,
+                                                                          (const double*)m1l, (const double*)m2l,
+                                                                          (const double*)rep, (const double*)rim,
+                                                                          sg_x + sl * N1, sg_b + sl * N2, dt,
+                                                                          (double*)lossd, (double*)gradd);
+            ctx->launches += 9;
+        }
+        CK(cudaGetLastError());
+    }
+    std::vector<real> Sh(q_n);
+    std::vector<double> lh(nt), gh(nt);
+    CK(cudaMemcpyAsync(Sh.data(), Sd, q_n * rs, cudaMemcpyDeviceToHost, ctx->stream));
+    if (nt) {
+        CK(cudaMemcpyAsync(lh.data(), lossd, (size_t)nt * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(gh.data(), gradd, (size_t)nt * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    // the context's state is left at rest
+    CK(cudaMemsetAsync(ctx->e, 0, N1 * rs, ctx->stream));
+    CK(cudaMemsetAsync(ctx->ep, 0, n1pad * rs, ctx->stream));
+    CK(cudaMemsetAsync(ctx->b[0], 0, N2 * rs, ctx->stream));
+    CK(cudaMemsetAsync(ctx->b[1], 0, N2 * rs, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->cur = 0;
+    ctx->staggered = false;
+    ctx->step = ctx->step_base = 0;
+    ctx->t_base = 0.0;
+    ctx->hist_n = 0;
+    double Ls = 0.0;
+    for (int i = 0; i < nt; ++i) Ls += lh[i];
+    *loss = Ls;
+    if (grad) {
+        std::vector<double> qbar;
+        pairs_to_csr(S, Sh, qbar);
+        if ((rc = ygm::q1_vjp(ctx->S, qbar.data(), grad, 0)))
+            return fail(ctx, rc == -1 ? YGM_EINVAL : YGM_ENOTSPD, "adjoint: the SPAI derivative failed");
+        for (int i = 0; i < nt; ++i) grad[R.tets[i]] += gh[i];
+    }
+    (void)T;
+    return YGM_OK;
+}
+
+extern "C" {
+
+int ygm_adjoint(ygm_ctx* ctx, int64_t nsteps, double dt, const ygm_source* src, int32_t n_src, const uint8_t* region,
+                int32_t checkpoint_every, double* loss, double* grad_eps) {
+    if (ctx && ctx->host_only) return fail(ctx, YGM_ENODEV, "context was created host-only (device = -1)");
+    if (!ctx || !region || !loss) return fail(ctx, YGM_EINVAL, "NULL argument");
+    if (nsteps < 1 || !(dt > 0) || !std::isfinite(dt) || checkpoint_every < 1)
+        return fail(ctx, YGM_EINVAL, "need nsteps >= 1, finite dt > 0 and checkpoint_every >= 1");
+    if (dt > ctx->S.tau_cfl * (1.0 + 1e-12))
+        return fail(ctx, YGM_ECFL, "dt exceeds the CFL bound 2/omega_max (Prop. stability)");
+    if (!ctx->use_sym || ctx->n_rhs != 1 || !ctx->wterms)
+        return fail(ctx, YGM_EINVAL, "ygm_adjoint needs a one-column context with uniform mu on the lattice path");
+    if (n_src < 0 || (n_src > 0 && !src)) return fail(ctx, YGM_EINVAL, "bad source list");
+    int rc = set_sources(ctx, src, n_src);
+    if (rc) return rc;
+    CK(cudaSetDevice(ctx->device));
+    const int32_t K = (int32_t)std::min<int64_t>(checkpoint_every, nsteps);
+    return ctx->precision == YGM_FP64 ? adjoint_run<double>(ctx, nsteps, dt, K, region, loss, grad_eps)
+                                      : adjoint_run<float>(ctx, nsteps, dt, K, region, loss, grad_eps);
+}
+
 int ygm_qapply_counts(const ygm_ctx* ctx, int all_rows, int64_t* rows, int64_t* unique_values,
                       int64_t* stored_values) {
     if (!ctx) return YGM_EINVAL;
@@ -2592,7 +3868,8 @@ void ygm_destroy(ygm_ctx* ctx) {
     void* more[] = {ctx->qslots, ctx->qblocks, ctx->eblocks, ctx->bblocks, ctx->pterms, ctx->pbeg,
                     ctx->qsd,    ctx->soff2,   ctx->sblks,   ctx->xp,      ctx->bp,     ctx->wterms,
                     ctx->cterms, ctx->lblks_b, ctx->lblks_e, ctx->qpart,  ctx->ticket, ctx->M2af,
-                    ctx->lblks_es, ctx->sbeg,    ctx->sent};
+                    ctx->lblks_es, ctx->sbeg,    ctx->sent,     ctx->uterm,  ctx->acls,  ctx->wt,
+                    ctx->tc_err};
     for (void* p : more)
         if (p) cudaFree(p);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);

@@ -151,3 +151,46 @@ def test_batched_invalid_rhs_counts():
         c.step(1, 0.5 * c.tau_cfl, [dict(x=[0.5, 0.5, 0.5], d=[0, 0, 1], omega=1.0, t0=0.0, sigma=1.0, rhs=2)])
     assert ei.value.code == Y.YGM_EINVAL
     c.close()
+
+
+# Tensor-core C^T M2 (tcgen05, kind::tf32).  3xTF32 splits each operand into its TF32 part and the
+# rest (about 2^-21 relative per product): held to the FP32 bound.  One-pass TF32 truncates both
+# operands to a 10-bit mantissa (~1e-3 per product, measured ~6e-3 relative L2 after 60 steps):
+# stated, and held to 1e-2.
+TC_TOL = {Y.YGM_FP32_TC_3XTF32: 2e-5, Y.YGM_FP32_TC_TF32: 1e-2}
+
+
+@pytest.mark.parametrize("n,k,R", [(3, 1, 32), (4, 2, 64), (3, 2, 128)])
+@pytest.mark.parametrize("precision", [Y.YGM_FP32_TC_3XTF32, Y.YGM_FP32_TC_TF32])
+def test_tensor_core_columns_follow_oracle(n, k, R, precision):
+    f, g, eps, _ = oracle_model(n, k, eps_seed=3000)
+    tau = 0.5 * g.tau_cfl()
+    srcs = _sources(R, tau, 3001)
+    steps = 60
+    c = Y.Context(n, k, eps=eps, precision=precision, n_rhs=R, energy_every=10)
+    c.set_state(np.zeros(c.N1 * R, np.float32), np.zeros(c.N2 * R, np.float32))
+    c.step(steps, tau, srcs)
+    e, b = c.get_state(synced=True)
+    W = c.energy_history().reshape(-1, R)
+    e, b = _columns(e, f.mesh.N1, R), _columns(b, f.mesh.N2, R)
+    tol = TC_TOL[precision]
+    for r in (0, R // 2, R - 1):
+        s = {kk: v for kk, v in srcs[r].items() if kk != "rhs"}
+        s["width_steps"] = 5.0
+        e_or, _, bs_or, W_or = run_oracle(f, g, np.zeros(f.mesh.N1), np.zeros(f.mesh.N2), tau, steps, sources=[s],
+                                          energy_every=10)
+        assert np.linalg.norm(e_or) > 0
+        assert rel_l2(e[:, r], e_or) < tol, r
+        assert rel_l2(b[:, r], bs_or) < tol, r
+        assert np.max(np.abs(W[:, r] - W_or)) <= tol * np.max(np.abs(W_or)), r
+    c.close()
+
+
+def test_tensor_core_precisions_reject_unsupported_contexts():
+    for kw in (dict(n_rhs=1), dict(n_rhs=16), dict(n_rhs=64, mu=synth.tet_eps(7, 2, 1.0, 2.0))):
+        with pytest.raises(Y.YgmError) as ei:
+            Y.Context(2, 1, precision=Y.YGM_FP32_TC_3XTF32, **kw)
+        assert ei.value.code == Y.YGM_EINVAL
+    with pytest.raises(Y.YgmError) as ei:
+        Y.Context(2, 3, precision=Y.YGM_FP32_TC_TF32, n_rhs=64)      # order 3 tables exceed shared memory
+    assert ei.value.code == Y.YGM_EINVAL
