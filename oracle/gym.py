@@ -6,7 +6,8 @@ Paper passages followed:
   Eq. discEOM          a' = -Q1 e,  e' = c^2 C^T M2 C a
   Eq. preYeeFEECEqns   b' = -C Q1 e, e' = c^2 C^T M2 b          (b = C a)
   Eq. shearMaps        Phi^e_tau (a, e) = (a - tau Q1 e, e);  Phi^a_tau (a, e) = (a, e + tau P2 a)
-  Eq. strangSplit      Phi_tau = Phi^e_{tau/2} o Phi^a_tau o Phi^e_{tau/2}
+  Eq. strangSplit      Phi_tau = Phi^e_{tau/2} o Phi^a_tau o Phi^e_{tau/2}; higher-order
+                       splittings as symmetric compositions of Strang maps (composed_step)
   Eq. YeeLeapfrog      initial half step of Phi^e, then alternate full steps
   Prop. stability      tau <= 2 / omega_max, omega_max^2 = lambda_max(Q1 P2)
   Eq. allEOM (3rd)     e' = -sum q xdot . Lambda1(x_s): template of the dipole current term
@@ -114,6 +115,36 @@ class GYM:
             e, b = e_new, b_new
         return e, b, W
 
+    # -------------------------------------------------------------- composed (higher-order) splittings
+    def composed_step(self, e, b_sync, tau, weights, t0=0.0, source=None):
+        """One step of a symmetric composition of Strang steps (the higher-order splittings the
+        paper mentions after Eq. strangSplit): Strang maps of sizes w_1 tau, ..., w_m tau in turn,
+        each in the (b, e) form  b -= (w tau / 2) C Q1 e;  e += w tau (C^T M2 b - j(t_mid));
+        b -= (w tau / 2) C Q1 e,  with t_mid the midpoint of the sub-step.  From and to
+        synchronised b."""
+        t = t0
+        for w in weights:
+            h = w * tau
+            b_sync = b_sync - 0.5 * h * (self.C @ (self.Q1 @ e))
+            e = e + h * (self.CT @ (self.M2 @ b_sync))
+            if source is not None:
+                e = e - h * source(t + 0.5 * h)
+            b_sync = b_sync - 0.5 * h * (self.C @ (self.Q1 @ e))
+            t = t + h
+        return e, b_sync
+
+    def run_composed(self, e, b_sync, tau, nsteps, weights, source=None):
+        for n in range(nsteps):
+            e, b_sync = self.composed_step(e, b_sync, tau, weights, t0=n * tau, source=source)
+        return e, b_sync
+
+    def composed_jacobian(self, tau, weights):
+        """Dense Jacobian of one composed step on (a, e) (products of Strang Jacobians)."""
+        J = np.eye(2 * self.Q1.shape[0])
+        for w in weights:
+            J = self.strang_jacobian(w * tau) @ J
+        return J
+
     def W(self, e, b, tau):
         """Conserved discrete energy of the state (e_n, b_{n-1/2})."""
         x = self.Q1 @ e
@@ -134,6 +165,14 @@ class GYM:
         Je = np.block([[I, -0.5 * tau * Q], [np.zeros((n, n)), I]])
         Ja = np.block([[I, np.zeros((n, n))], [tau * P, I]])
         return Je @ Ja @ Je
+
+
+def yoshida4():
+    """Weights of the fourth-order symmetric triple composition of a second-order symmetric map
+    (Yoshida 1990): w1 = 1 / (2 - 2^(1/3)), w0 = -2^(1/3) / (2 - 2^(1/3)); (w1, w0, w1), sum 1."""
+    c = 2.0 ** (1.0 / 3.0)
+    w1 = 1.0 / (2.0 - c)
+    return (w1, -c * w1, w1)
 
 
 def pulse(t, amp, omega, t0, sigma):

@@ -8,6 +8,7 @@ import scipy.sparse as sp
 import synth
 from oracle import spai as SP
 from oracle.fem import FEM
+from oracle import gym as G
 from oracle.gym import GYM, DipoleSource
 from oracle.mesh import KuhnMesh
 
@@ -195,3 +196,60 @@ def test_modified_hamiltonian_oscillation_scales_with_dt_squared():
     a2, _, _ = deviation(tau / 2)
     assert 3.4 < a1 / a2 < 4.6
     assert h2 <= 1.05 * h1
+
+
+# ---------------------------------------------------------------- composed (higher-order) splittings
+def _exact_semidiscrete(g, e0, b0, T):
+    """(e, b)(T) of the semi-discrete system b' = -C Q1 e, e' = C^T M2 b (Eq. preYeeFEECEqns),
+    exactly, by the matrix exponential (tiny meshes)."""
+    import scipy.linalg as sla
+    N1, N2 = g.Q1.shape[0], g.C.shape[0]
+    A = np.zeros((N1 + N2, N1 + N2))
+    A[N1:, :N1] = -(g.C @ g.Q1).toarray()
+    A[:N1, N1:] = (g.CT @ g.M2).toarray()
+    y = sla.expm(A * T) @ np.concatenate([e0, b0])
+    return y[:N1], y[N1:]
+
+
+def test_yoshida_weights_are_the_fourth_order_triple_jump():
+    w = G.yoshida4()
+    assert abs(sum(w) - 1) < 1e-15                      # consistency
+    assert abs(sum(x ** 3 for x in w)) < 1e-14           # the third-order condition of a symmetric composition
+    assert w[0] == w[2] and w[1] < 0
+
+
+@pytest.mark.parametrize("weights,order", [((1.0,), 2), (None, 4)])
+def test_composed_splitting_converges_at_its_order(weights, order):
+    """Against the exact semi-discrete solution: halving tau divides the error by 2^order."""
+    weights = weights or G.yoshida4()
+    f = FEM(KuhnMesh(2, 1), eps=synth.tet_eps(61, 2, 1.0, 4.0))
+    M1 = f.M1()
+    Q, _ = SP.gym_q1(f, M1)
+    g = G.GYM(f.C(), f.M2(), Q, M1)
+    rng = np.random.default_rng(5)
+    e0 = rng.standard_normal(f.mesh.N1)
+    b0 = f.C() @ rng.standard_normal(f.mesh.N1)
+    T = 0.6
+    ee, be = _exact_semidiscrete(g, e0, b0, T)
+    errs = []
+    for m in (80, 160, 320):
+        e, b = g.run_composed(e0.copy(), b0.copy(), T / m, m, weights)
+        errs.append(np.linalg.norm(np.concatenate([e - ee, b - be])) / np.linalg.norm(np.concatenate([ee, be])))
+    rates = [np.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(abs(r - order) < 0.15 for r in rates), (errs, rates)
+    if order == 4:
+        assert errs[-1] < 1e-7
+
+
+def test_composed_step_is_symplectic_and_time_symmetric():
+    f = FEM(KuhnMesh(2, 1))
+    M1 = f.M1()
+    Q, _ = SP.gym_q1(f, M1)
+    g = G.GYM(f.C(), f.M2(), Q, M1)
+    tau = 0.3 * g.tau_cfl()
+    J = g.composed_jacobian(tau, G.yoshida4())
+    n = Q.shape[0]
+    Om = np.block([[np.zeros((n, n)), np.eye(n)], [-np.eye(n), np.zeros((n, n))]])
+    assert np.abs(J.T @ Om @ J - Om).max() < 1e-10 * np.abs(J).max() ** 2
+    Jb = g.composed_jacobian(-tau, G.yoshida4())
+    assert np.abs(Jb @ J - np.eye(2 * n)).max() < 1e-10 * np.abs(J).max() ** 2
