@@ -51,6 +51,12 @@ def source_for(W, dt, column=None):
                  rhs=r if column is None else 0) for r in cols]
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one curl-rows Q1-apply launch of
+# the default workload, from the ncu capture summarised in profiles/k_qapply_s_cavity_N32_k2_fp32.md
+# (taken on the kernel as it stands; to be re-taken whenever k_qapply_s changes)
+QAPPLY_TRAFFIC_BYTES = 834.205184e6 + 9.822208e6
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -360,6 +366,8 @@ def run_ours(args, rank, world, local_rank):
             w = W32[:, r]
             drift32.append(float(np.max(np.abs(w[3:] - w[3])) / w[3]) if len(w) > 4 else None)
         acc = dict(columns_checked=cols, rel_l2_e_vs_fp64_gpu=max(errs_e), rel_l2_b_vs_fp64_gpu=max(errs_b),
+                   fp64_gpu_vs_oracle=("every output of one step of this cavity within 1e-12 of the FP64 oracle "
+                                       "(its Q1 rows evaluated locally): tests/test_gpu_2_fullsize.py"),
                    energy_drift_fp64_after_pulse=max((d for d in drift64 if d is not None), default=None),
                    energy_every=100,
                    note="drift = max |W_n - W_300| / W_300 over n >= 300 (pulse over); FP64 reference = "
@@ -391,7 +399,10 @@ def run_ours(args, rank, world, local_rank):
                              d2h_bytes_per_step=rs * (ctx.N1 + ctx.N2) * R),
                     gpu_launches=launches,
                     roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
-                                  traffic=None, kernel="k_qapply_s" if R == 1 else "k_qapply_p",
+                                  traffic=(QAPPLY_TRAFFIC_BYTES if (R == 1 and W["n"] == 32 and W["k"] == 2 and
+                                                                    prec == Y.YGM_FP32) else None),
+                                  traffic_unit="bytes per launch (ncu, profiles/k_qapply_s_cavity_N32_k2_fp32.md)",
+                                  kernel="k_qapply_s" if R == 1 else ("k_qapply_rt" if prec != Y.YGM_FP64 else "k_qapply_p"),
                                   bytes_per_launch=alg_bytes,
                                   launches=dict(curl_rows_only=n_act, all_rows=n_all),
                                   streamed_gbs=streamed_gbs,

@@ -47,3 +47,13 @@ def test_workload_recipes_are_seeded_and_in_range():
     src = bench.source_for(B, 0.01)
     assert len(src) == 64 and [s["rhs"] for s in src] == list(range(64))
     assert all(abs(s["sigma"] - 0.2) < 1e-15 and abs(s["t0"] - 0.8) < 1e-15 for s in src)
+
+
+def test_cpu_baseline_line_reports_single_and_all_core_rates():
+    """The timed oracle leg on a tiny sample: one process and one spawned replica per host core."""
+    import types
+    line = bench.cpu_baseline_line(types.SimpleNamespace(cpu_n=2, cpu_steps=20))
+    assert line["kind"] == "oracle" and line["cores"] == (os.cpu_count() or 1)
+    assert line["value"] > 0 and line["single_thread"]["value"] > 0 and line["single_thread"]["cores"] == 1
+    assert line["first_workload_in_full"]["value"] > 0
+    assert "2^3 cube" in line["sample"]
