@@ -402,7 +402,7 @@ def run_ours(args, rank, world, local_rank):
                                   traffic=(QAPPLY_TRAFFIC_BYTES if (R == 1 and W["n"] == 32 and W["k"] == 2 and
                                                                     prec == Y.YGM_FP32) else None),
                                   traffic_unit="bytes per launch (ncu, profiles/k_qapply_s_cavity_N32_k2_fp32.md)",
-                                  kernel="k_qapply_s" if R == 1 else ("k_qapply_rt" if prec != Y.YGM_FP64 else "k_qapply_p"),
+                                  kernel="k_qapply_s" if R == 1 else "k_qapply_p",
                                   bytes_per_launch=alg_bytes,
                                   launches=dict(curl_rows_only=n_act, all_rows=n_all),
                                   streamed_gbs=streamed_gbs,

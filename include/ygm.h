@@ -161,6 +161,17 @@ int ygm_step(ygm_ctx* ctx, int64_t n, double dt, const ygm_source* src, int32_t 
  * context stream; errors YGM_EINVAL, YGM_ECFL, YGM_ENODEV, YGM_ECUDA. */
 int ygm_step_noalloc(ygm_ctx* ctx, void* e, const void* b_in, void* b_out, double dt);
 
+/* Splitting of one time step of ygm_step.  order 2 (default): the Strang leapfrog of Eq. strangSplit
+ * / Eq. YeeLeapfrog.  order 4: the higher-order splitting the paper mentions after Eq. strangSplit,
+ * taken as the symmetric triple composition of Strang steps of sizes w1 dt, w0 dt, w1 dt with
+ * w1 = 1 / (2 - 2^(1/3)), w0 = 1 - 2 w1 (Yoshida's fourth-order weights; w0 < 0, so the CFL check is
+ * |w0| dt <= tau_CFL).  The sub-steps reuse the leapfrog kernels with their own coefficients and
+ * the sources are applied at each sub-step's midpoint; the staggered b lags by w1 dt / 2.  Must be
+ * set before the first step (or after ygm_set_state / ygm_project_E); order 4 needs
+ * energy_every = 0 (W_n is the Strang leapfrog's invariant) and is not available to ygm_adjoint
+ * or the batch.  Errors: YGM_EINVAL. */
+int ygm_set_splitting(ygm_ctx* ctx, int32_t order);
+
 /* Conserved discrete energy of the current state (e_n, b_{n-1/2}), per right-hand side:
  *   W_n = 1/2 e_n^T Q1 e_n + 1/2 b_{n+1/2}^T M2 b_{n-1/2}
  * (telescoping invariant of the leapfrog; exact up to round-off without sources), and the
@@ -292,6 +303,26 @@ int ygm_batch_tune(ygm_batch* batch, int32_t trial_steps, const double* dt, cons
                    int32_t* order, double* ms_per_step);
 const char* ygm_batch_last_error(const ygm_batch* batch);
 void ygm_batch_destroy(ygm_batch* batch);   /* NULL-safe; does not destroy the members */
+
+/* ---- cubical Whitney GYM (the Yee scheme) on a periodic box: the structured-grid kernel family ----
+ * Sec. 4: with cubical Whitney forms (average-normalised DoFs, Eq. WhitneyFormDefn), the curl of
+ * Eq. dIsFiniteDiff (+-1/h), and diagonal Q1 and M2 (Eq. YeeMassMatrices: Q1 = Delta_V^-1 I,
+ * M2 = Delta_V I), the GYM leapfrog is Yee's method.  Grid n[3] cubes with edge lengths h[3],
+ * periodic; DoFs: x, y, z edges (e) and faces with x, y, z normals (b) anchored at each vertex
+ * (i, j, k), index a * nc + i + n0 (j + n1 k), nc = n0 n1 n2.  q1, m2: 3 nc positive diagonal
+ * values each (e.g. material weights or an S(1) SPAI), NULL for the lumped defaults.  The CFL bound
+ * is the Gershgorin bound of lambda_max(Q1 C^T M2 C) (conservative; ygm_yee_sizes).  State and
+ * staggering as for ygm_set_state / ygm_step / ygm_get_state; no sources.  Errors: YGM_EINVAL,
+ * YGM_ECFL, YGM_ECUDA, YGM_ENOMEM; messages via ygm_yee_last_error (NULL for creation). */
+typedef struct ygm_yee ygm_yee;
+int ygm_yee_create(const int32_t n[3], const double h[3], const double* q1, const double* m2, int32_t precision,
+                   int32_t device, void* stream, ygm_yee** out);
+int ygm_yee_sizes(const ygm_yee* yee, int64_t* n1, int64_t* n2, double* dt_cfl);
+int ygm_yee_set_state(ygm_yee* yee, const void* e, const void* b, int on_device);
+int ygm_yee_step(ygm_yee* yee, int64_t n, double dt);
+int ygm_yee_get_state(ygm_yee* yee, void* e, void* b, int on_device, int synced);
+const char* ygm_yee_last_error(const ygm_yee* yee);
+void ygm_yee_destroy(ygm_yee* yee);
 
 /* SPD check of Q1 (Sec. 5.1, practical considerations): Lanczos estimates of the smallest and
  * largest eigenvalue before any shift, the diagonal shift applied (0 if none), lambda_max(Q1 P2),

@@ -19,7 +19,9 @@ YGM_Q1_DEFAULT, YGM_Q1_DIAG, YGM_Q1_SM1, YGM_Q1_SM1SQ = 0, 1, 2, 3
 
 EXPORTED = ["ygm_create", "ygm_create_like", "ygm_sizes", "ygm_set_state", "ygm_get_state", "ygm_project_E", "ygm_step", "ygm_step_noalloc",
             "ygm_energy", "ygm_energy_history", "ygm_time", "ygm_export_q1", "ygm_set_q1", "ygm_spai_op", "ygm_cavity_modes", "ygm_q1_vjp", "ygm_q1_info",
-            "ygm_local_blocks", "ygm_kernel_timing", "ygm_kernel_times", "ygm_launch_count", "ygm_adjoint",
+            "ygm_local_blocks", "ygm_kernel_timing", "ygm_kernel_times", "ygm_launch_count", "ygm_adjoint", "ygm_set_splitting",
+            "ygm_yee_create", "ygm_yee_sizes", "ygm_yee_set_state", "ygm_yee_step", "ygm_yee_get_state",
+            "ygm_yee_last_error", "ygm_yee_destroy",
             "ygm_batch_create", "ygm_batch_step", "ygm_batch_status", "ygm_batch_status_clear", "ygm_batch_wait_limit",
             "ygm_batch_tune", "ygm_batch_last_error",
             "ygm_batch_destroy",
@@ -75,6 +77,7 @@ def load_library(path=LIB_PATH):
         "ygm_spai_op": (C.c_int, [P, pD, C.c_int32, D, C.c_int32, D, pI32, pD]),
         "ygm_cavity_modes": (C.c_int, [P, C.c_int32, pD, pD, C.c_int32, D, pI32]),
         "ygm_q1_vjp": (C.c_int, [P, pD, pD]),
+        "ygm_set_splitting": (C.c_int, [P, C.c_int32]),
         "ygm_adjoint": (C.c_int, [P, I64, D, C.POINTER(ygm_source), C.c_int32, C.POINTER(C.c_uint8), C.c_int32, pD, pD]),
         "ygm_q1_info": (C.c_int, [P, pD, pD, pD, pD, pI32, pI32]),
         "ygm_local_blocks": (C.c_int, [P, pI32, pI32, pD, pD]),
@@ -90,6 +93,13 @@ def load_library(path=LIB_PATH):
         "ygm_batch_tune": (C.c_int, [P, C.c_int32, pD, C.POINTER(ygm_source), pI32, pI32, pD]),
         "ygm_batch_last_error": (C.c_char_p, [P]),
         "ygm_batch_destroy": (None, [P]),
+        "ygm_yee_create": (C.c_int, [C.POINTER(C.c_int32), pD, pD, pD, C.c_int32, C.c_int32, P, C.POINTER(P)]),
+        "ygm_yee_sizes": (C.c_int, [P, pI64, pI64, pD]),
+        "ygm_yee_set_state": (C.c_int, [P, P, P, C.c_int]),
+        "ygm_yee_step": (C.c_int, [P, I64, D]),
+        "ygm_yee_get_state": (C.c_int, [P, P, P, C.c_int, C.c_int]),
+        "ygm_yee_last_error": (C.c_char_p, [P]),
+        "ygm_yee_destroy": (None, [P]),
         "ygm_last_error": (C.c_char_p, [P]),
         "ygm_destroy": (None, [P]),
     }
@@ -203,6 +213,10 @@ class Context:
             outp[0], outp[1], outp[2] = float(v[0]), float(v[1]), float(v[2])
         self._cb = E0_CB(cb)
         self._check(_lib.ygm_project_E(self._h, self._cb, None, rhs))
+
+    def set_splitting(self, order):
+        """2: Strang leapfrog (default); 4: fourth-order symmetric composition (ygm_set_splitting)."""
+        self._check(_lib.ygm_set_splitting(self._h, int(order)))
 
     def step(self, n, dt, sources=()):
         self._check(_lib.ygm_step(self._h, int(n), float(dt), _source_array(sources), len(sources)))
@@ -345,6 +359,57 @@ class Context:
         r, u, st = C.c_int64(), C.c_int64(), C.c_int64()
         self._check(_lib.ygm_qapply_counts(self._h, 1 if all_rows else 0, C.byref(r), C.byref(u), C.byref(st)))
         return r.value, u.value, st.value
+
+
+class Yee:
+    """Cubical Whitney GYM (Yee) on a periodic box (ygm_yee_*): n = (n0, n1, n2) cubes, h = edge
+    lengths, optional diagonal q1 / m2 (3 n0 n1 n2 values each)."""
+
+    def __init__(self, n, h, q1=None, m2=None, precision=YGM_FP64, device=0, stream=None):
+        nn = (C.c_int32 * 3)(*[int(v) for v in n])
+        hh = (C.c_double * 3)(*[float(v) for v in h])
+        self._q = None if q1 is None else np.ascontiguousarray(q1, np.float64)
+        self._m = None if m2 is None else np.ascontiguousarray(m2, np.float64)
+        pq = self._q.ctypes.data_as(C.POINTER(C.c_double)) if self._q is not None else None
+        pm = self._m.ctypes.data_as(C.POINTER(C.c_double)) if self._m is not None else None
+        self._h = C.c_void_p()
+        rc = _lib.ygm_yee_create(nn, hh, pq, pm, precision, device, C.c_void_p(stream) if stream else None,
+                                 C.byref(self._h))
+        if rc:
+            raise YgmError(rc, _lib.ygm_yee_last_error(None).decode())
+        self.dtype = np.float64 if precision == YGM_FP64 else np.float32
+        n1, n2, dt = C.c_int64(), C.c_int64(), C.c_double()
+        self._check(_lib.ygm_yee_sizes(self._h, C.byref(n1), C.byref(n2), C.byref(dt)))
+        self.N1, self.N2, self.tau_cfl = n1.value, n2.value, dt.value
+
+    def _check(self, rc):
+        if rc:
+            raise YgmError(rc, _lib.ygm_yee_last_error(self._h).decode())
+
+    def set_state(self, e, b):
+        pe, de = _ptr(e)
+        pb, db = _ptr(b)
+        self._check(_lib.ygm_yee_set_state(self._h, pe, pb, de))
+
+    def step(self, n, dt):
+        self._check(_lib.ygm_yee_step(self._h, int(n), float(dt)))
+
+    def get_state(self, synced=True):
+        e = np.empty(self.N1, self.dtype)
+        b = np.empty(self.N2, self.dtype)
+        self._check(_lib.ygm_yee_get_state(self._h, _ptr(e)[0], _ptr(b)[0], 0, 1 if synced else 0))
+        return e, b
+
+    def close(self):
+        if self._h:
+            _lib.ygm_yee_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:

@@ -1,4 +1,4 @@
-"""Build libygm.so in-tree for sm_103a (nvcc, parallel compile of the two translation units)."""
+"""Build libygm.so in-tree for sm_103a (nvcc, parallel compile of the three translation units)."""
 import os
 import shutil
 import subprocess
@@ -19,7 +19,7 @@ def _nvcc():
 
 
 def build(verbose=False, force=False):
-    srcs = [os.path.join(CSRC, f) for f in ("builder.cpp", "ygm.cu", "builder.h")]
+    srcs = [os.path.join(CSRC, f) for f in ("builder.cpp", "ygm.cu", "yee.cu", "builder.h")]
     srcs.append(os.path.join(os.path.dirname(HERE), "include", "ygm.h"))
     if not force and os.path.exists(OUT) and all(os.path.getmtime(OUT) >= os.path.getmtime(s) for s in srcs):
         return OUT
@@ -30,6 +30,7 @@ def build(verbose=False, force=False):
     jobs = [
         [nvcc, "-x", "c++", *common, "-c", os.path.join(CSRC, "builder.cpp"), "-o", os.path.join(bdir, "builder.o")],
         [nvcc, *ARCH, *common, "-Xptxas", "-O3", "-c", os.path.join(CSRC, "ygm.cu"), "-o", os.path.join(bdir, "ygm.o")],
+        [nvcc, *ARCH, *common, "-Xptxas", "-O3", "-c", os.path.join(CSRC, "yee.cu"), "-o", os.path.join(bdir, "yee.o")],
     ]
 
     def run(cmd):
@@ -39,10 +40,11 @@ def build(verbose=False, force=False):
         if verbose and (r.stdout or r.stderr):
             print(r.stdout + r.stderr, file=sys.stderr)
 
-    with ThreadPoolExecutor(2) as ex:
+    with ThreadPoolExecutor(3) as ex:
         list(ex.map(run, jobs))
     tmp = OUT + ".tmp"
     run([nvcc, *ARCH, "-shared", "-o", tmp, os.path.join(bdir, "builder.o"), os.path.join(bdir, "ygm.o"),
+         os.path.join(bdir, "yee.o"),
          "-Xcompiler", "-pthread"])
     os.replace(tmp, OUT)
     return OUT

@@ -1164,17 +1164,35 @@ __global__ void __launch_bounds__(256, 1) k_curlT_e_tc(TcGeo G, const int4* __re
             gidx[i] = gi;
         }
         __syncthreads();
-        // A = gathered b, K-major: one warp instruction fills an (8 rows x 4 k) tile, conflict-free
-        for (int tile = warp; tile < 16 * KC; tile += blockDim.x >> 5) {
-            const int grp = tile / KC, kc = tile - grp * KC;
-            const int m = grp * 8 + (lane & 7), k = kc * 4 + (lane >> 3);
-            const int p = m >> G.rshift, r = m & (R - 1);
-            const int gi = p < G.P ? gidx[p * G.Kp + k] : -1;
-            const float v = gi >= 0 ? __ldg(b + ((long long)gi << G.rshift) + r) : 0.f;
-            const int off = grp * G.sboA + kc * 128 + (lane & 7) * 16 + (lane >> 3) * 4;
-            const float hi = PASSES == 3 ? tf32_hi(v) : v;
-            *(float*)(sAhi + off) = hi;
-            if (PASSES == 3) *(float*)(sAlo + off) = v - hi;
+        // A = gathered b, K-major: one warp instruction fills an (8 rows x 4 k) tile, conflict-free;
+        // eight tiles per round, their loads issued before the first store
+        {
+            const int nw = blockDim.x >> 5, ntile = 16 * KC;
+            for (int t0 = warp; t0 < ntile; t0 += 8 * nw) {
+                float v[8];
+                int off[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int tile = t0 + u * nw;
+                    v[u] = 0.f;
+                    off[u] = -1;
+                    if (tile < ntile) {
+                        const int grp = tile / KC, kc = tile - grp * KC;
+                        const int m = grp * 8 + (lane & 7), k = kc * 4 + (lane >> 3);
+                        const int p = m >> G.rshift, r = m & (R - 1);
+                        const int gi = p < G.P ? gidx[p * G.Kp + k] : -1;
+                        if (gi >= 0) v[u] = __ldg(b + ((long long)gi << G.rshift) + r);
+                        off[u] = grp * G.sboA + kc * 128 + (lane & 7) * 16 + (lane >> 3) * 4;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (off[u] >= 0) {
+                        const float hi = PASSES == 3 ? tf32_hi(v[u]) : v[u];
+                        *(float*)(sAhi + off[u]) = hi;
+                        if (PASSES == 3) *(float*)(sAlo + off[u]) = v[u] - hi;
+                    }
+            }
         }
         asm volatile("fence.proxy.async.shared::cta;");
         __syncthreads();
@@ -1228,19 +1246,32 @@ __global__ void __launch_bounds__(256, 1) k_curlT_e_tc(TcGeo G, const int4* __re
                              : "r"(taddr));
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
                 if (!okp) continue;
+                long long gi[8], pi[8];
+                float eo[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const int j = jc + u;
-                    if (j >= G.Ma) break;
-                    const DCls C = c1[acls[j]];
-                    const int rx = vx - C.lo[0], ry = vy - C.lo[1], rz = vz - C.lo[2];
-                    if (!in_box(C, rx, ry, rz)) continue;
-                    const long long gi = (C.off + ((long long)rz * C.num[1] + ry) * C.num[0] + rx) << G.rshift;
-                    const float d = __uint_as_float(v[u]);
-                    const float nv = fmaf(ctau.lo, d, fmaf(ctau.hi, d, e[gi + r]));
-                    e[gi + r] = nv;
-                    ep[((long long)pad_index(C, pg, vx, vy, vz) << G.rshift) + r] = nv;
+                    gi[u] = -1;
+                    pi[u] = 0;
+                    eo[u] = 0.f;
+                    if (j < G.Ma) {
+                        const DCls C = c1[acls[j]];
+                        const int rx = vx - C.lo[0], ry = vy - C.lo[1], rz = vz - C.lo[2];
+                        if (in_box(C, rx, ry, rz)) {
+                            gi[u] = ((C.off + ((long long)rz * C.num[1] + ry) * C.num[0] + rx) << G.rshift) + r;
+                            pi[u] = ((long long)pad_index(C, pg, vx, vy, vz) << G.rshift) + r;
+                            eo[u] = e[gi[u]];
+                        }
+                    }
                 }
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (gi[u] >= 0) {
+                        const float d = __uint_as_float(v[u]);
+                        const float nv = fmaf(ctau.lo, d, fmaf(ctau.hi, d, eo[u]));
+                        e[gi[u]] = nv;
+                        ep[pi[u]] = nv;
+                    }
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
@@ -1534,6 +1565,7 @@ struct ygm_ctx {
     SBlk *lblks_b = nullptr, *lblks_e = nullptr;
     int nlb = 0, nle = 0;
     int64_t qc_rows[2] = {0, 0}, qc_unique[2] = {0, 0}, qc_stored[2] = {0, 0};   // [active only, all rows]
+    std::vector<double> split_w{1.0};        // weights of the composed splitting (Strang: {1})
     int tc_passes = 0;                       // > 0: C^T M2 on tensor cores (YGM_FP32_TC_*), 1 or 3 TF32 passes
     TcGeo tcg{};
     int4* uterm = nullptr;                   // union of the merged C^T M2 terms (class, dx, dy, dz)
@@ -2582,7 +2614,7 @@ int ygm_get_state(ygm_ctx* ctx, void* e, void* b, int on_device, int synced) {
         if (synced && ctx->staggered) {
             CK(cudaMemcpyAsync(ctx->bscr, ctx->b[ctx->cur], nb, cudaMemcpyDeviceToDevice, ctx->stream));
             launch_qapply(ctx, ctx->x, false);
-            launch_curl_b(ctx, ctx->x, ctx->b[ctx->cur], ctx->bscr, 0.5 * ctx->dt_prev);
+            launch_curl_b(ctx, ctx->x, ctx->b[ctx->cur], ctx->bscr, 0.5 * ctx->split_w[0] * ctx->dt_prev);
             src = ctx->bscr;
         }
         CK(cudaMemcpyAsync(b, src, nb, kind, ctx->stream));
@@ -2728,35 +2760,54 @@ int ygm_step(ygm_ctx* ctx, int64_t n, double dt, const ygm_source* src, int32_t 
     if (ctx && ctx->host_only) return fail(ctx, YGM_ENODEV, "context was created host-only (device = -1)");
     if (!ctx) return YGM_EINVAL;
     if (n < 0 || !(dt > 0) || !std::isfinite(dt)) return fail(ctx, YGM_EINVAL, "need n >= 0 and finite dt > 0");
-    if (dt > ctx->S.tau_cfl * (1.0 + 1e-12))
-        return fail(ctx, YGM_ECFL, "dt exceeds the CFL bound 2/omega_max (Prop. stability)");
+    const std::vector<double>& wts = ctx->split_w;
+    double wmax = 0.0;
+    for (double w : wts) wmax = std::max(wmax, std::fabs(w));
+    if (wmax * dt > ctx->S.tau_cfl * (1.0 + 1e-12))
+        return fail(ctx, YGM_ECFL, "dt (times the largest splitting weight) exceeds the CFL bound 2/omega_max (Prop. stability)");
     if (n_src < 0 || (n_src > 0 && !src)) return fail(ctx, YGM_EINVAL, "bad source list");
     int rc = set_sources(ctx, src, n_src);
     if (rc) return rc;
     CK(cudaSetDevice(ctx->device));
     void* b0 = ctx->b[ctx->cur];
+    const double w1 = wts[0];
     if (!ctx->staggered) {
-        // initial half step Phi^e_{dt/2} (Eq. YeeLeapfrog): b_{-1/2} = b_0 + dt/2 C Q1 e_0
+        // initial half step Phi^e_{dt/2} (Eq. YeeLeapfrog): b_{-1/2} = b_0 + dt/2 C Q1 e_0 (with a
+        // composed splitting, the half of its first Strang sub-step, w_1 dt / 2)
         launch_qapply(ctx, ctx->x, false);
-        launch_curl_b(ctx, ctx->x, b0, b0, -0.5 * dt);
+        launch_curl_b(ctx, ctx->x, b0, b0, -0.5 * w1 * dt);
         ctx->staggered = true;
         ctx->step_base = ctx->step;
         ctx->t_base = 0.0;
     } else if (dt != ctx->dt_prev) {
         // close the old staggering and reopen it with the new step (exact Strang composition)
         launch_qapply(ctx, ctx->x, false);
-        launch_curl_b(ctx, ctx->x, b0, b0, 0.5 * ctx->dt_prev - 0.5 * dt);
+        launch_curl_b(ctx, ctx->x, b0, b0, 0.5 * w1 * ctx->dt_prev - 0.5 * w1 * dt);
         ctx->t_base += (double)(ctx->step - ctx->step_base) * ctx->dt_prev;
         ctx->step_base = ctx->step;
     }
     ctx->dt_prev = dt;
     // source amplitudes dt * s(t_{n+1/2}) for every step of this call (host, FP64); steps whose
     // amplitudes are all exactly 0.0 need no source launch (the update would add 0)
+    // sub-steps of one step: kicks w_j dt at the sub-step midpoints, drifts (w_{j-1} + w_j) / 2 dt
+    // (w_1 dt for the first: the pending half of the previous step's last sub-step, w_m = w_1, plus
+    // its own leading half)
+    const int m = (int)wts.size();
+    std::vector<double> kick(m), drift(m), tmid(m);
+    {
+        double acc = 0.0;
+        for (int j = 0; j < m; ++j) {
+            kick[j] = wts[j];
+            drift[j] = j == 0 ? wts[0] : 0.5 * (wts[j - 1] + wts[j]);
+            tmid[j] = acc + 0.5 * wts[j];
+            acc += wts[j];
+        }
+    }
     const double* amp_dev = nullptr;
     std::vector<char> src_on;
     if (ctx->nsrc && n > 0) {
         const int nsrc = ctx->nsrc;
-        const size_t namp = (size_t)n * nsrc;
+        const size_t namp = (size_t)n * m * nsrc;
         int bsel = ctx->damp_cur;
         ctx->damp_cur ^= 1;
         CK(cudaEventSynchronize(ctx->damp_ev[bsel]));   // the buffer's previous readers are done
@@ -2770,17 +2821,18 @@ int ygm_step(ygm_ctx* ctx, int64_t n, double dt, const ygm_source* src, int32_t 
             ctx->damp_cap[bsel] = namp;
         }
         double* amp = ctx->hamp[bsel];
-        src_on.assign(n, 0);
-        for (int64_t i = 0; i < n; ++i) {
-            const double t = ctx->t_base + ((double)(ctx->step + i - ctx->step_base) + 0.5) * dt;
-            for (int q = 0; q < nsrc; ++q) {
-                const ygm_source& S0 = ctx->src_cache[q];
-                const double u = (t - S0.t0) / S0.sigma;
-                const double a = dt * S0.amp * std::exp(-u * u) * std::sin(S0.omega * (t - S0.t0));
-                amp[(size_t)i * nsrc + q] = a;
-                if (a != 0.0) src_on[i] = 1;
+        src_on.assign((size_t)n * m, 0);
+        for (int64_t i = 0; i < n; ++i)
+            for (int j = 0; j < m; ++j) {
+                const double t = ctx->t_base + ((double)(ctx->step + i - ctx->step_base) + tmid[j]) * dt;
+                for (int q = 0; q < nsrc; ++q) {
+                    const ygm_source& S0 = ctx->src_cache[q];
+                    const double u = (t - S0.t0) / S0.sigma;
+                    const double a = kick[j] * dt * S0.amp * std::exp(-u * u) * std::sin(S0.omega * (t - S0.t0));
+                    amp[((size_t)i * m + j) * nsrc + q] = a;
+                    if (a != 0.0) src_on[(size_t)i * m + j] = 1;
+                }
             }
-        }
         CK(cudaMemcpyAsync(ctx->damp[bsel], amp, namp * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
         amp_dev = ctx->damp[bsel];
     }
@@ -2803,18 +2855,38 @@ int ygm_step(ygm_ctx* ctx, int64_t n, double dt, const ygm_source* src, int32_t 
         }
     }
     for (int64_t i = 0; i < n; ++i) {
-        void* bo = ctx->b[ctx->cur];
-        void* bn = ctx->b[ctx->cur ^ 1];
-        const bool want_w = ctx->energy_every && ctx->step % ctx->energy_every == 0;
-        launch_qapply(ctx, ctx->x, want_w);     // W_n needs e^T Q1 e over every row
-        launch_curl_b(ctx, ctx->x, bo, bn, dt);
-        if (want_w) launch_energy(ctx, ctx->e, ctx->x, bn, bo, ctx->hist + (size_t)ctx->n_rhs * ctx->hist_n++);
-        launch_curlT_e(ctx, bn, ctx->e, dt, amp_dev && src_on[i] ? amp_dev + (size_t)i * ctx->nsrc : nullptr);
-        ctx->cur ^= 1;
+        for (int j = 0; j < m; ++j) {
+            void* bo = ctx->b[ctx->cur];
+            void* bn = ctx->b[ctx->cur ^ 1];
+            const bool want_w = m == 1 && ctx->energy_every && ctx->step % ctx->energy_every == 0;
+            launch_qapply(ctx, ctx->x, want_w);     // W_n needs e^T Q1 e over every row
+            launch_curl_b(ctx, ctx->x, bo, bn, drift[j] * dt);
+            if (want_w) launch_energy(ctx, ctx->e, ctx->x, bn, bo, ctx->hist + (size_t)ctx->n_rhs * ctx->hist_n++);
+            const size_t si = (size_t)i * m + j;
+            launch_curlT_e(ctx, bn, ctx->e, kick[j] * dt, amp_dev && src_on[si] ? amp_dev + si * ctx->nsrc : nullptr);
+            ctx->cur ^= 1;
+        }
         ctx->step++;
     }
     if (amp_dev) CK(cudaEventRecord(ctx->damp_ev[ctx->damp_cur ^ 1], ctx->stream));
     CK(cudaGetLastError());
+    return YGM_OK;
+}
+
+int ygm_set_splitting(ygm_ctx* ctx, int32_t order) {
+    if (!ctx) return YGM_EINVAL;
+    if (ctx->staggered)
+        return fail(ctx, YGM_EINVAL, "set the splitting before the first step (or after ygm_set_state / ygm_project_E)");
+    if (order == 2) {
+        ctx->split_w.assign(1, 1.0);
+    } else if (order == 4) {
+        if (ctx->energy_every)
+            return fail(ctx, YGM_EINVAL, "W_n is the invariant of the Strang leapfrog only: energy_every must be 0 for order 4");
+        const double c = std::cbrt(2.0), w1 = 1.0 / (2.0 - c);
+        ctx->split_w = {w1, -c * w1, w1};
+    } else {
+        return fail(ctx, YGM_EINVAL, "splitting order must be 2 or 4");
+    }
     return YGM_OK;
 }
 
@@ -2827,10 +2899,11 @@ int ygm_energy(ygm_ctx* ctx, double* W, double* Htilde) {
     void* bo = ctx->b[ctx->cur];
     launch_qapply(ctx, ctx->x, true);
     if (ctx->staggered) {
+        const double tw = ctx->split_w[0] * ctx->dt_prev;   // the (first) Strang sub-step
         CK(cudaMemcpyAsync(ctx->bscr, bo, nb, cudaMemcpyDeviceToDevice, ctx->stream));
-        launch_curl_b(ctx, ctx->x, bo, ctx->bscr, ctx->dt_prev);
+        launch_curl_b(ctx, ctx->x, bo, ctx->bscr, tw);
         launch_energy(ctx, ctx->e, ctx->x, ctx->bscr, bo, dout);
-        launch_curl_b(ctx, ctx->x, bo, ctx->bscr, 0.5 * ctx->dt_prev);
+        launch_curl_b(ctx, ctx->x, bo, ctx->bscr, 0.5 * tw);
         launch_energy(ctx, ctx->e, ctx->x, ctx->bscr, ctx->bscr, dout + R);
     } else {
         // not yet staggered: b is synchronised, W is reported as H~
@@ -3207,8 +3280,8 @@ int ygm_batch_create(ygm_ctx* const* cavities, int32_t count, ygm_batch** out) {
         ygm_ctx* x = cavities[i];
         if (!x) return bad(YGM_EINVAL, "NULL context");
         if (x->host_only) return bad(YGM_ENODEV, "host-only context in the batch");
-        if (!x->use_sym || x->n_rhs != 1 || !x->wterms || !x->nle || x->tc_passes)
-            return bad(YGM_EINVAL, "batch members must be one-column FP32/FP64 contexts with uniform mu on the lattice path");
+        if (!x->use_sym || x->n_rhs != 1 || !x->wterms || !x->nle || x->tc_passes || x->split_w.size() != 1)
+            return bad(YGM_EINVAL, "batch members must be one-column FP32/FP64 Strang contexts with uniform mu on the lattice path");
         if (x->device != cavities[0]->device || x->precision != cavities[0]->precision)
             return bad(YGM_EINVAL, "batch members must share the device and the precision");
         B->cav.push_back(x);
@@ -3771,8 +3844,8 @@ int ygm_adjoint(ygm_ctx* ctx, int64_t nsteps, double dt, const ygm_source* src, 
         return fail(ctx, YGM_EINVAL, "need nsteps >= 1, finite dt > 0 and checkpoint_every >= 1");
     if (dt > ctx->S.tau_cfl * (1.0 + 1e-12))
         return fail(ctx, YGM_ECFL, "dt exceeds the CFL bound 2/omega_max (Prop. stability)");
-    if (!ctx->use_sym || ctx->n_rhs != 1 || !ctx->wterms)
-        return fail(ctx, YGM_EINVAL, "ygm_adjoint needs a one-column context with uniform mu on the lattice path");
+    if (!ctx->use_sym || ctx->n_rhs != 1 || !ctx->wterms || ctx->split_w.size() != 1)
+        return fail(ctx, YGM_EINVAL, "ygm_adjoint needs a one-column Strang context with uniform mu on the lattice path");
     if (n_src < 0 || (n_src > 0 && !src)) return fail(ctx, YGM_EINVAL, "bad source list");
     int rc = set_sources(ctx, src, n_src);
     if (rc) return rc;

@@ -9,6 +9,7 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 import synth
+from oracle.gym import DipoleSource
 from oracle_runs import oracle_model, run_oracle, rel_l2, te110
 
 Y = pytest.importorskip("paper_2301_01753_gb300")
@@ -247,3 +248,35 @@ def test_energy_history_keeps_every_record():
     assert len(W) == 70000
     assert np.max(np.abs(W - W[0])) / W[0] < 1e-11
     c.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-5)])
+def test_fourth_order_splitting_follows_the_oracle(precision, tol):
+    """ygm_set_splitting(4): each step the symmetric composition of Strang steps w1, w0, w1 (with a
+    negative middle weight) against the oracle's composed_step, sources at sub-step midpoints."""
+    from oracle.gym import yoshida4
+    n, k, steps = 3, 2, 60
+    f, g, eps, _ = oracle_model(n, k, eps_seed=2000)
+    w = yoshida4()
+    tau = 0.5 * g.tau_cfl() / abs(w[1])
+    src = [_dipole(tau, width=5.0)]
+    J = DipoleSource(f, [dict(s) for s in src], tau)
+    rng = np.random.default_rng(8)
+    e0 = rng.standard_normal(f.mesh.N1)
+    b0 = f.C() @ rng.standard_normal(f.mesh.N1)
+    e_or, b_or = g.run_composed(e0.copy(), b0.copy(), tau, steps, w, source=J)
+    c = Y.Context(n, k, eps=eps, precision=precision)
+    c.set_splitting(4)
+    dtp = np.float64 if precision == 0 else np.float32
+    c.set_state(e0.astype(dtp), b0.astype(dtp))
+    c.step(25, tau, [dict(s) for s in src])
+    c.step(35, tau, [dict(s) for s in src])
+    e, b = c.get_state(synced=True)
+    assert rel_l2(e, e_or) < tol and rel_l2(b, b_or) < tol
+    assert c.time()[0] == steps and abs(c.time()[1] - steps * tau) < 1e-12
+    with pytest.raises(Y.YgmError) as ei:
+        c.set_splitting(2)                                 # only before the first step
+    assert ei.value.code == Y.YGM_EINVAL
+    with pytest.raises(Y.YgmError) as ei:
+        c.step(1, 1.01 * c.tau_cfl / abs(w[1]))           # CFL on the largest sub-step
+    assert ei.value.code == Y.YGM_ECFL
