@@ -1,8 +1,9 @@
 """GPU (sm_103a) parity of the C-ABI leapfrog against the FP64 oracle.
 
 Tolerances (relative L2 of e and b): FP64 1e-12 (same operators and operation order up to
-summation order); FP32 5e-5 after the run (float state and Q1: rounding errors of about 6e-8 per
-operation, accumulated over a few hundred norm-preserving steps)."""
+summation order); FP32 1e-5 after the run (float state and Q1 with compensated Q1 sums and a hi/lo
+step size: rounding errors of about 6e-8 per operation, accumulated over a few hundred
+norm-preserving steps; measured 1.3e-6 / 2.2e-6 on the dipole case)."""
 import numpy as np
 import pytest
 
@@ -15,7 +16,7 @@ from oracle_runs import oracle_model, run_oracle, rel_l2, te110
 Y = pytest.importorskip("paper_2301_01753_gb300")
 
 FP64_TOL = 1e-12
-FP32_TOL = 5e-5
+FP32_TOL = 1e-5
 
 
 def _dipole(tau, x=(0.41, 0.52, 0.47), d=(0.0, 0.0, 1.0), width=20.0):

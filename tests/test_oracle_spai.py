@@ -204,3 +204,33 @@ def test_default_policy_keeps_the_lowest_cavity_modes(n, k, tol):
     wq = np.sort(np.linalg.eigvals(Q.toarray() @ P2).real)
     wq = wq[wq > 1e-8 * wq[-1]][:3]
     assert np.all(np.abs(wq - we) / we < tol)
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_primed_basis_assembled_tet_by_tet_gives_the_same_q1(k):
+    """Reading R2, pinned from a second route: the primed mass matrix assembled tet by tet from the
+    transformed local blocks (T restricted to each tet's DoFs: every entity lies in the tet)
+    equals T M1 T^T, is the identity inside every entity, and its column SPAI mapped back as
+    T^T Q' T is, entry by entry, the Q1 of gym_q1."""
+    f = FEM(KuhnMesh(2, k), eps=synth.tet_eps(15 + k, 2, 1, 4))
+    M1 = f.M1()
+    T = SP.ortho_basis_transform(f, M1).toarray()
+    N1 = f.mesh.N1
+    Mp = np.zeros((N1, N1))
+    for t in range(f.mesh.n_tets):
+        d = f.dof1[t]
+        ok = np.nonzero(d >= 0)[0]
+        g = d[ok]
+        blk = f.eps[t] * f.local(f.mesh.tet_shape[t])["M1"][np.ix_(ok, ok)]
+        Tt = T[np.ix_(g, g)]
+        Mp[np.ix_(g, g)] += Tt @ blk @ Tt.T
+    assert np.allclose(Mp, T @ M1.toarray() @ T.T, rtol=0, atol=1e-12 * np.abs(Mp).max())
+    for grp in sum(SP.entity_groups(f), []):
+        grp = list(grp)
+        assert np.allclose(Mp[np.ix_(grp, grp)], np.eye(len(grp)), atol=1e-10)
+    S = SP.pattern("sm1sq", M1, f.dof1)
+    Qp = SP.symmetrize(SP.spai_columns(sp.csr_matrix(Mp), S)).toarray()
+    Q_route2 = T.T @ Qp @ T
+    Q_route2 = 0.5 * (Q_route2 + Q_route2.T)
+    Q, _ = SP.gym_q1(f, M1)
+    assert np.abs(Q_route2 - Q.toarray()).max() <= 1e-9 * np.abs(Q.toarray()).max()
