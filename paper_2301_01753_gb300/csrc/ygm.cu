@@ -1104,8 +1104,13 @@ __device__ __forceinline__ unsigned long long umma_desc(unsigned addr, unsigned 
            ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);   // version 1, no swizzle
 }
 __device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
+// 3xTF32 tables fill most of shared memory (one CTA per SM): 16 warps, all of which gather.  One
+// pass: 8 warps, so that two CTAs fit per SM.  Warps 0-7 read the accumulator back (4 lane
+// quarters x 2 column halves).
 template <int PASSES>
-__global__ void __launch_bounds__(256, 1) k_curlT_e_tc(TcGeo G, const int4* __restrict__ uterm, const DCls* __restrict__ c1,
+constexpr int tc_threads() { return PASSES == 3 ? 512 : 256; }
+template <int PASSES>
+__global__ void __launch_bounds__(tc_threads<PASSES>(), 1) k_curlT_e_tc(TcGeo G, const int4* __restrict__ uterm, const DCls* __restrict__ c1,
                                                        const DCls* __restrict__ c2, const int* __restrict__ acls,
                                                        const float* __restrict__ Wt, const float* __restrict__ b,
                                                        float* __restrict__ e, float* __restrict__ ep, PadGeo pg,
@@ -1230,8 +1235,8 @@ __global__ void __launch_bounds__(256, 1) k_curlT_e_tc(TcGeo G, const int4* __re
         }
         phase ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        if (!failed) {
-            // epilogue: warp w reads lanes 32 (w % 4) .. +31 (rows m) and half of the columns
+        if (!failed && warp < 8) {
+            // epilogue: warp w < 8 reads lanes 32 (w % 4) .. +31 (rows m) and half of the columns
             const int m = (warp & 3) * 32 + lane;
             const int p = m >> G.rshift, r = m & (R - 1);
             const int pt = bt * G.P + p;
@@ -2295,7 +2300,8 @@ static int launch_curlT_e(ygm_ctx* ctx, const void* b, void* e, double ctau, con
         if (!ctx->neblocks) {
         } else if (ctx->tc_passes && ctx->wt) {
             auto k = ctx->tc_passes == 3 ? k_curlT_e_tc<3> : k_curlT_e_tc<1>;
-            k<<<ctx->tc_grid, 256, ctx->tc_smem, ctx->stream>>>(ctx->tcg, ctx->uterm, ctx->c1, ctx->c2, ctx->acls, ctx->wt,
+            const int thr = ctx->tc_passes == 3 ? tc_threads<3>() : tc_threads<1>();
+            k<<<ctx->tc_grid, thr, ctx->tc_smem, ctx->stream>>>(ctx->tcg, ctx->uterm, ctx->c1, ctx->c2, ctx->acls, ctx->wt,
                                                                (const float*)b, (float*)e, (float*)ctx->ep, ctx->pg,
                                                                split_tau<float>(ctau), ctx->tc_err);
         } else if (ctx->pterms) {
