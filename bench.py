@@ -256,7 +256,9 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     W = workload(n=args.n, k=args.order, leapfrog_steps=args.leapfrog_steps, rhs=args.rhs)
     R = args.rhs
-    stream = torch.cuda.current_stream()
+    # a stream of our own: the context launches on it and the timing events are recorded on it
+    stream = torch.cuda.Stream(device=local_rank)
+    torch.cuda.set_stream(stream)
     prec = dict(fp32=Y.YGM_FP32, fp64=Y.YGM_FP64, tf32=Y.YGM_FP32_TC_TF32, tf32x3=Y.YGM_FP32_TC_3XTF32)[args.precision]
     tb = time.perf_counter()
     # the timed context also records the conserved energy every 100 steps (row A-5)

@@ -88,7 +88,11 @@ typedef struct {
     int32_t device;        /* CUDA device ordinal; -1 = host-only set-up (operators can be
                               inspected with ygm_sizes / ygm_export_q1 / ygm_local_blocks /
                               ygm_q1_info; every stepping call returns YGM_ENODEV) */
-    void*   stream;        /* cudaStream_t to run on; NULL = the context creates its own */
+    void*   stream;        /* cudaStream_t to run on; NULL = the context creates its own
+                              non-blocking stream.  cudaStreamLegacy is accepted, but a batch
+                              whose first member runs on it cannot replay a CUDA graph (the
+                              legacy stream cannot be captured: ygm_batch_step returns
+                              YGM_ECUDA with use_graph = 1) */
 } ygm_opts;
 
 /* Point dipole J = d delta(x - x0) s(t), s(t) = amp exp(-((t - t0)/sigma)^2) sin(omega (t - t0)),
@@ -333,6 +337,19 @@ int ygm_q1_info(const ygm_ctx* ctx, double* lmin, double* lmax, double* shift, d
 /* Local reference blocks (FP64, identical for the 6 Kuhn shapes in local order):
  * M1 (n1 x n1), M2 restricted to the curl-carrying 2-forms (n2a x n2a), sizes in n1/n2a. */
 int ygm_local_blocks(const ygm_ctx* ctx, int32_t* n1, int32_t* n2a, double* M1, double* M2a);
+
+/* Q1 apply kernel of a one-column context (x = Q1 e of Eq. YeeLeapfrog on the upper-triangle
+ * lattice: every value of the symmetric Q1 of Sec. 5 stored once per pair).  kernel: 0 = automatic
+ * (per-thread loads, the faster of the two on GB300: 205 us against 284 us for one FP32 apply at
+ * N = 32, k = 2), 1 = per-thread loads (k_qapply_s), 2 = bulk copies of each slot's run into
+ * shared-memory stages by a producer warp (k_qapply_t; available where every run it copies lies
+ * inside the stored lattice).
+ * stages (kernel 0 or 2): 0 = as many as fit (at most 4), else 2..8.  Both kernels add the same
+ * terms in the same order and give bit-identical x.  *blocks_per_sm (NULL allowed) receives the
+ * selected kernel's resident blocks per SM.  Synchronises the context stream.  Errors: YGM_EINVAL
+ * (kernel or stages out of range, kernel 2 unavailable, or a context with n_rhs > 1, which has
+ * no upper-triangle path), YGM_ENODEV, YGM_ECUDA. */
+int ygm_set_qapply(ygm_ctx* ctx, int32_t kernel, int32_t stages, int32_t* blocks_per_sm);
 
 /* Per-launch CUDA-event timing on the context stream: enable = 1 brackets every kernel launch
  * with a pair of events; ygm_kernel_times synchronises, returns the summed milliseconds and

@@ -19,7 +19,7 @@ YGM_Q1_DEFAULT, YGM_Q1_DIAG, YGM_Q1_SM1, YGM_Q1_SM1SQ = 0, 1, 2, 3
 
 EXPORTED = ["ygm_create", "ygm_create_like", "ygm_sizes", "ygm_set_state", "ygm_get_state", "ygm_project_E", "ygm_step", "ygm_step_noalloc",
             "ygm_energy", "ygm_energy_history", "ygm_time", "ygm_export_q1", "ygm_set_q1", "ygm_spai_op", "ygm_cavity_modes", "ygm_q1_vjp", "ygm_q1_info",
-            "ygm_local_blocks", "ygm_kernel_timing", "ygm_kernel_times", "ygm_launch_count", "ygm_adjoint", "ygm_set_splitting",
+            "ygm_local_blocks", "ygm_kernel_timing", "ygm_kernel_times", "ygm_set_qapply", "ygm_launch_count", "ygm_adjoint", "ygm_set_splitting",
             "ygm_yee_create", "ygm_yee_sizes", "ygm_yee_set_state", "ygm_yee_step", "ygm_yee_get_state",
             "ygm_yee_last_error", "ygm_yee_destroy",
             "ygm_batch_create", "ygm_batch_step", "ygm_batch_status", "ygm_batch_status_clear", "ygm_batch_wait_limit",
@@ -82,6 +82,7 @@ def load_library(path=LIB_PATH):
         "ygm_q1_info": (C.c_int, [P, pD, pD, pD, pD, pI32, pI32]),
         "ygm_local_blocks": (C.c_int, [P, pI32, pI32, pD, pD]),
         "ygm_kernel_timing": (C.c_int, [P, C.c_int]),
+        "ygm_set_qapply": (C.c_int, [P, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]),
         "ygm_kernel_times": (C.c_int, [P, pD, pI64]),
         "ygm_launch_count": (C.c_int, [P, pI64]),
         "ygm_qapply_counts": (C.c_int, [P, C.c_int, pI64, pI64, pI64]),
@@ -122,6 +123,15 @@ def _ptr(a):
     return a.ctypes.data_as(C.c_void_p), 0
 
 
+def _stream_arg(stream):
+    """cudaStream_t for the opts: None lets the context create its own non-blocking stream; 0 is
+    the legacy default stream (the handle torch reports for its default stream), passed as
+    cudaStreamLegacy so that work and events on torch's default stream are ordered with it."""
+    if stream is None:
+        return None
+    return C.c_void_p(1 if int(stream) == 0 else int(stream))
+
+
 class Context:
     """One GYM cavity: operators on the device plus the state (e, b)."""
 
@@ -130,7 +140,7 @@ class Context:
         self._h = C.c_void_p()
         mesh = ygm_mesh(int(n), float(side))
         opts = ygm_opts(precision, q1_pattern, n_rhs, energy_every, threads, device,
-                        C.c_void_p(stream) if stream else None)
+                        _stream_arg(stream))
         T = 6 * n ** 3
         self._eps = None if eps is None else np.ascontiguousarray(eps, np.float64)
         self._mu = None if mu is None else np.ascontiguousarray(mu, np.float64)
@@ -153,7 +163,7 @@ class Context:
         new._h = C.c_void_p()
         precision = self.precision if precision is None else precision
         dev = self.device if device is None else device
-        opts = ygm_opts(precision, 0, n_rhs, energy_every, 0, dev, C.c_void_p(stream) if stream else None)
+        opts = ygm_opts(precision, 0, n_rhs, energy_every, 0, dev, _stream_arg(stream))
         rc = _lib.ygm_create_like(self._h, C.byref(opts), C.byref(new._h))
         if rc:
             raise YgmError(rc, _lib.ygm_last_error(None).decode())
@@ -339,6 +349,13 @@ class Context:
                                           M2.ctypes.data_as(C.POINTER(C.c_double))))
         return M1.reshape(n1.value, -1), M2.reshape(n2a.value, -1)
 
+    def set_qapply(self, kernel=0, stages=0):
+        """Select the Q1 apply kernel (0 automatic, 1 per-thread loads, 2 bulk copies into shared-
+        memory stages; stages 0 = as many as fit) and return its resident blocks per SM."""
+        bps = C.c_int32(0)
+        self._check(_lib.ygm_set_qapply(self._h, int(kernel), int(stages), C.byref(bps)))
+        return bps.value
+
     def kernel_timing(self, enable=True):
         self._check(_lib.ygm_kernel_timing(self._h, 1 if enable else 0))
 
@@ -373,7 +390,7 @@ class Yee:
         pq = self._q.ctypes.data_as(C.POINTER(C.c_double)) if self._q is not None else None
         pm = self._m.ctypes.data_as(C.POINTER(C.c_double)) if self._m is not None else None
         self._h = C.c_void_p()
-        rc = _lib.ygm_yee_create(nn, hh, pq, pm, precision, device, C.c_void_p(stream) if stream else None,
+        rc = _lib.ygm_yee_create(nn, hh, pq, pm, precision, device, _stream_arg(stream),
                                  C.byref(self._h))
         if rc:
             raise YgmError(rc, _lib.ygm_yee_last_error(None).decode())

@@ -1405,6 +1405,10 @@ bool pack_sym(Setup& S, int threads_in) {
     S.qs_nz = L.n;
     S.qs_vol = (int64_t)S.qs_nx * S.qs_ny * S.qs_nz;
     S.qs_guard = (((int64_t)H * S.qs_ny + H) * S.qs_nx + H + 31) / 32 * 32;
+    // the device kernels copy whole runs of 256 lattice points per slot, plus 16 bytes, starting
+    // up to 16 bytes below a neighbour address: the band also covers a run that starts at the
+    // last lattice point of the last class
+    S.qs_guard = std::max<int64_t>(S.qs_guard, 512);
     for (size_t c = 0; c < nc; ++c) {
         const Box& b = L.c1[c].box;
         for (int a = 0; a < 3; ++a)

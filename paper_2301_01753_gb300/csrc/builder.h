@@ -126,7 +126,8 @@ struct Setup {
     // upper-triangle storage on the common anchor lattice for the plane-sweep Q1 apply: every
     // class and upper slot owns an NZ x NY x NX box indexed by the row's absolute anchor
     // (qsym[qs_base[c] + s * qs_vol + (vz * NY + vy) * NX + vx]), zero where no row exists, with a
-    // zeroed guard of qs_guard entries at both ends so every stencil neighbour address is in range
+    // zeroed guard of qs_guard entries (at least 512) at both ends so every stencil neighbour
+    // address, and every 256-point run the kernels copy from one, is in range
     int qs_nx = 0, qs_ny = 0, qs_nz = 0, qs_h = 0;
     int64_t qs_vol = 0, qs_guard = 0;
     std::vector<int64_t> qs_base;                // per class (size C1 + 1; the last is the end of the data)

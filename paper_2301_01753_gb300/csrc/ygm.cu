@@ -275,14 +275,28 @@ __device__ __forceinline__ void curl_b_rows(const SBlk& B, const DCls* __restric
     const int rx = vx - C.lo[0], ry = vy - C.lo[1];
     if ((unsigned)rx >= (unsigned)C.num[0] || (unsigned)ry >= (unsigned)C.num[1]) return;
     const int p = pad_row(g, vx, vy, B.vz);
-    real acc = real(0);
-    for (int s = C.st_begin; s < C.st_end; ++s) {
-        const CTermL T = terms[s];
-        const real xv = __ldg(xp + p + T.off);
-        acc += T.sign > 0 ? xv : -xv;
-    }
     const long long gi = C.off + ((long long)(B.vz - C.lo[2]) * C.num[1] + ry) * C.num[0] + rx;
-    const real v = fma(-ctau.lo, acc, fma(-ctau.hi, acc, b_in[gi]));
+    const real bo = b_in[gi];
+    // at most three terms (Whitney incidence) or one (curl of a higher-order 1-form): every load is
+    // issued before the first sum, which keeps the term order
+    const int nt = C.st_end - C.st_begin;
+    real xv[3];
+    int sg[3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+        xv[u] = real(0);
+        sg[u] = 0;
+        if (u < nt) {
+            const CTermL T = terms[C.st_begin + u];
+            xv[u] = __ldg(xp + p + T.off);
+            sg[u] = T.sign;
+        }
+    }
+    real acc = real(0);
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+        if (u < nt) acc += sg[u] > 0 ? xv[u] : -xv[u];
+    const real v = fma(-ctau.lo, acc, fma(-ctau.hi, acc, bo));
     b_out[gi] = v;
     bp[C.pbase + p] = v;
 }
@@ -872,6 +886,157 @@ __global__ void __launch_bounds__(SBLOCK, 1) k_qapply_s(const SBlk* __restrict__
     }
 }
 
+// x = Q1 e on the upper-triangle lattice with the Q1 stream moved off the threads' load path.
+// A block's slot s reads the SBLOCK consecutive lattice entries qs[q0 + t0 + o.x(s) + 0 .. SBLOCK-1],
+// one contiguous run per slot.  A producer warp copies the runs into a ring of nst shared-memory
+// stages (cp.async.bulk, QT_SPS slots per stage, one lane per slot; completion counted in bytes on
+// the stage's "full" mbarrier) while SBLOCK consumer threads, one per row as in k_qapply_s, read
+// their Q1 values from shared memory and gather e; each consumer warp signals a consumed stage on
+// its "empty" mbarrier, which the producer waits for before refilling it.  The warps never wait
+// for each other otherwise.  The sum runs over the same slots in the same order as k_qapply_s,
+// so both give bit-identical x.  A lower slot's run starts wherever its neighbour offset puts it:
+// the copy starts at the 16-byte boundary below and takes 16 bytes more, and the thread indexes
+// from the remainder.  Upper runs carry the L2 evict-last hint, lower runs evict-first, as in
+// k_qapply_s.  Every wait has an iteration cap: a warp that gives up sets bit QT_ERR_BIT of *err
+// and stops; the producer then waits (capped) for the copies it still has in flight, so that no
+// copy lands after the block has gone.  The qs guard band keeps every run, with its extra 16
+// bytes, inside the array.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+template <typename real>
+struct QtCfg {
+    static constexpr int SPS = 64 / (int)sizeof(real);             // slots per stage: 16 (FP32), 8 (FP64)
+    static constexpr int SL = SBLOCK + 16 / (int)sizeof(real);     // stage slice: one run + 16 bytes
+};
+constexpr int QT_THREADS = SBLOCK + 32;         // eight consumer warps and the producer warp
+constexpr int QT_HDR = 256;                     // shared-memory header: 2 x 8 mbarriers
+constexpr int QT_ERR_BIT = 2;
+constexpr long long QT_WAIT_CAP = 1LL << 24;
+__device__ __forceinline__ bool mbar_wait_capped(unsigned bar, unsigned parity, long long cap) {
+    unsigned done = 0;
+    for (long long it = 0; it < cap && !done; ++it)
+        asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+    return done != 0;
+}
+template <typename real, bool ENERGY>
+__global__ void __launch_bounds__(QT_THREADS, 3) k_qapply_t(const SBlk* __restrict__ blks, const DCls* __restrict__ c1,
+                                                            const int2* __restrict__ soff2, SymGeo g, const real* __restrict__ qs,
+                                                            const real* __restrict__ ep, real* __restrict__ x, real* __restrict__ xp,
+                                                            double2* part, int nst, int* err) {
+    constexpr int SPS = QtCfg<real>::SPS, SL = QtCfg<real>::SL, NCW = SBLOCK / 32;
+    extern __shared__ __align__(16) unsigned char qt_raw[];
+    unsigned long long* full = (unsigned long long*)qt_raw;                       // nst <= 8 each
+    unsigned long long* empty = full + 8;
+    real* stg = (real*)(qt_raw + QT_HDR);                                         // nst * SPS slices of SL
+    int2* s_o2 = (int2*)(qt_raw + QT_HDR + (size_t)nst * SPS * SL * sizeof(real));   // the class's slot offsets
+    const SBlk B = blks[blockIdx.x];
+    const DCls C = c1[B.cls];
+    const int ns = C.st_end - C.st_begin, nup = C.nup, nch = (ns + SPS - 1) / SPS;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int s = tid; s < ns; s += blockDim.x) s_o2[s] = soff2[C.st_begin + s];
+    if (tid == 0) {
+        for (int st = 0; st < nst; ++st) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(full + st)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(empty + st)), "r"(NCW));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const real* qrow = qs + (B.q0 + B.t0);        // slot offset 0 of the block's first lattice point
+    const int t = B.t0 + tid;
+    const int vy = t / g.NX, vx = t - vy * g.NX;
+    const int rx = vx - C.lo[0], ry = vy - C.lo[1];
+    const bool row = tid < B.cnt && tid < SBLOCK && (unsigned)rx < (unsigned)C.num[0] && (unsigned)ry < (unsigned)C.num[1];
+    const int pe = C.pbase + ((B.vz + g.H) * g.NP + (vy + g.H)) * g.NP + vx + g.H;
+    KSum<real> a;
+    bool failed = false;
+    if (warp == NCW) {
+        // producer: stage ch % nst takes chunk ch once the consumers have released chunk ch - nst
+        unsigned long long pol;
+        int ch = 0;
+        for (; ch < nch; ++ch) {
+            const int st = ch % nst, s0 = ch * SPS, m = min(SPS, ns - s0);
+            if (ch >= nst) {
+                const bool ok = lane != 0 || mbar_wait_capped(smem_u32(empty + st), (unsigned)((ch / nst - 1) & 1), QT_WAIT_CAP);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    failed = true;
+                    break;
+                }
+            }
+            if (lane == 0)
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(full + st)),
+                             "r"((unsigned)(m * SL * (int)sizeof(real)))
+                             : "memory");
+            __syncwarp();
+            if (lane < m) {
+                const int s = s0 + lane;
+                if (s < nup)
+                    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+                else
+                    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+                const uintptr_t src = (uintptr_t)(qrow + s_o2[s].x) & ~(uintptr_t)15;
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+                        smem_u32(stg + (size_t)(st * SPS + lane) * SL)),
+                    "l"(src), "r"((unsigned)(SL * sizeof(real))), "r"(smem_u32(full + st)), "l"(pol)
+                    : "memory");
+            }
+        }
+        // copies can be in flight only for the last nst chunks issued (one per stage): the producer
+        // waits for them, so that none lands after the block has gone even if a consumer gave up
+        if (lane == 0) {
+            bool landed = true;
+            for (int c = max(0, ch - nst); c < ch; ++c)
+                landed &= mbar_wait_capped(smem_u32(full + c % nst), (unsigned)((c / nst) & 1), QT_WAIT_CAP);
+            if (failed || !landed) atomicOr(err, QT_ERR_BIT);
+        }
+        __syncwarp();
+    } else {
+        const real* __restrict__ e0 = ep + pe;
+        for (int ch = 0; ch < nch; ++ch) {
+            const int st = ch % nst;
+            if (!__all_sync(0xffffffffu, mbar_wait_capped(smem_u32(full + st), (unsigned)((ch / nst) & 1), QT_WAIT_CAP))) {
+                if (lane == 0) atomicOr(err, QT_ERR_BIT);
+                failed = true;
+                break;
+            }
+            if (row) {
+                const real* sq = stg + (size_t)st * SPS * SL;
+                const int s0 = ch * SPS;
+                real qv[SPS], ev[SPS];
+#pragma unroll
+                for (int u = 0; u < SPS; ++u) {
+                    qv[u] = real(0);
+                    ev[u] = real(0);
+                    if (s0 + u < ns) {
+                        const int2 o = s_o2[s0 + u];
+                        const int sh = (int)(((uintptr_t)(qrow + o.x) & 15) / sizeof(real));
+                        qv[u] = sq[u * SL + sh + tid];
+                        ev[u] = __ldg(e0 + o.y);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < SPS; ++u)
+                    if (s0 + u < ns) a.add(qv[u], ev[u]);
+            }
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(empty + st)) : "memory");
+        }
+    }
+    Neu w{0.0, 0.0};
+    if (row && !failed) {
+        x[C.off + ((long long)(B.vz - C.lo[2]) * C.num[1] + ry) * C.num[0] + rx] = a.s;
+        xp[pe] = a.s;
+        if (ENERGY) w = neu_add(w, (double)ep[pe] * (double)a.s);
+    }
+    if (ENERGY) {
+        w = block_reduce(w);
+        if (threadIdx.x == 0) part[blockIdx.x] = make_double2(w.s, w.c);
+    }
+}
+
 // partial[blockIdx] = sum_i e_i x_i over a grid-stride slice (fixed order)
 template <typename real>
 __global__ void __launch_bounds__(BLOCK) k_dot(const real* __restrict__ a, const real* __restrict__ b, long long n,
@@ -1098,7 +1263,6 @@ struct TcGeo {
     int offAlo, offBhi, offBlo, offIdx, offBar;   // shared-memory layout (bytes from the 1024-aligned base)
     int tmem_cols;
 };
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ unsigned long long umma_desc(unsigned addr, unsigned lbo, unsigned sbo) {
     return (unsigned long long)((addr >> 4) & 0x3FFFu) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
            ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);   // version 1, no swizzle
@@ -1231,7 +1395,7 @@ __global__ void __launch_bounds__(tc_threads<PASSES>(), 1) k_curlT_e_tc(TcGeo G,
                              : "=r"(done)
                              : "r"(smem_u32(bar)), "r"(phase));
             failed = __syncthreads_or(!done) != 0;     // the same decision in every thread
-            if (failed && tid == 0) atomicExch(err, 1);
+            if (failed && tid == 0) atomicOr(err, 1);
         }
         phase ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;");
@@ -1576,7 +1740,12 @@ struct ygm_ctx {
     int4* uterm = nullptr;                   // union of the merged C^T M2 terms (class, dx, dy, dz)
     int* acls = nullptr;                     // curl-carrying 1-form class of each GEMM column
     float* wt = nullptr;                     // merged weights, [column][K]
-    int* tc_err = nullptr;                   // set by k_curlT_e_tc when an MMA wait times out
+    bool qt_ok = false;                      // k_qapply_t usable (every copied run inside qsym)
+    int qt_mode = 0;                         // 0 automatic (k_qapply_s), 1 k_qapply_s, 2 k_qapply_t
+    int qt_nst = 0;                          // k_qapply_t stages
+    size_t qt_smem = 0;
+    int* dev_err = nullptr;                  // bit 1: a k_curlT_e_tc MMA wait timed out; bit QT_ERR_BIT:
+                                             // a k_qapply_t copy wait timed out
     size_t tc_smem = 0;
     int tc_grid = 0;
     double2* qpart = nullptr;                // per-block e_i x_i partials of an all-rows k_qapply_s
@@ -1698,6 +1867,46 @@ static std::vector<DRow> make_rows(const std::vector<ygm::DofClass>& cls, int n,
     return rows;
 }
 
+// The device word the kernels set when a bounded wait gives up (read by check_device_flags).
+static int alloc_dev_err(ygm_ctx* ctx) {
+    if (ctx->dev_err) return 0;
+    CK(cudaMalloc((void**)&ctx->dev_err, sizeof(int)));
+    CK(cudaMemsetAsync(ctx->dev_err, 0, sizeof(int), ctx->stream));
+    return 0;
+}
+
+// k_qapply_t stage count: stages = 0 takes the most that fit beside the slot table in 227 KB (at
+// most 4: three blocks per SM in FP32), else 2..8 if they fit.  Sets the kernels' shared-memory size and asks for the largest
+// shared-memory carveout (the stages, not L1, hold the Q1 stream); *bps receives the resident
+// blocks per SM.
+static int qt_configure(ygm_ctx* ctx, int stages, int* bps) {
+    const bool f64 = ctx->precision == YGM_FP64;
+    const size_t slice = (size_t)(f64 ? QtCfg<double>::SPS * QtCfg<double>::SL * 8 : QtCfg<float>::SPS * QtCfg<float>::SL * 4);
+    const size_t tab = (size_t)ctx->max_ns * sizeof(int2);
+    auto fits = [&](int nst) { return QT_HDR + nst * slice + tab <= 227 * 1024; };
+    int nst = 0;
+    if (stages == 0) {
+        for (int t = 4; t >= 2 && !nst; --t)
+            if (fits(t)) nst = t;
+        if (!nst) return fail(ctx, YGM_EINVAL, "k_qapply_t: two stages do not fit in shared memory");
+    } else {
+        if (stages < 2 || stages > 8 || !fits(stages))
+            return fail(ctx, YGM_EINVAL, "k_qapply_t: stages must be 2..8 and fit in 227 KB of shared memory");
+        nst = stages;
+    }
+    const size_t smem = QT_HDR + nst * slice + tab;
+    const void* ks[2] = {f64 ? (const void*)k_qapply_t<double, false> : (const void*)k_qapply_t<float, false>,
+                         f64 ? (const void*)k_qapply_t<double, true> : (const void*)k_qapply_t<float, true>};
+    for (const void* k : ks) {
+        CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        CK(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared));
+    }
+    ctx->qt_nst = nst;
+    ctx->qt_smem = smem;
+    if (bps) CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, ks[0], QT_THREADS, smem));
+    return 0;
+}
+
 // k_qapply_s tables (one column only): (Q1, padded e) offsets per stencil slot and the z-plane
 // ordered block lists -- curl-carrying classes only, then every class.  Skipped (the full-row
 // kernel is used) when the lattice offsets do not fit 32 bits.
@@ -1752,6 +1961,25 @@ static int setup_sym(ygm_ctx* ctx, const std::vector<int>& eoff) {
         return rc;
     ctx->sg = SymGeo{NX, ctx->pg.H, ctx->pg.NP};
     ctx->use_sym = true;
+    // k_qapply_t: every run it copies (aligned down to 16 bytes, SL entries) must lie inside qsym:
+    // checked here for every block and slot, else the kernel is not used
+    ctx->qt_ok = true;
+    {
+        const long long al = 16 / (ctx->precision == YGM_FP64 ? 8 : 4);
+        const long long SL = ctx->precision == YGM_FP64 ? QtCfg<double>::SL : QtCfg<float>::SL;
+        const long long size = (long long)S.qsym.size();
+        for (const SBlk& bk : sb) {
+            for (int sidx = S.st_begin[bk.cls]; sidx < S.st_begin[bk.cls + 1] && ctx->qt_ok; ++sidx) {
+                const long long st = bk.q0 + bk.t0 + o2[sidx].x, lo = st - (st % al + al) % al;
+                if (lo < 0 || lo + SL > size) ctx->qt_ok = false;
+            }
+            if (!ctx->qt_ok) break;
+        }
+    }
+    if (ctx->qt_ok) {
+        if ((rc = alloc_dev_err(ctx))) return rc;
+        if ((rc = qt_configure(ctx, 0, nullptr))) return rc;
+    }
     return 0;
 }
 
@@ -1804,8 +2032,7 @@ static int setup_tc(ygm_ctx* ctx, const std::vector<std::pair<ygm::Nbr, double>>
         return fail(ctx, YGM_EINVAL, "tensor-core C^T M2 tables exceed shared memory (order 3 is not supported)");
     int rc;
     if ((rc = upload(ctx, &ctx->uterm, ut)) || (rc = upload(ctx, &ctx->acls, ac)) || (rc = upload(ctx, &ctx->wt, w))) return rc;
-    CK(cudaMalloc((void**)&ctx->tc_err, sizeof(int)));
-    CK(cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), ctx->stream));
+    if ((rc = alloc_dev_err(ctx))) return rc;
     if (three)
         CK(cudaFuncSetAttribute(k_curlT_e_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->tc_smem));
     else
@@ -2208,7 +2435,19 @@ static int launch_qapply(ygm_ctx* ctx, void* x, bool all_rows) {
         const SBlk* blks = ctx->sblks + (all_rows ? ctx->nsblks_act : 0);
         time_begin(ctx, KQ);
         const size_t smem = (size_t)(ctx->max_ns + 8) * sizeof(int2);
-        if (ctx->precision == YGM_FP64) {
+        if (ctx->qt_ok && ctx->qt_mode == 2) {
+            if (ctx->precision == YGM_FP64) {
+                auto k = all_rows ? k_qapply_t<double, true> : k_qapply_t<double, false>;
+                k<<<nb, QT_THREADS, ctx->qt_smem, ctx->stream>>>(blks, ctx->c1, ctx->soff2, ctx->sg, (const double*)ctx->qsd,
+                                                              (const double*)ctx->ep, (double*)x, (double*)ctx->xp, ctx->qpart,
+                                                              ctx->qt_nst, ctx->dev_err);
+            } else {
+                auto k = all_rows ? k_qapply_t<float, true> : k_qapply_t<float, false>;
+                k<<<nb, QT_THREADS, ctx->qt_smem, ctx->stream>>>(blks, ctx->c1, ctx->soff2, ctx->sg, (const float*)ctx->qsd,
+                                                              (const float*)ctx->ep, (float*)x, (float*)ctx->xp, ctx->qpart,
+                                                              ctx->qt_nst, ctx->dev_err);
+            }
+        } else if (ctx->precision == YGM_FP64) {
             auto k = all_rows ? k_qapply_s<double, true> : k_qapply_s<double, false>;
             k<<<nb, SBLOCK, smem, ctx->stream>>>(blks, ctx->c1, ctx->soff2, ctx->sg, (const double*)ctx->qsd,
                                                  (const double*)ctx->ep, (double*)x, (double*)ctx->xp, ctx->qpart);
@@ -2303,7 +2542,7 @@ static int launch_curlT_e(ygm_ctx* ctx, const void* b, void* e, double ctau, con
             const int thr = ctx->tc_passes == 3 ? tc_threads<3>() : tc_threads<1>();
             k<<<ctx->tc_grid, thr, ctx->tc_smem, ctx->stream>>>(ctx->tcg, ctx->uterm, ctx->c1, ctx->c2, ctx->acls, ctx->wt,
                                                                (const float*)b, (float*)e, (float*)ctx->ep, ctx->pg,
-                                                               split_tau<float>(ctau), ctx->tc_err);
+                                                               split_tau<float>(ctau), ctx->dev_err);
         } else if (ctx->pterms) {
             const size_t smem = (size_t)ctx->max_terms * (ctx->precision == YGM_FP64 ? sizeof(PTerm<double>) : sizeof(PTerm<float>));
             if (ctx->precision == YGM_FP64)
@@ -2432,11 +2671,13 @@ static int launch_energy(ygm_ctx* ctx, const void* e, const void* x, const void*
 // Device-side failures reported through flags (a tensor-core MMA wait that gave up): checked by
 // the calls that synchronise the stream anyway.
 static int check_device_flags(ygm_ctx* ctx) {
-    if (!ctx->tc_err) return 0;
+    if (!ctx->dev_err) return 0;
     int h = 0;
-    CK(cudaMemcpyAsync(&h, ctx->tc_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&h, ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    if (h) return fail(ctx, YGM_ETIMEOUT, "a tensor-core MMA completion wait gave up (k_curlT_e_tc); results are invalid");
+    if (h & 1) return fail(ctx, YGM_ETIMEOUT, "a tensor-core MMA completion wait gave up (k_curlT_e_tc); results are invalid");
+    if (h & QT_ERR_BIT)
+        return fail(ctx, YGM_ETIMEOUT, "a Q1 bulk-copy completion wait gave up (k_qapply_t); results are invalid");
     return 0;
 }
 
@@ -3893,6 +4134,34 @@ int ygm_local_blocks(const ygm_ctx* ctx, int32_t* n1, int32_t* n2a, double* M1, 
     return YGM_OK;
 }
 
+int ygm_set_qapply(ygm_ctx* ctx, int32_t kernel, int32_t stages, int32_t* blocks_per_sm) {
+    if (!ctx) return YGM_EINVAL;
+    if (ctx->host_only) return fail(ctx, YGM_ENODEV, "context was created host-only (device = -1)");
+    if (kernel < 0 || kernel > 2) return fail(ctx, YGM_EINVAL, "kernel must be 0 (automatic), 1 (k_qapply_s) or 2 (k_qapply_t)");
+    if (!ctx->use_sym) return fail(ctx, YGM_EINVAL, "no upper-triangle Q1 path on this context (n_rhs > 1)");
+    if (kernel == 2 && !ctx->qt_ok) return fail(ctx, YGM_EINVAL, "k_qapply_t is not available on this context");
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    int bps = 0;
+    if (ctx->qt_ok) {
+        const int rc = qt_configure(ctx, stages, &bps);
+        if (rc) return rc;
+    } else if (stages) {
+        return fail(ctx, YGM_EINVAL, "stages apply to k_qapply_t only");
+    }
+    ctx->qt_mode = kernel;
+    if (blocks_per_sm) {
+        if (!ctx->qt_ok || kernel != 2) {
+            const size_t smem = (size_t)(ctx->max_ns + 8) * sizeof(int2);
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &bps, ctx->precision == YGM_FP64 ? (const void*)k_qapply_s<double, false> : (const void*)k_qapply_s<float, false>,
+                SBLOCK, smem));
+        }
+        *blocks_per_sm = bps;
+    }
+    return YGM_OK;
+}
+
 int ygm_kernel_timing(ygm_ctx* ctx, int enable) {
     if (!ctx) return YGM_EINVAL;
     if (ctx->host_only) return fail(ctx, YGM_ENODEV, "context was created host-only (device = -1)");
@@ -3948,7 +4217,7 @@ void ygm_destroy(ygm_ctx* ctx) {
                     ctx->qsd,    ctx->soff2,   ctx->sblks,   ctx->xp,      ctx->bp,     ctx->wterms,
                     ctx->cterms, ctx->lblks_b, ctx->lblks_e, ctx->qpart,  ctx->ticket, ctx->M2af,
                     ctx->lblks_es, ctx->sbeg,    ctx->sent,     ctx->uterm,  ctx->acls,  ctx->wt,
-                    ctx->tc_err};
+                    ctx->dev_err};
     for (void* p : more)
         if (p) cudaFree(p);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);

@@ -273,3 +273,19 @@ def test_noalloc_step_argument_checks_without_a_device():
     assert Y._lib.ygm_step_noalloc(c._h, None, p, p, 0.01) == Y.YGM_EINVAL
     assert Y._lib.ygm_step_noalloc(c._h, p, p, p, 0.01) == Y.YGM_ENODEV
     assert b"host-only" in Y._lib.ygm_last_error(c._h)
+
+
+def test_stream_handles_passed_to_the_opts():
+    # None: the context makes its own stream; 0 (torch's default stream) is the legacy default
+    # stream, so events recorded there order with the context's launches; others pass through
+    import paper_2301_01753_gb300 as Y
+    assert Y._stream_arg(None) is None
+    assert Y._stream_arg(0).value == 1
+    assert Y._stream_arg(0x5000).value == 0x5000
+
+
+def test_q1_kernel_selection_needs_a_device():
+    import paper_2301_01753_gb300 as Y
+    c = Y.Context(3, 2, device=-1)
+    with pytest.raises(Y.YgmError):
+        c.set_qapply(2, 0)

@@ -281,3 +281,49 @@ def test_fourth_order_splitting_follows_the_oracle(precision, tol):
     with pytest.raises(Y.YgmError) as ei:
         c.step(1, 1.01 * c.tau_cfl / abs(w[1]))           # CFL on the largest sub-step
     assert ei.value.code == Y.YGM_ECFL
+
+
+# n = 17 and 12: planes of 24 x 17 and 16 x 12 lattice points, so a (class, plane) spans two
+# blocks of 256 with a ragged second one; the small cases also follow the oracle
+@pytest.mark.parametrize("n,k,precision,oracle", [(2, 2, 1, True), (5, 1, 1, True), (4, 2, 0, True), (3, 3, 0, True),
+                                                  (17, 2, 1, False), (12, 3, 1, False), (17, 1, 0, False)])
+def test_q1_kernels_agree_bit_for_bit(n, k, precision, oracle):
+    """The bulk-copy Q1 apply (shared-memory stages) and the per-thread-load one add the same terms
+    in the same order: the states and energies after a run with energy read-outs are identical,
+    for every stage count."""
+    if oracle:
+        f, g, eps, _ = oracle_model(n, k, eps_seed=90 + n)
+    else:
+        eps = synth.tet_eps(90 + n, n, 1.0, 4.0)
+    c0 = Y.Context(n, k, eps=eps, precision=precision, energy_every=7)
+    tau = 0.45 * c0.tau_cfl
+    rng = np.random.default_rng(n * 13 + k)
+    e0 = rng.standard_normal(c0.N1)
+    b0 = np.zeros(c0.N2)
+    dt = np.float64 if precision == Y.YGM_FP64 else np.float32
+    runs = []
+    for kernel, stages in [(1, 0), (2, 0), (2, 2), (2, 5)]:
+        c = c0.like(energy_every=7)           # same operators, fresh state, clock and energy record
+        assert c.set_qapply(kernel, stages) >= 1
+        c.set_state(np.ascontiguousarray(e0, dt), np.ascontiguousarray(b0, dt))
+        c.step(40, tau)
+        e, b = c.get_state(synced=True)
+        runs.append((e, b, c.energy_history()))
+    assert np.linalg.norm(runs[0][1]) > 0
+    for e, b, W in runs[1:]:
+        assert np.array_equal(e, runs[0][0]) and np.array_equal(b, runs[0][1]) and np.array_equal(W, runs[0][2])
+    if oracle:
+        e_or, _, bs_or, _ = run_oracle(f, g, e0, b0, tau, 40)
+        tol = FP32_TOL if precision == Y.YGM_FP32 else PIPE_TOL[k]
+        assert rel_l2(runs[0][0], e_or) < tol and rel_l2(runs[0][1], bs_or) < tol
+
+
+def test_q1_kernel_selection_rejects_bad_arguments():
+    c = Y.Context(4, 2, precision=Y.YGM_FP32)
+    for kernel, stages in [(3, 0), (-1, 0), (2, 1), (2, 9), (0, 99)]:
+        with pytest.raises(Y.YgmError):
+            c.set_qapply(kernel, stages)
+    assert c.set_qapply(0, 0) >= 1
+    r = Y.Context(4, 2, precision=Y.YGM_FP32, n_rhs=4)
+    with pytest.raises(Y.YgmError):
+        r.set_qapply(1, 0)
