@@ -351,6 +351,13 @@ int ygm_local_blocks(const ygm_ctx* ctx, int32_t* n1, int32_t* n2a, double* M1, 
  * no upper-triangle path), YGM_ENODEV, YGM_ECUDA. */
 int ygm_set_qapply(ygm_ctx* ctx, int32_t kernel, int32_t stages, int32_t* blocks_per_sm);
 
+/* Launch mode of the one-column step's kernels (x = Q1 e, the b update, the e update of Eq.
+ * YeeLeapfrog).  pdl = 1 (the default): each is launched with programmatic stream serialization,
+ * so its blocks start and load their constant tables while the previous kernel finishes, then
+ * wait for it before reading its output or writing anything; results are identical to pdl = 0,
+ * ordinary stream-ordered launches.  Errors: YGM_EINVAL (pdl not 0 or 1), YGM_ENODEV. */
+int ygm_set_launch(ygm_ctx* ctx, int32_t pdl);
+
 /* Per-launch CUDA-event timing on the context stream: enable = 1 brackets every kernel launch
  * with a pair of events; ygm_kernel_times synchronises, returns the summed milliseconds and
  * launch counts of each kernel kind since the last query (kinds: 0 Q1 apply, 1 curl -> b,

@@ -19,7 +19,7 @@ YGM_Q1_DEFAULT, YGM_Q1_DIAG, YGM_Q1_SM1, YGM_Q1_SM1SQ = 0, 1, 2, 3
 
 EXPORTED = ["ygm_create", "ygm_create_like", "ygm_sizes", "ygm_set_state", "ygm_get_state", "ygm_project_E", "ygm_step", "ygm_step_noalloc",
             "ygm_energy", "ygm_energy_history", "ygm_time", "ygm_export_q1", "ygm_set_q1", "ygm_spai_op", "ygm_cavity_modes", "ygm_q1_vjp", "ygm_q1_info",
-            "ygm_local_blocks", "ygm_kernel_timing", "ygm_kernel_times", "ygm_set_qapply", "ygm_launch_count", "ygm_adjoint", "ygm_set_splitting",
+            "ygm_local_blocks", "ygm_kernel_timing", "ygm_kernel_times", "ygm_set_qapply", "ygm_set_launch", "ygm_launch_count", "ygm_adjoint", "ygm_set_splitting",
             "ygm_yee_create", "ygm_yee_sizes", "ygm_yee_set_state", "ygm_yee_step", "ygm_yee_get_state",
             "ygm_yee_last_error", "ygm_yee_destroy",
             "ygm_batch_create", "ygm_batch_step", "ygm_batch_status", "ygm_batch_status_clear", "ygm_batch_wait_limit",
@@ -83,6 +83,7 @@ def load_library(path=LIB_PATH):
         "ygm_local_blocks": (C.c_int, [P, pI32, pI32, pD, pD]),
         "ygm_kernel_timing": (C.c_int, [P, C.c_int]),
         "ygm_set_qapply": (C.c_int, [P, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]),
+        "ygm_set_launch": (C.c_int, [P, C.c_int32]),
         "ygm_kernel_times": (C.c_int, [P, pD, pI64]),
         "ygm_launch_count": (C.c_int, [P, pI64]),
         "ygm_qapply_counts": (C.c_int, [P, C.c_int, pI64, pI64, pI64]),
@@ -355,6 +356,10 @@ class Context:
         bps = C.c_int32(0)
         self._check(_lib.ygm_set_qapply(self._h, int(kernel), int(stages), C.byref(bps)))
         return bps.value
+
+    def set_launch(self, pdl=True):
+        """Programmatic dependent launch between the one-column step's kernels (on by default)."""
+        self._check(_lib.ygm_set_launch(self._h, 1 if pdl else 0))
 
     def kernel_timing(self, enable=True):
         self._check(_lib.ygm_kernel_timing(self._h, 1 if enable else 0))

@@ -22,6 +22,7 @@
 #include <map>
 #include <mutex>
 #include <type_traits>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -300,11 +301,22 @@ __device__ __forceinline__ void curl_b_rows(const SBlk& B, const DCls* __restric
     b_out[gi] = v;
     bp[C.pbase + p] = v;
 }
+// Programmatic dependent launch between the kernels of a one-column step (k_qapply_s ->
+// k_curl_b_s -> k_curlT_e_s -> k_qapply_s ...).  Each of them lets the next grid launch once its
+// own blocks are all running (pdl_trigger) and, after loading only constant tables, waits for the
+// previous grid to complete with its writes visible (pdl_wait) before it reads the previous
+// kernel's output or writes anything.  So no kernel touches mutable data before its predecessor
+// has finished, and each predecessor had itself waited for its own.  Under an ordinary launch both
+// instructions do nothing.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 template <typename real>
 __global__ void __launch_bounds__(SBLOCK) k_curl_b_s(const SBlk* __restrict__ blks, const DCls* __restrict__ c2,
                                                      const CTermL* __restrict__ terms, PadGeo g, int NX,
                                                      const real* __restrict__ xp, const real* b_in, real* b_out,
                                                      real* __restrict__ bp, Tau<real> ctau) {
+    pdl_trigger();
+    pdl_wait();
     curl_b_rows(blks[blockIdx.x], c2, terms, g, NX, xp, b_in, b_out, bp, ctau);
 }
 // A dipole source DoF inside a block of k_curlT_e_s: thread, source index, weight d . Lambda1_i(x0).
@@ -363,6 +375,8 @@ __global__ void __launch_bounds__(SBLOCK) k_curlT_e_s(const SBlk* __restrict__ b
     const int tb = pbeg[B.cls], nt = pbeg[B.cls + 1] - tb;
     for (int s = threadIdx.x; s < nt; s += blockDim.x) s_t[s] = terms[tb + s];
     __syncthreads();
+    pdl_trigger();
+    pdl_wait();
     curlT_e_rows(B, c1, s_t, nt, g, NX, bp, e, ctau, ep, sbeg, sent, amp, (int)blockIdx.x);
 }
 
@@ -860,6 +874,8 @@ __global__ void __launch_bounds__(SBLOCK, 1) k_qapply_s(const SBlk* __restrict__
     const int ns = C.st_end - C.st_begin;
     for (int s = threadIdx.x; s < ns; s += blockDim.x) s_o2[s] = soff2[C.st_begin + s];
     __syncthreads();
+    pdl_trigger();
+    pdl_wait();
     const int t = B.t0 + (int)threadIdx.x;
     const int vy = t / g.NX, vx = t - vy * g.NX;
     const int rx = vx - C.lo[0], ry = vy - C.lo[1];
@@ -1740,6 +1756,7 @@ struct ygm_ctx {
     int4* uterm = nullptr;                   // union of the merged C^T M2 terms (class, dx, dy, dz)
     int* acls = nullptr;                     // curl-carrying 1-form class of each GEMM column
     float* wt = nullptr;                     // merged weights, [column][K]
+    bool pdl = true;                         // programmatic dependent launch between the step's kernels
     bool qt_ok = false;                      // k_qapply_t usable (every copied run inside qsym)
     int qt_mode = 0;                         // 0 automatic (k_qapply_s), 1 k_qapply_s, 2 k_qapply_t
     int qt_nst = 0;                          // k_qapply_t stages
@@ -2425,6 +2442,23 @@ static int setup_device(ygm_ctx* ctx) {
 }
 
 // ------------------------------------------------------------------ launch helpers
+// One kernel launch on the context stream; with ctx->pdl the launch carries programmatic stream
+// serialization, so the kernel's blocks may start while the previous kernel of the stream is
+// finishing (the kernel waits for it with pdl_wait before touching its output).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_k(const ygm_ctx* ctx, void (*k)(KArgs...), unsigned grid, unsigned block, size_t smem, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = ctx->pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
 // x = Q1 e of the context state, read from the padded copy of e; all_rows = false computes only
 // the rows of the curl-carrying 1-forms (all that C x needs).  On the upper-triangle path an
 // all-rows apply also leaves the per-block e_i x_i partials of W_n in ctx->qpart.
@@ -2449,12 +2483,12 @@ static int launch_qapply(ygm_ctx* ctx, void* x, bool all_rows) {
             }
         } else if (ctx->precision == YGM_FP64) {
             auto k = all_rows ? k_qapply_s<double, true> : k_qapply_s<double, false>;
-            k<<<nb, SBLOCK, smem, ctx->stream>>>(blks, ctx->c1, ctx->soff2, ctx->sg, (const double*)ctx->qsd,
-                                                 (const double*)ctx->ep, (double*)x, (double*)ctx->xp, ctx->qpart);
+            CK(launch_k(ctx, k, nb, SBLOCK, smem, blks, ctx->c1, ctx->soff2, ctx->sg, (const double*)ctx->qsd,
+                        (const double*)ctx->ep, (double*)x, (double*)ctx->xp, ctx->qpart));
         } else {
             auto k = all_rows ? k_qapply_s<float, true> : k_qapply_s<float, false>;
-            k<<<nb, SBLOCK, smem, ctx->stream>>>(blks, ctx->c1, ctx->soff2, ctx->sg, (const float*)ctx->qsd,
-                                                 (const float*)ctx->ep, (float*)x, (float*)ctx->xp, ctx->qpart);
+            CK(launch_k(ctx, k, nb, SBLOCK, smem, blks, ctx->c1, ctx->soff2, ctx->sg, (const float*)ctx->qsd,
+                        (const float*)ctx->ep, (float*)x, (float*)ctx->xp, ctx->qpart));
         }
         time_end(ctx);
         ctx->launches++;
@@ -2484,13 +2518,11 @@ static int launch_curl_b(ygm_ctx* ctx, const void* x, const void* bin, void* bou
     time_begin(ctx, KB);
     if (ctx->use_sym && ctx->nlb) {      // x was written to its padded copy by k_qapply_s
         if (ctx->precision == YGM_FP64)
-            k_curl_b_s<double><<<ctx->nlb, SBLOCK, 0, ctx->stream>>>(ctx->lblks_b, ctx->c2, ctx->cterms, ctx->pg, ctx->sg.NX,
-                                                                     (const double*)ctx->xp, (const double*)bin, (double*)bout,
-                                                                     (double*)ctx->bp, split_tau<double>(ctau));
+            CK(launch_k(ctx, k_curl_b_s<double>, ctx->nlb, SBLOCK, 0, ctx->lblks_b, ctx->c2, ctx->cterms, ctx->pg, ctx->sg.NX,
+                        (const double*)ctx->xp, (const double*)bin, (double*)bout, (double*)ctx->bp, split_tau<double>(ctau)));
         else
-            k_curl_b_s<float><<<ctx->nlb, SBLOCK, 0, ctx->stream>>>(ctx->lblks_b, ctx->c2, ctx->cterms, ctx->pg, ctx->sg.NX,
-                                                                    (const float*)ctx->xp, (const float*)bin, (float*)bout,
-                                                                    (float*)ctx->bp, split_tau<float>(ctau));
+            CK(launch_k(ctx, k_curl_b_s<float>, ctx->nlb, SBLOCK, 0, ctx->lblks_b, ctx->c2, ctx->cterms, ctx->pg, ctx->sg.NX,
+                        (const float*)ctx->xp, (const float*)bin, (float*)bout, (float*)ctx->bp, split_tau<float>(ctau)));
     } else if (ctx->rshift) {
         if (ctx->precision == YGM_FP64)
             k_curl_b_r<double><<<ctx->nbblocks, BLOCK, 0, ctx->stream>>>(ctx->c1, ctx->c2, ctx->terms, ctx->bblocks, ctx->rshift,
@@ -2523,15 +2555,13 @@ static int launch_curlT_e(ygm_ctx* ctx, const void* b, void* e, double ctau, con
         const int nb = src ? ctx->nle_src : ctx->nle;
         const double* amp = src ? amp_dev : nullptr;
         if (ctx->precision == YGM_FP64)
-            k_curlT_e_s<double><<<nb, SBLOCK, smem, ctx->stream>>>(blks, ctx->c1, ctx->pbeg, (const WTermL<double>*)ctx->wterms,
-                                                                  ctx->pg, ctx->sg.NX, (const double*)ctx->bp, (double*)e,
-                                                                  split_tau<double>(ctau), (double*)ctx->ep, ctx->sbeg,
-                                                                  (const SrcE<double>*)ctx->sent, amp);
+            CK(launch_k(ctx, k_curlT_e_s<double>, nb, SBLOCK, smem, blks, ctx->c1, ctx->pbeg, (const WTermL<double>*)ctx->wterms,
+                        ctx->pg, ctx->sg.NX, (const double*)ctx->bp, (double*)e, split_tau<double>(ctau), (double*)ctx->ep,
+                        ctx->sbeg, (const SrcE<double>*)ctx->sent, amp));
         else
-            k_curlT_e_s<float><<<nb, SBLOCK, smem, ctx->stream>>>(blks, ctx->c1, ctx->pbeg, (const WTermL<float>*)ctx->wterms,
-                                                                 ctx->pg, ctx->sg.NX, (const float*)ctx->bp, (float*)e,
-                                                                 split_tau<float>(ctau), (float*)ctx->ep, ctx->sbeg,
-                                                                 (const SrcE<float>*)ctx->sent, amp);
+            CK(launch_k(ctx, k_curlT_e_s<float>, nb, SBLOCK, smem, blks, ctx->c1, ctx->pbeg, (const WTermL<float>*)ctx->wterms,
+                        ctx->pg, ctx->sg.NX, (const float*)ctx->bp, (float*)e, split_tau<float>(ctau), (float*)ctx->ep,
+                        ctx->sbeg, (const SrcE<float>*)ctx->sent, amp));
         time_end(ctx);
         ctx->launches++;
         return 0;
@@ -4159,6 +4189,14 @@ int ygm_set_qapply(ygm_ctx* ctx, int32_t kernel, int32_t stages, int32_t* blocks
         }
         *blocks_per_sm = bps;
     }
+    return YGM_OK;
+}
+
+int ygm_set_launch(ygm_ctx* ctx, int32_t pdl) {
+    if (!ctx) return YGM_EINVAL;
+    if (ctx->host_only) return fail(ctx, YGM_ENODEV, "context was created host-only (device = -1)");
+    if (pdl != 0 && pdl != 1) return fail(ctx, YGM_EINVAL, "pdl must be 0 or 1");
+    ctx->pdl = pdl != 0;
     return YGM_OK;
 }
 

@@ -289,3 +289,12 @@ def test_q1_kernel_selection_needs_a_device():
     c = Y.Context(3, 2, device=-1)
     with pytest.raises(Y.YgmError):
         c.set_qapply(2, 0)
+
+
+def test_launch_mode_needs_a_device_and_checks_its_argument():
+    import ctypes
+    import paper_2301_01753_gb300 as Y
+    c = Y.Context(3, 1, device=-1)
+    with pytest.raises(Y.YgmError):
+        c.set_launch(True)
+    assert Y._lib.ygm_set_launch(c._h, 2) != 0
