@@ -253,3 +253,55 @@ def test_composed_step_is_symplectic_and_time_symmetric():
     assert np.abs(J.T @ Om @ J - Om).max() < 1e-10 * np.abs(J).max() ** 2
     Jb = g.composed_jacobian(-tau, G.yoshida4())
     assert np.abs(Jb @ J - np.eye(2 * n)).max() < 1e-10 * np.abs(J).max() ** 2
+
+
+def _exact_driven(g, j, s, T):
+    """(e, b)(T) of the driven semi-discrete system e' = C^T M2 b - s(t) j, b' = -C Q1 e from rest
+    (Eq. preYeeFEECEqns with the current term of Eq. allEOM), by SciPy's DOP853 at tight tolerance."""
+    from scipy.integrate import solve_ivp
+    N1 = g.Q1.shape[0]
+    CQ = (g.C @ g.Q1).toarray()
+    CTM = (g.CT @ g.M2).toarray()
+
+    def rhs(t, y):
+        return np.concatenate([CTM @ y[N1:] - s(t) * j, -CQ @ y[:N1]])
+
+    sol = solve_ivp(rhs, (0.0, T), np.zeros(N1 + g.C.shape[0]), method="DOP853", rtol=1e-12, atol=1e-14)
+    return sol.y[:N1, -1], sol.y[N1:, -1]
+
+
+def test_driven_leapfrog_converges_to_the_exact_driven_solution():
+    """The dipole current enters the e update at the half step t_{n+1/2}: from rest, the leapfrog
+    converges at order 2 to the exact driven solution.  Sampling the current at t_n instead (a
+    half-step shift planted here in the oracle) drops the rate to 1, so the pin sees the time
+    placement, the sign and the weight of the source term."""
+    f = FEM(KuhnMesh(2, 1), eps=synth.tet_eps(62, 2, 1.0, 4.0))
+    M1 = f.M1()
+    Q, _ = SP.gym_q1(f, M1)
+    g = G.GYM(f.C(), f.M2(), Q, M1)
+    T = 1.0
+    src = DipoleSource(f, [dict(x=np.array([0.37, 0.58, 0.44]), d=np.array([0.2, 0.1, 1.0]), omega=np.pi * np.sqrt(5.0),
+                               width_steps=5.0)], T / 80)      # sigma = T / 16, t0 = T / 4: over by T
+    j = src(0.3)
+    a = src.items[0]
+    s = lambda t: G.pulse(t, a["amp"], a["omega"], a["t0"], a["sigma"])
+    assert np.allclose(src(0.3), s(0.3) * (j / s(0.3)))
+    jw = j / s(0.3)
+    ee, be = _exact_driven(g, jw, s, T)
+    assert np.linalg.norm(ee) > 1e-3
+    scale = np.linalg.norm(np.concatenate([ee, be]))
+
+    def err(m, shift):
+        tau = T / m
+        z1, z2 = np.zeros(f.mesh.N1), np.zeros(f.C().shape[0])
+        e, b, _ = g.run(z1, g.half_init(z1, z2, tau), tau, m, source=lambda t: src(t - shift * tau))
+        b = g.sync(e, b, tau)
+        return np.linalg.norm(np.concatenate([e - ee, b - be])) / scale
+
+    errs = [err(m, 0.0) for m in (80, 160, 320)]
+    rates = [np.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(abs(r - 2) < 0.15 for r in rates), (errs, rates)
+    assert errs[-1] < 1e-3
+    shifted = [err(m, 0.5) for m in (160, 320)]
+    r_shift = np.log2(shifted[0] / shifted[1])
+    assert abs(r_shift - 1) < 0.2 and shifted[1] > 10 * errs[-1], (shifted, r_shift)
