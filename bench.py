@@ -52,9 +52,12 @@ def source_for(W, dt, column=None):
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one curl-rows Q1-apply launch of
-# the default workload, from the ncu capture summarised in profiles/k_qapply_s_cavity_N32_k2_fp32.md
-# (taken on the kernel as it stands; to be re-taken whenever k_qapply_s changes)
+# the default workload, from the ncu capture summarised in profiles/k_qapply_s_cavity_N32_k2_fp32.md.
+# The kernel has changed since (the programmatic-dependent-launch prologue, no memory operation
+# added), so the line reports traffic as null and this figure as the last capture, of the kernel
+# without that prologue; set QAPPLY_TRAFFIC_CURRENT once a capture of the current kernel exists.
 QAPPLY_TRAFFIC_BYTES = 834.205184e6 + 9.822208e6
+QAPPLY_TRAFFIC_CURRENT = False
 
 
 # ------------------------------------------------------------------ clocks
@@ -401,9 +404,13 @@ def run_ours(args, rank, world, local_rank):
                              d2h_bytes_per_step=rs * (ctx.N1 + ctx.N2) * R),
                     gpu_launches=launches,
                     roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
-                                  traffic=(QAPPLY_TRAFFIC_BYTES if (R == 1 and W["n"] == 32 and W["k"] == 2 and
-                                                                    prec == Y.YGM_FP32) else None),
+                                  traffic=(QAPPLY_TRAFFIC_BYTES if (QAPPLY_TRAFFIC_CURRENT and R == 1 and W["n"] == 32
+                                                                    and W["k"] == 2 and prec == Y.YGM_FP32) else None),
                                   traffic_unit="bytes per launch (ncu, profiles/k_qapply_s_cavity_N32_k2_fp32.md)",
+                                  traffic_last_capture=(QAPPLY_TRAFFIC_BYTES if (R == 1 and W["n"] == 32 and W["k"] == 2
+                                                                                 and prec == Y.YGM_FP32) else None),
+                                  traffic_last_capture_note="k_qapply_s before its two-instruction PDL prologue "
+                                                            "(griddepcontrol); no memory operation changed since",
                                   kernel="k_qapply_s" if R == 1 else "k_qapply_p",
                                   bytes_per_launch=alg_bytes,
                                   launches=dict(curl_rows_only=n_act, all_rows=n_all),
