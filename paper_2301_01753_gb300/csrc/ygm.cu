@@ -905,7 +905,7 @@ __global__ void __launch_bounds__(SBLOCK, 1) k_qapply_s(const SBlk* __restrict__
 // x = Q1 e on the upper-triangle lattice with the Q1 stream moved off the threads' load path.
 // A block's slot s reads the SBLOCK consecutive lattice entries qs[q0 + t0 + o.x(s) + 0 .. SBLOCK-1],
 // one contiguous run per slot.  A producer warp copies the runs into a ring of nst shared-memory
-// stages (cp.async.bulk, QT_SPS slots per stage, one lane per slot; completion counted in bytes on
+// stages (cp.async.bulk, QtCfg::SPS slots per stage, one lane per slot; completion counted in bytes on
 // the stage's "full" mbarrier) while SBLOCK consumer threads, one per row as in k_qapply_s, read
 // their Q1 values from shared memory and gather e; each consumer warp signals a consumed stage on
 // its "empty" mbarrier, which the producer waits for before refilling it.  The warps never wait
@@ -1893,9 +1893,9 @@ static int alloc_dev_err(ygm_ctx* ctx) {
 }
 
 // k_qapply_t stage count: stages = 0 takes the most that fit beside the slot table in 227 KB (at
-// most 4: three blocks per SM in FP32), else 2..8 if they fit.  Sets the kernels' shared-memory size and asks for the largest
-// shared-memory carveout (the stages, not L1, hold the Q1 stream); *bps receives the resident
-// blocks per SM.
+// most 4: three blocks per SM in FP32), else 2..8 if they fit.  Sets the kernels' shared-memory
+// size and asks for the largest shared-memory carveout (the stages, not L1, hold the Q1 stream);
+// *bps receives the resident blocks per SM.
 static int qt_configure(ygm_ctx* ctx, int stages, int* bps) {
     const bool f64 = ctx->precision == YGM_FP64;
     const size_t slice = (size_t)(f64 ? QtCfg<double>::SPS * QtCfg<double>::SL * 8 : QtCfg<float>::SPS * QtCfg<float>::SL * 4);
