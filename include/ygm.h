@@ -52,8 +52,9 @@ extern "C" {
 #define YGM_ENOMEM   -4   /* host or device allocation failed */
 #define YGM_ECUDA    -5   /* a CUDA call failed (message carries cudaGetErrorString) */
 #define YGM_ETIMEOUT -6   /* an iterative host solve (SPAI-OP PCG, cavity modes) reached its
-                             iteration limit without converging, or a device wait of the tensor-core
-                             kernel gave up (reported by the next ygm_get_state / ygm_energy) */
+                             iteration limit without converging, or a bounded device wait gave up:
+                             the tensor-core MMA completion, or a stage of the bulk-copy Q1 apply
+                             (reported by the next ygm_get_state / ygm_energy) */
 #define YGM_ENODEV   -7   /* no CUDA device is available */
 
 #define YGM_FP64 0        /* fields, Q1 and arithmetic in double */
